@@ -1,0 +1,183 @@
+/*
+ * htgb.h -- C-ABI of the GB300 (sm_103a) library for the HSVD truncation of
+ * tensors in the Hierarchical Tucker (HT) format after HT addition.
+ *
+ * Method: Grasedyck & Loebbert, "Distributed Hierarchical SVD in the
+ * Hierarchical Tucker Format".  Each call below names the section / equation
+ * that defines what it computes.  Every floating-point step runs in this
+ * library's CUDA kernels on the tensor's stream; there is no CPU fallback.
+ *
+ * Conventions
+ *  - Modes and tree nodes are 0-based.  The dimension tree is the balanced
+ *    tree of Sec. 2.1 (eq. "balanced"): node {mu..nu} has the sons
+ *    {mu..floor((mu+nu-1)/2)} and the rest (1-based), numbered in pre-order,
+ *    root = 0.  ht_tree_node gives the structure.
+ *  - Ranks are given per node in pre-order; the root's entry is 1 (k_D = 1).
+ *  - Leaf {mu}: frame U (n_mu x k_t), column-major, ld = n_mu.
+ *  - Inner node t with sons s1, s2: transfer tensor B_t (k_t x k_s1 x k_s2),
+ *    element (i,j,l) at (i*k_s1 + j)*k_s2 + l, so M_{2,3}(B_t) is the
+ *    column-major (k_s1 k_s2) x k_t matrix.  The root holds B_D (k_t1 x k_t2)
+ *    as [j][l].
+ *  - "Packed blob": the node arrays above concatenated in pre-order, in the
+ *    tensor's dtype.  ht_tensor_upload / ht_tensor_download use it.
+ *  - Ownership: handles are owned by the library (free them with the
+ *    matching *_free).  Pointers passed in are borrowed for the duration of
+ *    the call; device pointers returned by *_ptr calls stay valid until the
+ *    tensor is freed or changed by an in-place call.
+ *  - Errors: every call returns an ht_status; nothing is thrown across the
+ *    ABI.  ht_last_error() gives a thread-local message for the last failure.
+ *  - Streams: each tensor carries a cudaStream_t (passed as void*; NULL is
+ *    the legacy default stream).  Calls enqueue work on it and return without
+ *    waiting, except where a call is marked "synchronises".
+ */
+#ifndef HTGB_H
+#define HTGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ht_tree ht_tree;
+typedef struct ht_tensor ht_tensor;
+
+typedef enum {
+  HT_OK = 0,
+  HT_EINVAL = 1,       /* bad argument (sizes, ranks, null pointer, mismatched trees) */
+  HT_ENOMEM = 2,       /* device or host allocation failed */
+  HT_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  HT_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+  HT_ENUMERIC = 5,     /* non-finite values met where finite ones are required */
+  HT_EUNSUPPORTED = 6  /* valid request this build does not handle (e.g. dtype/precision mix) */
+} ht_status;
+
+typedef enum { HT_F64 = 0, HT_F32 = 1 } ht_dtype;
+
+/* Arithmetic of the truncation.  HT_PREC_FP64: every step in FP64 (F64
+ * tensors).  HT_PREC_FP32: storage and dense contractions in FP32, the small
+ * k x k Gramian eigendecompositions in FP64 (F32 tensors). */
+typedef enum { HT_PREC_FP64 = 0, HT_PREC_FP32 = 1 } ht_prec;
+
+typedef enum { HT_TRUNC_RANK = 0, HT_TRUNC_EPS = 1 } ht_trunc_mode;
+
+/* Launch schedule: all nodes of one tree level in one batched launch per
+ * step (default), or one launch per tree node (the plain reference schedule). */
+typedef enum { HT_SCHED_LEVEL = 0, HT_SCHED_NODE = 1 } ht_schedule;
+
+/* Options of the truncation T(X) (Sec. 3.3; Sec. 3.5 "to prescribed ranks or
+ * to prescribed accuracy"; Sec. 5: absolute eps with a rank cap).
+ *  mode = HT_TRUNC_RANK: r_t = min(ranks[t] (or rank_cap if ranks == NULL),
+ *         rank_cap if > 0, rank available after orthogonalization).
+ *  mode = HT_TRUNC_EPS:  r_t = smallest r >= 1 with sum_{i>r} sigma_{t,i}^2 <=
+ *         eps_abs^2 / (2d-3), eps_abs = eps * ||X|| if eps_relative, then
+ *         capped as above.  The two sons of the root have the same singular
+ *         values and share one rank (decided on the first son).
+ *  prec: HT_PREC_FP64 needs an F64 tensor, HT_PREC_FP32 an F32 tensor. */
+typedef struct {
+  int mode;
+  double eps;
+  int eps_relative;
+  int rank_cap;
+  const int *ranks; /* host, one per node in pre-order, or NULL */
+  int prec;
+  int schedule;
+} ht_trunc_opts;
+
+/* Optional report (pass NULL to skip; synchronises when given).
+ *  norm         ||X|| = ||B_D||_F after orthogonalization (Sec. 3.4)
+ *  discarded_sq sum over non-root nodes of the discarded sigma^2 (root pair once)
+ *  bound        sqrt(discarded_sq): the a-priori error bound of [Gr10]
+ *  ranks_out    caller array of 2d-1 ints, or NULL: the truncated ranks
+ *  korth_out    caller array of 2d-1 ints, or NULL: ranks after orthogonalization
+ *  sigma_out    caller array, or NULL: for every non-root node in pre-order,
+ *               korth_out[t] singular values (descending), concatenated */
+typedef struct {
+  double norm;
+  double discarded_sq;
+  double bound;
+  int *ranks_out;
+  int *korth_out;
+  double *sigma_out;
+} ht_trunc_report;
+
+/* ---- dimension tree (Sec. 2.1) ---------------------------------------- */
+
+/* Balanced dimension tree for d >= 2 modes (eq. "balanced"). */
+ht_status ht_tree_balanced(int d, ht_tree **out);
+void ht_tree_free(ht_tree *tree);
+/* Number of nodes (2d-1), or -1 for NULL. */
+int ht_tree_num_nodes(const ht_tree *tree);
+/* Structure of node t: mode range [lo, hi], parent (-1 at the root), sons
+ * (-1 at leaves), depth (root 0) and height (leaves 0).  Any output may be NULL. */
+ht_status ht_tree_node(const ht_tree *tree, int t, int *lo, int *hi, int *parent, int *son1, int *son2,
+                       int *depth, int *height);
+
+/* ---- HT container (Sec. 2.2) ------------------------------------------ */
+
+/* Allocate an HT tensor on the current device: n[d] mode sizes, ranks[2d-1]
+ * (root entry ignored, taken as 1), dtype, stream.  Contents are zero. */
+ht_status ht_tensor_create(const ht_tree *tree, const int64_t *n, const int *ranks, ht_dtype dtype, void *stream,
+                           ht_tensor **out);
+ht_status ht_tensor_free(ht_tensor *x);
+/* Current ranks (2d-1 ints); synchronises if ranks were decided on the device. */
+ht_status ht_tensor_ranks(ht_tensor *x, int *ranks);
+/* Number of elements of the packed blob at the current ranks (synchronises like ht_tensor_ranks). */
+ht_status ht_tensor_blob_size(ht_tensor *x, int64_t *count);
+/* Copy a packed blob (current ranks, tensor dtype) from host memory into the
+ * tensor: asynchronous on the tensor's stream; pinned host memory overlaps. */
+ht_status ht_tensor_upload(ht_tensor *x, const void *host_blob);
+/* Copy the tensor out as a packed blob into host memory (synchronises). */
+ht_status ht_tensor_download(ht_tensor *x, void *host_blob);
+/* Device pointer of node t's array (leaf frame / transfer tensor / root),
+ * and its element count at the current ranks. */
+ht_status ht_tensor_node_ptr(ht_tensor *x, int t, void **dev, int64_t *count);
+/* Multiply the tensor by alpha (scales the root transfer matrix). */
+ht_status ht_scale(ht_tensor *x, double alpha);
+
+/* ---- arithmetic --------------------------------------------------------- */
+
+/* HT addition, Lemma "sum of two H-tensors" (Sec. 3.5, eq. "sumleafframes"):
+ * W = [U, V] at the leaves, H_t = blockdiag(B_t, F_t) inside, H_D =
+ * blockdiag(B_D, F_D) at the root.  Allocates *out (ranks k + kbar) on a's
+ * stream.  a and c must share d, n and dtype. */
+ht_status ht_add(const ht_tensor *a, const ht_tensor *c, ht_tensor **out);
+/* Same, into an existing tensor whose ranks already equal k + kbar (no allocation). */
+ht_status ht_add_into(const ht_tensor *a, const ht_tensor *c, ht_tensor *out);
+
+/* Orthogonalization, Sec. 3.4 (leaves -> root): QR of every leaf frame and of
+ * M_{2,3}(B_t) of every inner node after B_t <- (I, R_s1, R_s2) o B_t; the root
+ * becomes R_t1 B_D R_t2^T.  In place; ranks become min(n, k) at leaves and
+ * min(k_t, k_s1 k_s2) inside (eq. "qrtransfer").  prec as in ht_trunc_opts. */
+ht_status ht_orthogonalize(ht_tensor *x, int prec);
+
+/* Reduced Gramians Bhat_t = V_t^T V_t of an ORTHOGONAL tensor, Sec. 3.3: eq.
+ * "acctransferroot" for the sons of the root, eqs. "acctransferSon1/2"
+ * top-down.  dev_out: device FP64 buffer, for every node in pre-order a
+ * k_t x k_t block (column-major; the root's block is the 1x1 matrix 1). */
+ht_status ht_gramians(ht_tensor *x_orth, double *dev_out, int prec);
+
+/* HSVD truncation T(X), Sec. 3.3 after Sec. 3.4, in place: orthogonalize,
+ * Gramians of all non-root nodes, their eigendecompositions (singular values
+ * of every matricization), ranks, then the projection U <- U Q|_r,
+ * B_t <- (Q_t|_r^T, Q_s1|_r^T, Q_s2|_r^T) o B_t (eq. "transfertransformationtrunc"),
+ * B_D <- Q_t1^T B_D Q_t2. */
+ht_status ht_truncate(ht_tensor *x, const ht_trunc_opts *opts, ht_trunc_report *report);
+/* Truncate count tensors (any d, n, ranks; one dtype) with the same options,
+ * each tree level of all tensors in one batched launch.  report: NULL or an
+ * array of count reports. */
+ht_status ht_truncate_batch(ht_tensor *const *xs, int count, const ht_trunc_opts *opts, ht_trunc_report *reports);
+
+/* ||X||: orthogonalizes a copy, returns ||B_D||_F (Sec. 3.4).  Synchronises. */
+ht_status ht_norm(const ht_tensor *x, double *out);
+/* Entries X[idx[e*d + 0], ..., idx[e*d + d-1]] for e < m (Sec. 3.1, eq.
+ * "transfermult").  idx and out are host arrays.  Synchronises. */
+ht_status ht_eval_entries(const ht_tensor *x, const int64_t *idx, int64_t m, double *out);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *ht_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HTGB_H */

@@ -1,0 +1,1663 @@
+// api.cu -- the C-ABI of htgb.h: dimension tree, HT container, HT addition,
+// and the plan builder that turns orthogonalization / Gramians / eigen /
+// rank selection / projection into a short sequence of batched launches.
+//
+// A "plan" is built on the host for one call: every launch walks a device
+// array of work items (internal.h).  Workspace pointers are recorded as
+// tagged offsets while the plan is built, then relocated once the workspace
+// is allocated; items and small metadata arrays are uploaded with a single
+// copy.  All work is stream-ordered on the tensor's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "htgb.h"
+#include "internal.h"
+
+using namespace htgb;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static ht_status fail(ht_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+#define HT_CU(call)                                                                           \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(HT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define HT_TRY(expr)                 \
+  do {                               \
+    ht_status s_ = (expr);           \
+    if (s_ != HT_OK) return s_;      \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// tree (Sec. 2.1)
+// ---------------------------------------------------------------------------
+struct ht_tree {
+  int d = 0, nn = 0, max_depth = 0, max_height = 0;
+  std::vector<int> lo, hi, par, s1, s2, depth, height, leaf_node;
+};
+
+static int tree_rec(ht_tree *T, int lo, int hi, int parent, int depth) {
+  int id = (int)T->lo.size();
+  T->lo.push_back(lo);
+  T->hi.push_back(hi);
+  T->par.push_back(parent);
+  T->depth.push_back(depth);
+  T->s1.push_back(-1);
+  T->s2.push_back(-1);
+  T->height.push_back(0);
+  if (lo != hi) {
+    int last1 = (lo + hi + 1) / 2 - 1;  // eq. "balanced", 0-based
+    int a = tree_rec(T, lo, last1, id, depth + 1);
+    int b = tree_rec(T, last1 + 1, hi, id, depth + 1);
+    T->s1[id] = a;
+    T->s2[id] = b;
+    T->height[id] = 1 + std::max(T->height[a], T->height[b]);
+  }
+  return id;
+}
+
+static void tree_init(ht_tree *T, int d) {
+  T->d = d;
+  tree_rec(T, 0, d - 1, -1, 0);
+  T->nn = (int)T->lo.size();
+  T->leaf_node.assign(d, -1);
+  for (int t = 0; t < T->nn; ++t) {
+    if (T->s1[t] < 0) T->leaf_node[T->lo[t]] = t;
+    T->max_depth = std::max(T->max_depth, T->depth[t]);
+  }
+  T->max_height = T->height[0];
+}
+
+static inline bool is_leaf(const ht_tree &T, int t) { return T.s1[t] < 0; }
+
+// ---------------------------------------------------------------------------
+// container (Sec. 2.2)
+// ---------------------------------------------------------------------------
+struct ht_tensor {
+  ht_tree tr;
+  std::vector<int64_t> n;
+  std::vector<int> k;     // current ranks (host copy, valid if ranks_ok)
+  std::vector<int> cap;   // slot capacities
+  std::vector<int64_t> slot;  // element offset of each node's slot, nn+1 entries
+  int dtype = HT_F64;
+  size_t esz = 8;
+  cudaStream_t stream = nullptr;
+  char *arena = nullptr;
+  int *d_ranks = nullptr;
+  bool ranks_ok = true;
+  bool orthogonal = false;
+};
+
+static int64_t node_elems(const ht_tree &T, const std::vector<int64_t> &n, const std::vector<int> &k, int t) {
+  if (is_leaf(T, t)) return n[T.lo[t]] * (int64_t)k[t];
+  int64_t kt = (t == 0) ? 1 : k[t];
+  return kt * k[T.s1[t]] * k[T.s2[t]];
+}
+
+static void *node_ptr(const ht_tensor *x, int t) { return x->arena + x->slot[t] * x->esz; }
+
+static ht_status sync_ranks(ht_tensor *x) {
+  if (x->ranks_ok) return HT_OK;
+  HT_CU(cudaMemcpyAsync(x->k.data(), x->d_ranks, sizeof(int) * x->tr.nn, cudaMemcpyDeviceToHost, x->stream));
+  HT_CU(cudaStreamSynchronize(x->stream));
+  x->k[0] = 1;
+  x->ranks_ok = true;
+  return HT_OK;
+}
+
+static void set_pool_threshold() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+  uint64_t thr = UINT64_MAX;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+}
+
+static ht_status tensor_alloc(const ht_tree &tr, const int64_t *n, const int *ranks, int dtype, cudaStream_t stream,
+                              ht_tensor **out) {
+  set_pool_threshold();
+  ht_tensor *x = new ht_tensor();
+  x->tr = tr;
+  x->n.assign(n, n + tr.d);
+  x->k.assign(ranks, ranks + tr.nn);
+  x->k[0] = 1;
+  x->cap = x->k;
+  x->dtype = dtype;
+  x->esz = (dtype == HT_F64) ? 8 : 4;
+  x->stream = stream;
+  x->slot.assign(tr.nn + 1, 0);
+  int64_t o = 0;
+  for (int t = 0; t < tr.nn; ++t) {
+    x->slot[t] = o;
+    o += node_elems(tr, x->n, x->cap, t);
+  }
+  x->slot[tr.nn] = o;
+  cudaError_t e = cudaMallocAsync((void **)&x->arena, std::max<int64_t>(o, 1) * x->esz, stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&x->d_ranks, sizeof(int) * tr.nn, stream);
+  if (e != cudaSuccess) {
+    if (x->arena) cudaFreeAsync(x->arena, stream);
+    delete x;
+    return fail(HT_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(x->d_ranks, x->k.data(), sizeof(int) * tr.nn, cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  // the host rank vector must stay alive until the copy has been staged
+  e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  *out = x;
+  return HT_OK;
+}
+
+static ht_status upload_ranks(ht_tensor *x) {
+  x->k[0] = 1;
+  HT_CU(cudaMemcpyAsync(x->d_ranks, x->k.data(), sizeof(int) * x->tr.nn, cudaMemcpyHostToDevice, x->stream));
+  HT_CU(cudaStreamSynchronize(x->stream));
+  x->ranks_ok = true;
+  return HT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plan builder
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint64_t TAG_P = 1ull << 62;  // persistent workspace
+constexpr uint64_t TAG_S = 1ull << 61;  // per-phase scratch workspace
+constexpr uint64_t TAG_M = 1ull << 60;  // metadata appended to the item upload
+constexpr uint64_t TAG_MASK = (1ull << 60) - 1;
+
+enum LKind { L_GEMM, L_QR, L_EIG, L_COPY, L_COMPACT, L_RANKS };
+
+struct Launch {
+  LKind kind;
+  size_t off = 0;  // byte offset of the first item in the upload
+  int n = 0;       // items
+  int tiles = 0;   // GEMM: total tiles
+  int max_m = 0, max_n = 0;
+  bool split = false;
+  int node = -1;
+  const void *ranks = nullptr;  // tagged pointer to the rank array used by the launch
+  void *scratch = nullptr;      // eig scratch (tagged)
+};
+
+template <typename P>
+inline P *tagp(uint64_t tag, size_t off) {
+  return reinterpret_cast<P *>(tag | (uint64_t)off);
+}
+
+struct Plan {
+  std::vector<uint8_t> items;
+  std::vector<uint8_t> meta;
+  std::vector<Launch> launches;
+  size_t p_bytes = 0, s_bytes = 0, s_peak = 0;
+  bool node_sched = false;
+  int dtype = HT_F64;
+  size_t esz = 8;
+  std::string err;  // set by a planning step that cannot handle its input
+
+  // --- workspace ---
+  template <typename P>
+  P *palloc(size_t count) {
+    size_t off = (p_bytes + 255) & ~size_t(255);
+    p_bytes = off + count * sizeof(P);
+    return tagp<P>(TAG_P, off);
+  }
+  void *palloc_bytes(size_t bytes) {
+    size_t off = (p_bytes + 255) & ~size_t(255);
+    p_bytes = off + bytes;
+    return tagp<void>(TAG_P, off);
+  }
+  void *salloc_bytes(size_t bytes) {
+    size_t off = (s_bytes + 255) & ~size_t(255);
+    s_bytes = off + bytes;
+    s_peak = std::max(s_peak, s_bytes);
+    return tagp<void>(TAG_S, off);
+  }
+  void sreset() { s_bytes = 0; }
+  template <typename P>
+  P *mpush(const P *data, size_t count) {
+    size_t off = (meta.size() + 15) & ~size_t(15);
+    meta.resize(off + count * sizeof(P));
+    if (count) memcpy(meta.data() + off, data, count * sizeof(P));
+    return tagp<P>(TAG_M, off);
+  }
+
+  // --- launches ---
+  void begin(LKind kind, const void *ranks = nullptr) {
+    Launch L;
+    L.kind = kind;
+    size_t off = (items.size() + 15) & ~size_t(15);
+    items.resize(off);
+    L.off = off;
+    L.ranks = ranks;
+    launches.push_back(L);
+  }
+  Launch &cur() { return launches.back(); }
+  template <typename I>
+  void push_item(const I &it, int node) {
+    Launch &L = cur();
+    if (node_sched && L.n > 0 && L.node != node) {
+      LKind k = L.kind;
+      const void *r = L.ranks;
+      begin(k, r);
+    }
+    Launch &M = cur();
+    M.node = node;
+    size_t off = items.size();
+    items.resize(off + sizeof(I));
+    memcpy(items.data() + off, &it, sizeof(I));
+    M.n++;
+  }
+  void gemm(GemmItem g, int node) {
+    if (g.ksplit < 1) g.ksplit = 1;
+    if (g.batch < 1) g.batch = 1;
+    if (g.Ko < 1) g.Ko = 1;
+    if (g.n_mult < 1) g.n_mult = 1;
+    if (g.b_mult < 1) g.b_mult = 1;
+    if (g.M <= 0 || g.N <= 0) return;
+    g.tiles_m = (g.M + 63) / 64;
+    g.tiles_n = (g.N + 63) / 64;
+    if (node_sched && cur().n > 0 && cur().node != node) {
+      LKind k = cur().kind;
+      const void *r = cur().ranks;
+      begin(k, r);
+    }
+    Launch &L = cur();
+    g.tile0 = L.tiles;
+    L.tiles += g.tiles_m * g.tiles_n * g.batch * g.ksplit;
+    if (g.ksplit > 1) {
+      L.split = true;
+      g.part = salloc_bytes((size_t)g.ksplit * g.batch * g.M * g.N * esz);
+    }
+    push_item(g, node);
+  }
+  void qr(const QrItem &q, int node) {
+    push_item(q, node);
+    Launch &L = cur();
+    L.max_m = std::max(L.max_m, q.m);
+    L.max_n = std::max(L.max_n, q.n);
+  }
+  void eig(const EigItem &e, int node) {
+    push_item(e, node);
+    cur().max_n = std::max(cur().max_n, e.k);
+  }
+  void copy(const CopyItem &c, int node) { push_item(c, node); }
+  void compact(const CompactItem &c, int node) { push_item(c, node); }
+  void rank(const RankItem &r, int node) { push_item(r, node); }
+};
+
+inline void *reloc(const void *p, char *pb, char *sb, char *mb) {
+  uint64_t u = (uint64_t)p;
+  if (u & TAG_P) return pb + (u & TAG_MASK);
+  if (u & TAG_S) return sb + (u & TAG_MASK);
+  if (u & TAG_M) return mb + (u & TAG_MASK);
+  return const_cast<void *>(p);
+}
+
+template <typename I>
+void reloc_items(uint8_t *base, int n, char *pb, char *sb, char *mb);
+
+template <>
+void reloc_items<GemmItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
+  GemmItem *it = reinterpret_cast<GemmItem *>(base);
+  for (int i = 0; i < n; ++i) {
+    it[i].A = reloc(it[i].A, pb, sb, mb);
+    it[i].B = reloc(it[i].B, pb, sb, mb);
+    it[i].C = reloc(it[i].C, pb, sb, mb);
+    it[i].part = reloc(it[i].part, pb, sb, mb);
+  }
+}
+template <>
+void reloc_items<QrItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
+  QrItem *it = reinterpret_cast<QrItem *>(base);
+  for (int i = 0; i < n; ++i) {
+    it[i].A = reloc(it[i].A, pb, sb, mb);
+    it[i].Q = reloc(it[i].Q, pb, sb, mb);
+    it[i].R = reloc(it[i].R, pb, sb, mb);
+  }
+}
+template <>
+void reloc_items<EigItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
+  EigItem *it = reinterpret_cast<EigItem *>(base);
+  for (int i = 0; i < n; ++i) {
+    it[i].G = (const double *)reloc(it[i].G, pb, sb, mb);
+    it[i].V = (double *)reloc(it[i].V, pb, sb, mb);
+    it[i].lam = (double *)reloc(it[i].lam, pb, sb, mb);
+  }
+}
+template <>
+void reloc_items<CopyItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
+  CopyItem *it = reinterpret_cast<CopyItem *>(base);
+  for (int i = 0; i < n; ++i) {
+    it[i].src = reloc(it[i].src, pb, sb, mb);
+    it[i].dst = reloc(it[i].dst, pb, sb, mb);
+  }
+}
+template <>
+void reloc_items<CompactItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
+  CompactItem *it = reinterpret_cast<CompactItem *>(base);
+  for (int i = 0; i < n; ++i) {
+    it[i].src = reloc(it[i].src, pb, sb, mb);
+    it[i].dst = reloc(it[i].dst, pb, sb, mb);
+  }
+}
+template <>
+void reloc_items<RankItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
+  RankItem *it = reinterpret_cast<RankItem *>(base);
+  for (int i = 0; i < n; ++i) {
+    it[i].lam = (const double *)reloc(it[i].lam, pb, sb, mb);
+    it[i].lam_off = (const int64_t *)reloc(it[i].lam_off, pb, sb, mb);
+    it[i].korth = (const int *)reloc(it[i].korth, pb, sb, mb);
+    it[i].target = (const int *)reloc(it[i].target, pb, sb, mb);
+    it[i].r_out = (int *)reloc(it[i].r_out, pb, sb, mb);
+    it[i].stats = (double *)reloc(it[i].stats, pb, sb, mb);
+    it[i].root = (const double *)reloc(it[i].root, pb, sb, mb);
+  }
+}
+
+// Execute a plan on a stream: allocate workspace (persistent | scratch |
+// upload), relocate, upload, launch.  The workspace is released in stream
+// order after the last launch.  `keep` receives the relocated persistent base
+// (so that callers can read results) and the caller must free it with
+// cudaFreeAsync; if keep is null, everything is freed here.
+ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base) {
+  if (!P.err.empty()) return fail(HT_EUNSUPPORTED, P.err);
+  const size_t p_sz = (P.p_bytes + 255) & ~size_t(255);
+  const size_t s_sz = (P.s_peak + 255) & ~size_t(255);
+  const size_t m_off = p_sz + s_sz;
+  const size_t i_off = m_off + ((P.meta.size() + 255) & ~size_t(255));
+  const size_t total = i_off + P.items.size();
+  char *base = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&base, std::max<size_t>(total, 256), s);
+  if (e != cudaSuccess) return fail(HT_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+  char *pb = base, *sb = base + p_sz, *mb = base + m_off;
+  for (Launch &L : P.launches) {
+    uint8_t *ib = P.items.data() + L.off;
+    switch (L.kind) {
+      case L_GEMM: reloc_items<GemmItem>(ib, L.n, pb, sb, mb); break;
+      case L_QR: reloc_items<QrItem>(ib, L.n, pb, sb, mb); break;
+      case L_EIG: reloc_items<EigItem>(ib, L.n, pb, sb, mb); break;
+      case L_COPY: reloc_items<CopyItem>(ib, L.n, pb, sb, mb); break;
+      case L_COMPACT: reloc_items<CompactItem>(ib, L.n, pb, sb, mb); break;
+      case L_RANKS: reloc_items<RankItem>(ib, L.n, pb, sb, mb); break;
+    }
+    L.ranks = reloc(L.ranks, pb, sb, mb);
+    L.scratch = reloc(L.scratch, pb, sb, mb);
+  }
+  if (!P.meta.empty()) {
+    e = cudaMemcpyAsync(mb, P.meta.data(), P.meta.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  }
+  char *ib_dev = base + i_off;
+  if (!P.items.empty()) {
+    e = cudaMemcpyAsync(ib_dev, P.items.data(), P.items.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  }
+  const bool f64 = (P.dtype == HT_F64);
+  for (const Launch &L : P.launches) {
+    if (L.n == 0) continue;
+    const void *items = ib_dev + L.off;
+    const int *rk = static_cast<const int *>(L.ranks);
+    switch (L.kind) {
+      case L_GEMM:
+        e = f64 ? launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, nullptr, s)
+                : launch_gemm<float>((const GemmItem *)items, L.n, L.tiles, rk, L.split, nullptr, s);
+        break;
+      case L_QR:
+        e = f64 ? launch_qr<double>((const QrItem *)items, L.n, L.max_m, L.max_n, s)
+                : launch_qr<float>((const QrItem *)items, L.n, L.max_m, L.max_n, s);
+        break;
+      case L_EIG: e = launch_eig((const EigItem *)items, L.n, L.max_n, (double *)L.scratch, s); break;
+      case L_COPY: e = launch_copy((const CopyItem *)items, L.n, rk, 0, s); break;
+      case L_COMPACT:
+        e = f64 ? launch_compact<double>((const CompactItem *)items, L.n, rk, s)
+                : launch_compact<float>((const CompactItem *)items, L.n, rk, s);
+        break;
+      case L_RANKS: e = launch_ranks((const RankItem *)items, L.n, s); break;
+    }
+    if (e != cudaSuccess) {
+      cudaFreeAsync(base, s);
+      return fail(HT_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+    }
+  }
+  if (keep_base) {
+    *keep_base = base;
+  } else {
+    e = cudaFreeAsync(base, s);
+    if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  }
+  return HT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-tensor state of a plan
+// ---------------------------------------------------------------------------
+struct TState {
+  ht_tensor *x = nullptr;
+  std::vector<int> kin, ko;       // input ranks, ranks after orthogonalization
+  std::vector<void *> R;          // R factors (T), ko[t] x kin[t], column-major, ld = ko[t]
+  std::vector<void *> G;          // Gramians (T), ko x ko
+  std::vector<double *> G64;      // Gramians (FP64)
+  std::vector<double *> V64;      // eigenvectors (FP64)
+  std::vector<void *> V;          // eigenvectors (T)
+  double *lam = nullptr;          // eigenvalues, all nodes
+  std::vector<int64_t> lam_off;
+  int *r = nullptr;               // truncated ranks (device)
+  double *stats = nullptr;        // norm, discarded, tail2
+  int node_base = 0;              // global index of node 0 in the plan's rank array
+};
+
+inline GemmItem gemm0() {
+  GemmItem g;
+  memset(&g, 0, sizeof(g));
+  g.m_ref = g.n_ref = g.b_ref = -1;
+  g.n_mult = g.b_mult = 1;
+  g.Ko = 1;
+  g.batch = 1;
+  g.ksplit = 1;
+  g.alpha = 1.0;
+  g.beta = 0.0;
+  return g;
+}
+
+inline CopyItem copy0() {
+  CopyItem c;
+  memset(&c, 0, sizeof(c));
+  c.rows_ref = c.cols_ref = -1;
+  c.alpha = 1.0;
+  return c;
+}
+
+// ---- TSQR: reduced QR of tall matrices (m >= n) --------------------------
+struct Mat {
+  const void *A;
+  int64_t lda;
+  int m, n;
+  void *Q;
+  int64_t ldq;
+  void *R;
+  int64_t ldr;
+  int node;
+};
+
+void plan_tsqr(Plan &P, const std::vector<Mat> &mats) {
+  struct Blk {
+    int64_t r0;
+    int m;
+  };
+  struct Lv {
+    const void *A;
+    int64_t lda;
+    int m;
+    void *tgt;
+    int64_t ldt;
+    void *W;
+    void *S;
+    void *QS;
+    std::vector<Blk> blocks;
+    bool top;
+  };
+  const size_t esz = P.esz;
+  std::vector<std::vector<Lv>> lv(mats.size());
+  int max_rounds = 0;
+  for (size_t i = 0; i < mats.size(); ++i) {
+    const Mat &M = mats[i];
+    const int rows_max = qr_max_rows(M.n, (int)esz);
+    if (rows_max < 2 * M.n && M.m > rows_max) {
+      P.err = "QR of a " + std::to_string(M.m) + " x " + std::to_string(M.n) +
+              " matrix: rank too large for the shared-memory TSQR in this precision";
+      return;
+    }
+    const void *A = M.A;
+    int64_t lda = M.lda;
+    int m = M.m;
+    void *tgt = M.Q;
+    int64_t ldt = M.ldq;
+    for (;;) {
+      Lv L;
+      L.A = A;
+      L.lda = lda;
+      L.m = m;
+      L.tgt = tgt;
+      L.ldt = ldt;
+      int p = (m + rows_max - 1) / rows_max;
+      if (p <= 1) {
+        L.top = true;
+        L.W = L.S = L.QS = nullptr;
+        lv[i].push_back(L);
+        break;
+      }
+      L.top = false;
+      L.W = P.salloc_bytes((size_t)m * M.n * esz);
+      L.S = P.salloc_bytes((size_t)p * M.n * M.n * esz);
+      L.QS = P.salloc_bytes((size_t)p * M.n * M.n * esz);
+      int base = m / p, rem = m % p;
+      int64_t r0 = 0;
+      for (int b = 0; b < p; ++b) {
+        int mb = base + (b < rem ? 1 : 0);
+        L.blocks.push_back({r0, mb});
+        r0 += mb;
+      }
+      lv[i].push_back(L);
+      A = L.S;
+      lda = (int64_t)p * M.n;
+      m = p * M.n;
+      tgt = L.QS;
+      ldt = (int64_t)p * M.n;
+    }
+    max_rounds = std::max(max_rounds, (int)lv[i].size());
+  }
+  // QR rounds, bottom-up
+  for (int r = 0; r < max_rounds; ++r) {
+    P.begin(L_QR);
+    for (size_t i = 0; i < mats.size(); ++i) {
+      if (r >= (int)lv[i].size()) continue;
+      const Mat &M = mats[i];
+      const Lv &L = lv[i][r];
+      if (L.top) {
+        QrItem q{L.A, L.tgt, M.R, L.lda, L.ldt, M.ldr, L.m, M.n};
+        P.qr(q, M.node);
+      } else {
+        const int64_t ldS = (int64_t)L.blocks.size() * M.n;
+        for (size_t b = 0; b < L.blocks.size(); ++b) {
+          const Blk &B = L.blocks[b];
+          QrItem q;
+          q.A = static_cast<const char *>(L.A) + B.r0 * esz;
+          q.lda = L.lda;
+          q.Q = static_cast<char *>(L.W) + B.r0 * esz;
+          q.ldq = L.m;
+          q.R = static_cast<char *>(L.S) + (int64_t)b * M.n * esz;
+          q.ldr = ldS;
+          q.m = B.m;
+          q.n = M.n;
+          P.qr(q, M.node);
+        }
+      }
+    }
+  }
+  // recombination, top-down: tgt_r[block b] = W_r[block b] * QS_r[b*n:(b+1)*n, :]
+  for (int r = max_rounds - 2; r >= 0; --r) {
+    P.begin(L_GEMM);
+    for (size_t i = 0; i < mats.size(); ++i) {
+      if (r + 1 >= (int)lv[i].size()) continue;
+      const Mat &M = mats[i];
+      const Lv &L = lv[i][r];
+      const int64_t ldS = (int64_t)L.blocks.size() * M.n;
+      for (size_t b = 0; b < L.blocks.size(); ++b) {
+        const Blk &B = L.blocks[b];
+        GemmItem g = gemm0();
+        g.A = static_cast<const char *>(L.W) + B.r0 * esz;
+        g.sam = 1;
+        g.sak = L.m;
+        g.B = static_cast<const char *>(L.QS) + (int64_t)b * M.n * esz;
+        g.sbk = 1;
+        g.sbn = ldS;
+        g.C = static_cast<char *>(L.tgt) + B.r0 * esz;
+        g.scm = 1;
+        g.scn = L.ldt;
+        g.M = B.m;
+        g.N = M.n;
+        g.K = M.n;
+        P.gemm(g, M.node);
+      }
+    }
+  }
+}
+
+// ---- orthogonalization (Sec. 3.4) ----------------------------------------
+void plan_orthogonalize(Plan &P, std::vector<TState> &TS) {
+  const size_t esz = P.esz;
+  int max_h = 0;
+  for (TState &S : TS) {
+    const ht_tree &T = S.x->tr;
+    S.kin = S.x->k;
+    S.ko = S.kin;
+    S.R.assign(T.nn, nullptr);
+    max_h = std::max(max_h, T.max_height);
+  }
+  for (int h = 0; h <= max_h; ++h) {
+    P.sreset();
+    if (h == 0) {
+      // leaves: U = Q R (Sec. 3.4 step 1)
+      std::vector<Mat> mats;
+      std::vector<CopyItem> rcopies, idfills;
+      std::vector<int> rnodes, inodes;
+      for (TState &S : TS) {
+        const ht_tree &T = S.x->tr;
+        for (int t = 0; t < T.nn; ++t) {
+          if (!is_leaf(T, t)) continue;
+          const int64_t nm = S.x->n[T.lo[t]];
+          const int k = S.kin[t];
+          void *slot = node_ptr(S.x, t);
+          if (nm >= k) {
+            S.R[t] = P.palloc_bytes((size_t)k * k * esz);
+            mats.push_back({slot, nm, (int)nm, k, slot, nm, S.R[t], k, S.node_base + t});
+            S.ko[t] = k;
+          } else {
+            // n < k: Q = I_n, R = U (n x k)
+            S.R[t] = P.palloc_bytes((size_t)nm * k * esz);
+            CopyItem c = copy0();
+            c.src = slot;
+            c.dst = S.R[t];
+            c.sr = 1;
+            c.sc = nm;
+            c.dr = 1;
+            c.dc = nm;
+            c.rows = (int)nm;
+            c.cols = k;
+            c.src_f64 = c.dst_f64 = (P.dtype == HT_F64);
+            rcopies.push_back(c);
+            rnodes.push_back(S.node_base + t);
+            CopyItem idc = copy0();
+            idc.dst = slot;
+            idc.dr = 1;
+            idc.dc = nm;
+            idc.rows = (int)nm;
+            idc.cols = (int)nm;
+            idc.dst_f64 = (P.dtype == HT_F64);
+            idfills.push_back(idc);
+            inodes.push_back(S.node_base + t);
+            S.ko[t] = (int)nm;
+          }
+        }
+      }
+      if (!rcopies.empty()) {
+        P.begin(L_COPY);
+        for (size_t i = 0; i < rcopies.size(); ++i) P.copy(rcopies[i], rnodes[i]);
+        P.begin(L_COPY);
+        for (size_t i = 0; i < idfills.size(); ++i) P.copy(idfills[i], inodes[i]);
+      }
+      if (!mats.empty()) plan_tsqr(P, mats);
+      continue;
+    }
+    // inner nodes of height h: B <- (I, R_s1, R_s2) o B, then QR of M_{2,3}(B)
+    struct Job {
+      TState *S;
+      int t, K0, k1, k2, p1, p2;
+      void *Tbuf, *Bp;
+    };
+    std::vector<Job> jobs;
+    for (TState &S : TS) {
+      const ht_tree &T = S.x->tr;
+      for (int t = 0; t < T.nn; ++t) {
+        if (is_leaf(T, t) || T.height[t] != h) continue;
+        Job J;
+        J.S = &S;
+        J.t = t;
+        J.K0 = (t == 0) ? 1 : S.kin[t];
+        J.k1 = S.kin[T.s1[t]];
+        J.k2 = S.kin[T.s2[t]];
+        J.p1 = S.ko[T.s1[t]];
+        J.p2 = S.ko[T.s2[t]];
+        J.Tbuf = P.salloc_bytes((size_t)J.p2 * J.K0 * J.k1 * esz);
+        J.Bp = (t == 0) ? node_ptr(S.x, 0) : P.salloc_bytes((size_t)J.K0 * J.p1 * J.p2 * esz);
+        jobs.push_back(J);
+      }
+    }
+    if (jobs.empty()) continue;
+    // mode 3: T (p2 x K0*k1) = R2 (p2 x k2) * B_view (k2 x K0*k1)
+    P.begin(L_GEMM);
+    for (Job &J : jobs) {
+      const ht_tree &T = J.S->x->tr;
+      GemmItem g = gemm0();
+      g.A = J.S->R[T.s2[J.t]];
+      g.sam = 1;
+      g.sak = J.p2;
+      g.B = node_ptr(J.S->x, J.t);
+      g.sbk = 1;
+      g.sbn = J.k2;
+      g.C = J.Tbuf;
+      g.scm = 1;
+      g.scn = J.p2;
+      g.M = J.p2;
+      g.N = J.K0 * J.k1;
+      g.K = J.k2;
+      P.gemm(g, J.S->node_base + J.t);
+    }
+    // mode 2: per i, Bp[i] (p2 x p1) = T[i] (p2 x k1) * R1^T (k1 x p1)
+    P.begin(L_GEMM);
+    for (Job &J : jobs) {
+      const ht_tree &T = J.S->x->tr;
+      GemmItem g = gemm0();
+      g.A = J.Tbuf;
+      g.sam = 1;
+      g.sak = J.p2;
+      g.sab = (int64_t)J.k1 * J.p2;
+      g.B = J.S->R[T.s1[J.t]];
+      g.sbk = J.p1;
+      g.sbn = 1;
+      g.C = J.Bp;
+      g.scm = 1;
+      g.scn = J.p2;
+      g.scb = (int64_t)J.p1 * J.p2;
+      g.M = J.p2;
+      g.N = J.p1;
+      g.K = J.k1;
+      g.batch = J.K0;
+      P.gemm(g, J.S->node_base + J.t);
+    }
+    std::vector<Mat> mats;
+    std::vector<CopyItem> rcopies, idfills;
+    std::vector<int> cnodes;
+    for (Job &J : jobs) {
+      if (J.t == 0) continue;
+      TState &S = *J.S;
+      const int64_t m = (int64_t)J.p1 * J.p2;
+      void *slot = node_ptr(S.x, J.t);
+      if (m >= J.K0) {
+        S.R[J.t] = P.palloc_bytes((size_t)J.K0 * J.K0 * esz);
+        mats.push_back({J.Bp, m, (int)m, J.K0, slot, m, S.R[J.t], J.K0, S.node_base + J.t});
+        S.ko[J.t] = J.K0;
+      } else {
+        // k_s1 k_s2 < k_t: Q = I, R = M_{2,3}(B) (eq. "qrtransfer" with k = k_s1 k_s2)
+        S.R[J.t] = P.palloc_bytes((size_t)m * J.K0 * esz);
+        CopyItem c = copy0();
+        c.src = J.Bp;
+        c.dst = S.R[J.t];
+        c.sr = 1;
+        c.sc = m;
+        c.dr = 1;
+        c.dc = m;
+        c.rows = (int)m;
+        c.cols = J.K0;
+        c.src_f64 = c.dst_f64 = (P.dtype == HT_F64);
+        rcopies.push_back(c);
+        CopyItem idc = copy0();
+        idc.dst = slot;
+        idc.dr = 1;
+        idc.dc = m;
+        idc.rows = (int)m;
+        idc.cols = (int)m;
+        idc.dst_f64 = (P.dtype == HT_F64);
+        idfills.push_back(idc);
+        cnodes.push_back(S.node_base + J.t);
+        S.ko[J.t] = (int)m;
+      }
+    }
+    if (!rcopies.empty()) {
+      P.begin(L_COPY);
+      for (size_t i = 0; i < rcopies.size(); ++i) P.copy(rcopies[i], cnodes[i]);
+      P.begin(L_COPY);
+      for (size_t i = 0; i < idfills.size(); ++i) P.copy(idfills[i], cnodes[i]);
+    }
+    if (!mats.empty()) plan_tsqr(P, mats);
+  }
+  for (TState &S : TS) S.ko[0] = 1;
+}
+
+// ---- reduced Gramians (Sec. 3.3) -----------------------------------------
+// dev_out: optional per-tensor FP64 output blocks (ht_gramians); else P-alloc.
+void plan_gramians(Plan &P, std::vector<TState> &TS, const std::vector<double *> *dev_out) {
+  const size_t esz = P.esz;
+  const bool f64 = (P.dtype == HT_F64);
+  int max_d = 0;
+  for (size_t si = 0; si < TS.size(); ++si) {
+    TState &S = TS[si];
+    const ht_tree &T = S.x->tr;
+    S.G.assign(T.nn, nullptr);
+    S.G64.assign(T.nn, nullptr);
+    int64_t off = 0;
+    for (int t = 0; t < T.nn; ++t) {
+      const int kt = (t == 0) ? 1 : S.ko[t];
+      if (dev_out) {
+        S.G64[t] = (*dev_out)[si] + off;
+        off += (int64_t)kt * kt;
+      } else {
+        S.G64[t] = P.palloc<double>((size_t)kt * kt);
+      }
+      S.G[t] = f64 ? (void *)S.G64[t] : P.palloc_bytes((size_t)kt * kt * esz);
+    }
+    max_d = std::max(max_d, T.max_depth);
+  }
+  // root Gramian = 1 (eq. "acctransferroot" written as eqs. "acctransferSon1/2")
+  P.begin(L_COPY);
+  for (TState &S : TS) {
+    CopyItem c = copy0();
+    c.dst = S.G[0];
+    c.rows = c.cols = 1;
+    c.dr = c.dc = 1;
+    c.dst_f64 = f64;
+    P.copy(c, S.node_base);
+    if (!f64) {
+      CopyItem c2 = c;
+      c2.dst = S.G64[0];
+      c2.dst_f64 = 1;
+      P.copy(c2, S.node_base);
+    }
+  }
+  for (int L = 0; L <= max_d; ++L) {
+    P.sreset();
+    struct Job {
+      TState *S;
+      int t, K0, k1, k2;
+      void *C;
+    };
+    std::vector<Job> jobs;
+    int tiles = 0;
+    for (TState &S : TS) {
+      const ht_tree &T = S.x->tr;
+      for (int t = 0; t < T.nn; ++t) {
+        if (is_leaf(T, t) || T.depth[t] != L) continue;
+        Job J;
+        J.S = &S;
+        J.t = t;
+        J.K0 = (t == 0) ? 1 : S.ko[t];
+        J.k1 = S.ko[T.s1[t]];
+        J.k2 = S.ko[T.s2[t]];
+        J.C = P.salloc_bytes((size_t)J.K0 * J.k1 * J.k2 * esz);
+        jobs.push_back(J);
+        tiles += ((J.k1 + 63) / 64) * ((J.k1 + 63) / 64) + ((J.k2 + 63) / 64) * ((J.k2 + 63) / 64);
+      }
+    }
+    if (jobs.empty()) continue;
+    // C[i2,p,l] = sum_i1 Bhat_t[i1,i2] B[i1,p,l]:  C_mat (k1k2 x K0) = B_mat (k1k2 x K0) * Bhat_t
+    P.begin(L_GEMM);
+    for (Job &J : jobs) {
+      GemmItem g = gemm0();
+      g.A = node_ptr(J.S->x, J.t);
+      g.sam = 1;
+      g.sak = (int64_t)J.k1 * J.k2;
+      g.B = J.S->G[J.t];
+      g.sbk = 1;
+      g.sbn = J.K0;
+      g.C = J.C;
+      g.scm = 1;
+      g.scn = (int64_t)J.k1 * J.k2;
+      g.M = J.k1 * J.k2;
+      g.N = J.K0;
+      g.K = J.K0;
+      P.gemm(g, J.S->node_base + J.t);
+    }
+    // eqs. "acctransferSon1" and "acctransferSon2"; the reduction over the
+    // parent index i is split across CTAs when the level has few nodes
+    int ksplit = std::max(1, (2 * kSmCount + tiles - 1) / std::max(tiles, 1));
+    P.begin(L_GEMM);
+    for (Job &J : jobs) {
+      const ht_tree &T = J.S->x->tr;
+      const int s1 = T.s1[J.t], s2 = T.s2[J.t];
+      const int64_t kk = (int64_t)J.k1 * J.k2;
+      GemmItem g = gemm0();
+      g.A = J.C;
+      g.sam = J.k2;
+      g.sak = 1;
+      g.sako = kk;
+      g.B = node_ptr(J.S->x, J.t);
+      g.sbk = 1;
+      g.sbko = kk;
+      g.sbn = J.k2;
+      g.C = J.S->G[s1];
+      g.scm = 1;
+      g.scn = J.k1;
+      g.M = J.k1;
+      g.N = J.k1;
+      g.K = J.k2;
+      g.Ko = J.K0;
+      g.ksplit = std::min(ksplit, J.K0);
+      P.gemm(g, J.S->node_base + J.t);
+      GemmItem h = gemm0();
+      h.A = J.C;
+      h.sam = 1;
+      h.sak = J.k2;
+      h.sako = kk;
+      h.B = node_ptr(J.S->x, J.t);
+      h.sbk = J.k2;
+      h.sbko = kk;
+      h.sbn = 1;
+      h.C = J.S->G[s2];
+      h.scm = 1;
+      h.scn = J.k2;
+      h.M = J.k2;
+      h.N = J.k2;
+      h.K = J.k1;
+      h.Ko = J.K0;
+      h.ksplit = std::min(ksplit, J.K0);
+      P.gemm(h, J.S->node_base + J.t);
+    }
+    if (!f64) {
+      P.begin(L_COPY);
+      for (Job &J : jobs) {
+        const ht_tree &T = J.S->x->tr;
+        for (int s : {T.s1[J.t], T.s2[J.t]}) {
+          const int ks = J.S->ko[s];
+          CopyItem c = copy0();
+          c.src = J.S->G[s];
+          c.dst = J.S->G64[s];
+          c.sr = c.dr = 1;
+          c.sc = c.dc = ks;
+          c.rows = c.cols = ks;
+          c.src_f64 = 0;
+          c.dst_f64 = 1;
+          P.copy(c, J.S->node_base + J.t);
+        }
+      }
+    }
+  }
+}
+
+// ---- eigen + ranks + projection (Sec. 3.3) -------------------------------
+void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, int *rank_array) {
+  (void)rank_array;
+  int max_k = 0, n_big = 0;
+  for (TState &S : TS) {
+    const ht_tree &T = S.x->tr;
+    S.V64.assign(T.nn, nullptr);
+    S.lam_off.assign(T.nn, 0);
+    int64_t off = 0;
+    for (int t = 0; t < T.nn; ++t) {
+      S.lam_off[t] = off;
+      off += (t == 0) ? 1 : S.ko[t];
+    }
+    S.lam = P.palloc<double>((size_t)off);
+    for (int t = 1; t < T.nn; ++t) {
+      S.V64[t] = P.palloc<double>((size_t)S.ko[t] * S.ko[t]);
+      max_k = std::max(max_k, S.ko[t]);
+      if (S.ko[t] > eig_smem_k()) n_big++;
+    }
+  }
+  P.sreset();
+  P.begin(L_EIG);
+  size_t n_eig = 0;
+  for (TState &S : TS) {
+    const ht_tree &T = S.x->tr;
+    for (int t = 1; t < T.nn; ++t) {
+      EigItem e{S.G64[t], S.V64[t], S.lam + S.lam_off[t], S.ko[t]};
+      P.eig(e, S.node_base + t);
+      n_eig++;
+    }
+  }
+  if (max_k > eig_smem_k()) {
+    // one scratch slab per item of a launch (node schedule: one item per launch)
+    size_t per = (size_t)max_k * max_k;
+    size_t cnt = P.node_sched ? 1 : n_eig;
+    void *scr = P.salloc_bytes(per * cnt * sizeof(double));
+    for (Launch &L : P.launches)
+      if (L.kind == L_EIG && !L.scratch) L.scratch = scr;
+  }
+  // ranks
+  P.begin(L_RANKS);
+  for (TState &S : TS) {
+    const ht_tree &T = S.x->tr;
+    S.stats = P.palloc<double>(4);
+    RankItem r;
+    memset(&r, 0, sizeof(r));
+    r.lam = S.lam;
+    r.lam_off = P.mpush(S.lam_off.data(), S.lam_off.size());
+    r.korth = P.mpush(S.ko.data(), S.ko.size());
+    if (o.mode == HT_TRUNC_RANK && o.ranks) r.target = P.mpush(o.ranks, (size_t)T.nn);
+    r.r_out = S.r;
+    r.stats = S.stats;
+    r.root = static_cast<const double *>(node_ptr(S.x, 0));
+    r.root_f64 = (P.dtype == HT_F64);
+    r.root_count = (int64_t)S.ko[T.s1[0]] * S.ko[T.s2[0]];
+    r.nn = T.nn;
+    r.t1 = T.s1[0];
+    r.t2 = T.s2[0];
+    r.d = T.d;
+    r.mode = o.mode;
+    r.eps_rel = o.eps_relative;
+    r.cap = o.rank_cap;
+    r.eps = o.eps;
+    P.rank(r, S.node_base);
+  }
+}
+
+void plan_project(Plan &P, std::vector<TState> &TS, const int *rank_array) {
+  const size_t esz = P.esz;
+  const bool f64 = (P.dtype == HT_F64);
+  P.sreset();
+  // eigenvectors in the working precision; the root's "Q" is the 1x1 identity
+  for (TState &S : TS) {
+    const ht_tree &T = S.x->tr;
+    S.V.assign(T.nn, nullptr);
+    S.V[0] = P.palloc_bytes(esz);
+    for (int t = 1; t < T.nn; ++t) S.V[t] = f64 ? (void *)S.V64[t] : P.palloc_bytes((size_t)S.ko[t] * S.ko[t] * esz);
+  }
+  P.begin(L_COPY);
+  for (TState &S : TS) {
+    const ht_tree &T = S.x->tr;
+    CopyItem c = copy0();
+    c.dst = S.V[0];
+    c.rows = c.cols = 1;
+    c.dr = c.dc = 1;
+    c.dst_f64 = f64;
+    P.copy(c, S.node_base);
+    if (!f64) {
+      for (int t = 1; t < T.nn; ++t) {
+        CopyItem v = copy0();
+        v.src = S.V64[t];
+        v.dst = S.V[t];
+        v.sr = v.dr = 1;
+        v.sc = v.dc = S.ko[t];
+        v.rows = v.cols = S.ko[t];
+        v.src_f64 = 1;
+        v.dst_f64 = 0;
+        P.copy(v, S.node_base + t);
+      }
+    }
+  }
+  const void *rk = rank_array;
+  // leaves: Out = U Q|_r
+  struct LJob {
+    TState *S;
+    int t;
+    int64_t nm;
+    void *out;
+  };
+  std::vector<LJob> lj;
+  P.begin(L_GEMM, rk);
+  for (TState &S : TS) {
+    const ht_tree &T = S.x->tr;
+    for (int t = 0; t < T.nn; ++t) {
+      if (!is_leaf(T, t)) continue;
+      const int64_t nm = S.x->n[T.lo[t]];
+      const int ko = S.ko[t];
+      LJob J{&S, t, nm, P.salloc_bytes((size_t)nm * ko * esz)};
+      lj.push_back(J);
+      GemmItem g = gemm0();
+      g.A = node_ptr(S.x, t);
+      g.sam = 1;
+      g.sak = nm;
+      g.B = S.V[t];
+      g.sbk = 1;
+      g.sbn = ko;
+      g.C = J.out;
+      g.scm = 1;
+      g.scn = nm;
+      g.M = (int)nm;
+      g.N = ko;
+      g.n_ref = S.node_base + t;
+      g.K = ko;
+      P.gemm(g, S.node_base + t);
+    }
+  }
+  // inner nodes and root: (Q_t|_r^T, Q_s1|_r^T, Q_s2|_r^T) o B, mode 1, 2, 3
+  struct IJob {
+    TState *S;
+    int t, K0, k1, k2;
+    void *P1, *P2, *P3;
+  };
+  std::vector<IJob> ij;
+  for (TState &S : TS) {
+    const ht_tree &T = S.x->tr;
+    for (int t = 0; t < T.nn; ++t) {
+      if (is_leaf(T, t)) continue;
+      IJob J;
+      J.S = &S;
+      J.t = t;
+      J.K0 = (t == 0) ? 1 : S.ko[t];
+      J.k1 = S.ko[T.s1[t]];
+      J.k2 = S.ko[T.s2[t]];
+      const size_t sz = (size_t)J.K0 * J.k1 * J.k2 * esz;
+      J.P1 = P.salloc_bytes(sz);
+      J.P2 = P.salloc_bytes(sz);
+      J.P3 = P.salloc_bytes(sz);
+      ij.push_back(J);
+    }
+  }
+  P.begin(L_GEMM, rk);
+  for (IJob &J : ij) {  // mode 1: P1 (k1k2 x r0) = B_mat (k1k2 x K0) * Q_t[:, :r0]
+    const int64_t kk = (int64_t)J.k1 * J.k2;
+    GemmItem g = gemm0();
+    g.A = node_ptr(J.S->x, J.t);
+    g.sam = 1;
+    g.sak = kk;
+    g.B = J.S->V[J.t];
+    g.sbk = 1;
+    g.sbn = J.K0;
+    g.C = J.P1;
+    g.scm = 1;
+    g.scn = kk;
+    g.M = (int)kk;
+    g.N = J.K0;
+    g.n_ref = (J.t == 0) ? -1 : J.S->node_base + J.t;
+    g.K = J.K0;
+    P.gemm(g, J.S->node_base + J.t);
+  }
+  P.begin(L_GEMM, rk);
+  for (IJob &J : ij) {  // mode 2: per a < r0, P2[a] (k2 x r1) = P1[a] (k2 x k1) * Q_s1[:, :r1]
+    const ht_tree &T = J.S->x->tr;
+    const int64_t kk = (int64_t)J.k1 * J.k2;
+    GemmItem g = gemm0();
+    g.A = J.P1;
+    g.sam = 1;
+    g.sak = J.k2;
+    g.sab = kk;
+    g.B = J.S->V[T.s1[J.t]];
+    g.sbk = 1;
+    g.sbn = J.k1;
+    g.C = J.P2;
+    g.scm = 1;
+    g.scn = J.k2;
+    g.scb = kk;
+    g.M = J.k2;
+    g.N = J.k1;
+    g.n_ref = J.S->node_base + T.s1[J.t];
+    g.K = J.k1;
+    g.batch = J.K0;
+    g.b_ref = (J.t == 0) ? -1 : J.S->node_base + J.t;
+    P.gemm(g, J.S->node_base + J.t);
+  }
+  P.begin(L_GEMM, rk);
+  for (IJob &J : ij) {  // mode 3: P3 (r2 x (a,b)) = Q_s2[:, :r2]^T * P2_view (k2 x (a*k1+b))
+    const ht_tree &T = J.S->x->tr;
+    GemmItem g = gemm0();
+    g.A = J.S->V[T.s2[J.t]];
+    g.sam = J.k2;
+    g.sak = 1;
+    g.B = J.P2;
+    g.sbk = 1;
+    g.sbn = J.k2;
+    g.C = J.P3;
+    g.scm = 1;
+    g.scn = J.k2;
+    g.M = J.k2;
+    g.m_ref = J.S->node_base + T.s2[J.t];
+    g.N = J.K0 * J.k1;
+    if (J.t != 0) {
+      g.n_ref = J.S->node_base + J.t;
+      g.n_mult = J.k1;
+    }
+    g.K = J.k2;
+    P.gemm(g, J.S->node_base + J.t);
+  }
+  P.begin(L_COMPACT, rk);
+  for (IJob &J : ij) {
+    const ht_tree &T = J.S->x->tr;
+    CompactItem c;
+    c.src = J.P3;
+    c.dst = node_ptr(J.S->x, J.t);
+    c.ref0 = (J.t == 0) ? -1 : J.S->node_base + J.t;
+    c.ref1 = J.S->node_base + T.s1[J.t];
+    c.ref2 = J.S->node_base + T.s2[J.t];
+    c.ld1 = J.k1;
+    c.ld2 = J.k2;
+    c.max0 = J.K0;
+    c.max1 = J.k1;
+    c.max2 = J.k2;
+    P.compact(c, J.S->node_base + J.t);
+  }
+  P.begin(L_COPY, rk);
+  for (LJob &J : lj) {
+    CopyItem c = copy0();
+    c.src = J.out;
+    c.dst = node_ptr(J.S->x, J.t);
+    c.sr = c.dr = 1;
+    c.sc = c.dc = J.nm;
+    c.rows = (int)J.nm;
+    c.cols = J.S->ko[J.t];
+    c.cols_ref = J.S->node_base + J.t;
+    c.src_f64 = c.dst_f64 = f64;
+    P.copy(c, J.S->node_base + J.t);
+  }
+}
+
+ht_status check_prec(const ht_tensor *x, int prec) {
+  if (prec == HT_PREC_FP64 && x->dtype != HT_F64)
+    return fail(HT_EUNSUPPORTED, "HT_PREC_FP64 needs an HT_F64 tensor");
+  if (prec == HT_PREC_FP32 && x->dtype != HT_F32)
+    return fail(HT_EUNSUPPORTED, "HT_PREC_FP32 needs an HT_F32 tensor");
+  if (prec != HT_PREC_FP64 && prec != HT_PREC_FP32) return fail(HT_EINVAL, "unknown precision");
+  return HT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *ht_last_error(void) { return g_err.c_str(); }
+
+ht_status ht_tree_balanced(int d, ht_tree **out) {
+  if (!out) return fail(HT_EINVAL, "null output");
+  if (d < 2 || d > 1 << 20) return fail(HT_EINVAL, "d must be >= 2");
+  ht_tree *T = new ht_tree();
+  tree_init(T, d);
+  *out = T;
+  return HT_OK;
+}
+
+void ht_tree_free(ht_tree *tree) { delete tree; }
+
+int ht_tree_num_nodes(const ht_tree *tree) { return tree ? tree->nn : -1; }
+
+ht_status ht_tree_node(const ht_tree *T, int t, int *lo, int *hi, int *parent, int *son1, int *son2, int *depth,
+                       int *height) {
+  if (!T || t < 0 || t >= T->nn) return fail(HT_EINVAL, "bad node");
+  if (lo) *lo = T->lo[t];
+  if (hi) *hi = T->hi[t];
+  if (parent) *parent = T->par[t];
+  if (son1) *son1 = T->s1[t];
+  if (son2) *son2 = T->s2[t];
+  if (depth) *depth = T->depth[t];
+  if (height) *height = T->height[t];
+  return HT_OK;
+}
+
+ht_status ht_tensor_create(const ht_tree *tree, const int64_t *n, const int *ranks, ht_dtype dtype, void *stream,
+                           ht_tensor **out) {
+  if (!tree || !n || !ranks || !out) return fail(HT_EINVAL, "null argument");
+  if (dtype != HT_F64 && dtype != HT_F32) return fail(HT_EINVAL, "bad dtype");
+  for (int m = 0; m < tree->d; ++m)
+    if (n[m] < 1) return fail(HT_EINVAL, "mode sizes must be >= 1");
+  for (int t = 1; t < tree->nn; ++t)
+    if (ranks[t] < 1) return fail(HT_EINVAL, "ranks must be >= 1");
+  HT_TRY(tensor_alloc(*tree, n, ranks, dtype, (cudaStream_t)stream, out));
+  ht_tensor *x = *out;
+  HT_CU(cudaMemsetAsync(x->arena, 0, x->slot[tree->nn] * x->esz, x->stream));
+  return HT_OK;
+}
+
+ht_status ht_tensor_free(ht_tensor *x) {
+  if (!x) return HT_OK;
+  cudaFreeAsync(x->arena, x->stream);
+  cudaFreeAsync(x->d_ranks, x->stream);
+  delete x;
+  return HT_OK;
+}
+
+ht_status ht_tensor_ranks(ht_tensor *x, int *ranks) {
+  if (!x || !ranks) return fail(HT_EINVAL, "null argument");
+  HT_TRY(sync_ranks(x));
+  memcpy(ranks, x->k.data(), sizeof(int) * x->tr.nn);
+  return HT_OK;
+}
+
+ht_status ht_tensor_blob_size(ht_tensor *x, int64_t *count) {
+  if (!x || !count) return fail(HT_EINVAL, "null argument");
+  HT_TRY(sync_ranks(x));
+  int64_t s = 0;
+  for (int t = 0; t < x->tr.nn; ++t) s += node_elems(x->tr, x->n, x->k, t);
+  *count = s;
+  return HT_OK;
+}
+
+static bool at_capacity(const ht_tensor *x) {
+  for (int t = 1; t < x->tr.nn; ++t)
+    if (x->k[t] != x->cap[t]) return false;
+  return true;
+}
+
+// gather / scatter between the slots and a packed blob held in device memory
+static ht_status pack_copy(ht_tensor *x, void *packed, bool to_packed) {
+  Plan P;
+  P.dtype = x->dtype;
+  P.esz = x->esz;
+  P.begin(L_COPY);
+  int64_t o = 0;
+  for (int t = 0; t < x->tr.nn; ++t) {
+    int64_t c = node_elems(x->tr, x->n, x->k, t);
+    CopyItem it = copy0();
+    char *pk = static_cast<char *>(packed) + o * x->esz;
+    it.src = to_packed ? node_ptr(x, t) : pk;
+    it.dst = to_packed ? (void *)pk : node_ptr(x, t);
+    it.sr = it.dr = 1;
+    it.sc = it.dc = c;
+    it.rows = (int)c;
+    it.cols = 1;
+    it.src_f64 = it.dst_f64 = (x->dtype == HT_F64);
+    P.copy(it, t);
+    o += c;
+  }
+  return run_plan(P, x->stream, nullptr);
+}
+
+ht_status ht_tensor_upload(ht_tensor *x, const void *host_blob) {
+  if (!x || !host_blob) return fail(HT_EINVAL, "null argument");
+  HT_TRY(sync_ranks(x));
+  int64_t count = 0;
+  for (int t = 0; t < x->tr.nn; ++t) count += node_elems(x->tr, x->n, x->k, t);
+  if (at_capacity(x)) {
+    HT_CU(cudaMemcpyAsync(x->arena, host_blob, count * x->esz, cudaMemcpyHostToDevice, x->stream));
+  } else {
+    void *tmp = nullptr;
+    HT_CU(cudaMallocAsync(&tmp, count * x->esz, x->stream));
+    HT_CU(cudaMemcpyAsync(tmp, host_blob, count * x->esz, cudaMemcpyHostToDevice, x->stream));
+    HT_TRY(pack_copy(x, tmp, false));
+    HT_CU(cudaFreeAsync(tmp, x->stream));
+  }
+  x->orthogonal = false;
+  return HT_OK;
+}
+
+ht_status ht_tensor_download(ht_tensor *x, void *host_blob) {
+  if (!x || !host_blob) return fail(HT_EINVAL, "null argument");
+  HT_TRY(sync_ranks(x));
+  int64_t count = 0;
+  for (int t = 0; t < x->tr.nn; ++t) count += node_elems(x->tr, x->n, x->k, t);
+  if (at_capacity(x)) {
+    HT_CU(cudaMemcpyAsync(host_blob, x->arena, count * x->esz, cudaMemcpyDeviceToHost, x->stream));
+  } else {
+    void *tmp = nullptr;
+    HT_CU(cudaMallocAsync(&tmp, count * x->esz, x->stream));
+    HT_TRY(pack_copy(x, tmp, true));
+    HT_CU(cudaMemcpyAsync(host_blob, tmp, count * x->esz, cudaMemcpyDeviceToHost, x->stream));
+    HT_CU(cudaFreeAsync(tmp, x->stream));
+  }
+  HT_CU(cudaStreamSynchronize(x->stream));
+  return HT_OK;
+}
+
+ht_status ht_tensor_node_ptr(ht_tensor *x, int t, void **dev, int64_t *count) {
+  if (!x || t < 0 || t >= x->tr.nn) return fail(HT_EINVAL, "bad node");
+  HT_TRY(sync_ranks(x));
+  if (dev) *dev = node_ptr(x, t);
+  if (count) *count = node_elems(x->tr, x->n, x->k, t);
+  return HT_OK;
+}
+
+ht_status ht_scale(ht_tensor *x, double alpha) {
+  if (!x) return fail(HT_EINVAL, "null tensor");
+  HT_TRY(sync_ranks(x));
+  int64_t c = node_elems(x->tr, x->n, x->k, 0);
+  cudaError_t e = (x->dtype == HT_F64) ? launch_scale<double>(node_ptr(x, 0), c, alpha, x->stream)
+                                       : launch_scale<float>(node_ptr(x, 0), c, alpha, x->stream);
+  if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  return HT_OK;
+}
+
+static ht_status add_check(const ht_tensor *a, const ht_tensor *c) {
+  if (!a || !c) return fail(HT_EINVAL, "null tensor");
+  if (a->tr.d != c->tr.d) return fail(HT_EINVAL, "tensors have different d");
+  if (a->dtype != c->dtype) return fail(HT_EINVAL, "tensors have different dtype");
+  for (int m = 0; m < a->tr.d; ++m)
+    if (a->n[m] != c->n[m]) return fail(HT_EINVAL, "tensors have different mode sizes");
+  return HT_OK;
+}
+
+static ht_status add_pack(const ht_tensor *a, const ht_tensor *c, ht_tensor *o) {
+  const ht_tree &T = a->tr;
+  std::vector<int64_t> desc(12 * (size_t)T.nn, 0);
+  int64_t max_e = 0;
+  for (int t = 0; t < T.nn; ++t) {
+    int64_t *ds = &desc[12 * (size_t)t];
+    ds[1] = a->slot[t];
+    ds[2] = c->slot[t];
+    ds[3] = o->slot[t];
+    ds[11] = node_elems(T, o->n, o->k, t);
+    max_e = std::max(max_e, ds[11]);
+    if (is_leaf(T, t)) {
+      ds[0] = 0;
+      ds[4] = a->n[T.lo[t]];
+      ds[5] = a->k[t];
+      ds[6] = c->k[t];
+    } else {
+      ds[0] = 1;
+      ds[4] = (t == 0) ? 1 : a->k[t];
+      ds[5] = (t == 0) ? 0 : 1;
+      ds[7] = a->k[T.s1[t]];
+      ds[8] = a->k[T.s2[t]];
+      ds[9] = c->k[T.s1[t]];
+      ds[10] = c->k[T.s2[t]];
+    }
+  }
+  int64_t *d_desc = nullptr;
+  HT_CU(cudaMallocAsync((void **)&d_desc, desc.size() * sizeof(int64_t), o->stream));
+  HT_CU(cudaMemcpyAsync(d_desc, desc.data(), desc.size() * sizeof(int64_t), cudaMemcpyHostToDevice, o->stream));
+  cudaError_t e = (a->dtype == HT_F64)
+                      ? launch_pack_add<double>(a->arena, c->arena, o->arena, d_desc, T.nn, max_e, o->stream)
+                      : launch_pack_add<float>(a->arena, c->arena, o->arena, d_desc, T.nn, max_e, o->stream);
+  if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  HT_CU(cudaFreeAsync(d_desc, o->stream));
+  return HT_OK;
+}
+
+ht_status ht_add(const ht_tensor *a, const ht_tensor *c, ht_tensor **out) {
+  HT_TRY(add_check(a, c));
+  if (!out) return fail(HT_EINVAL, "null output");
+  HT_TRY(sync_ranks(const_cast<ht_tensor *>(a)));
+  HT_TRY(sync_ranks(const_cast<ht_tensor *>(c)));
+  if (a->stream != c->stream) {
+    // c's pending work must be visible on a's stream
+    HT_CU(cudaStreamSynchronize(c->stream));
+  }
+  std::vector<int> k(a->tr.nn);
+  for (int t = 0; t < a->tr.nn; ++t) k[t] = a->k[t] + c->k[t];
+  k[0] = 1;
+  HT_TRY(tensor_alloc(a->tr, a->n.data(), k.data(), a->dtype, a->stream, out));
+  return add_pack(a, c, *out);
+}
+
+ht_status ht_add_into(const ht_tensor *a, const ht_tensor *c, ht_tensor *out) {
+  HT_TRY(add_check(a, c));
+  if (!out) return fail(HT_EINVAL, "null output");
+  HT_TRY(sync_ranks(const_cast<ht_tensor *>(a)));
+  HT_TRY(sync_ranks(const_cast<ht_tensor *>(c)));
+  if (out->tr.d != a->tr.d || out->dtype != a->dtype) return fail(HT_EINVAL, "output does not match");
+  for (int t = 1; t < a->tr.nn; ++t)
+    if (out->cap[t] != a->k[t] + c->k[t]) return fail(HT_EINVAL, "output capacity must equal k + kbar");
+  out->k = out->cap;
+  out->k[0] = 1;
+  out->orthogonal = false;
+  HT_TRY(upload_ranks(out));
+  return add_pack(a, c, out);
+}
+
+ht_status ht_orthogonalize(ht_tensor *x, int prec) {
+  if (!x) return fail(HT_EINVAL, "null tensor");
+  HT_TRY(check_prec(x, prec));
+  HT_TRY(sync_ranks(x));
+  Plan P;
+  P.dtype = x->dtype;
+  P.esz = x->esz;
+  std::vector<TState> TS(1);
+  TS[0].x = x;
+  plan_orthogonalize(P, TS);
+  HT_TRY(run_plan(P, x->stream, nullptr));
+  x->k = TS[0].ko;
+  x->orthogonal = true;
+  return upload_ranks(x);
+}
+
+ht_status ht_gramians(ht_tensor *x, double *dev_out, int prec) {
+  if (!x || !dev_out) return fail(HT_EINVAL, "null argument");
+  HT_TRY(check_prec(x, prec));
+  HT_TRY(sync_ranks(x));
+  Plan P;
+  P.dtype = x->dtype;
+  P.esz = x->esz;
+  std::vector<TState> TS(1);
+  TS[0].x = x;
+  TS[0].ko = x->k;
+  std::vector<double *> outs{dev_out};
+  plan_gramians(P, TS, &outs);
+  return run_plan(P, x->stream, nullptr);
+}
+
+static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_opts *o, ht_trunc_report *rep) {
+  if (!xs || count < 1 || !o) return fail(HT_EINVAL, "null argument");
+  if (o->mode != HT_TRUNC_RANK && o->mode != HT_TRUNC_EPS) return fail(HT_EINVAL, "bad mode");
+  if (o->mode == HT_TRUNC_EPS && !(o->eps >= 0.0)) return fail(HT_EINVAL, "eps must be >= 0");
+  const int dtype = xs[0]->dtype;
+  cudaStream_t s = xs[0]->stream;
+  for (int i = 0; i < count; ++i) {
+    if (!xs[i]) return fail(HT_EINVAL, "null tensor");
+    if (xs[i]->dtype != dtype) return fail(HT_EINVAL, "batch mixes dtypes");
+    HT_TRY(check_prec(xs[i], o->prec));
+    HT_TRY(sync_ranks(xs[i]));
+  }
+  if (count > 1 && o->ranks) return fail(HT_EINVAL, "per-node target ranks are only accepted for a single tensor");
+  Plan P;
+  P.dtype = dtype;
+  P.esz = (dtype == HT_F64) ? 8 : 4;
+  P.node_sched = (o->schedule == HT_SCHED_NODE);
+  std::vector<TState> TS(count);
+  int total_nodes = 0;
+  for (int i = 0; i < count; ++i) {
+    TS[i].x = xs[i];
+    TS[i].node_base = total_nodes;
+    total_nodes += xs[i]->tr.nn;
+  }
+  int *rank_array = P.palloc<int>((size_t)total_nodes);
+  for (int i = 0; i < count; ++i) TS[i].r = rank_array + TS[i].node_base;
+  plan_orthogonalize(P, TS);
+  plan_gramians(P, TS, nullptr);
+  plan_eig_ranks(P, TS, *o, rank_array);
+  plan_project(P, TS, rank_array);
+  char *pb = nullptr;
+  HT_TRY(run_plan(P, s, &pb));
+  // the new ranks live on the device
+  const int *d_r = reinterpret_cast<const int *>(reloc(rank_array, pb, nullptr, nullptr));
+  for (int i = 0; i < count; ++i) {
+    ht_tensor *x = xs[i];
+    if (x->stream != s) HT_CU(cudaStreamSynchronize(s));
+    HT_CU(cudaMemcpyAsync(x->d_ranks, d_r + TS[i].node_base, sizeof(int) * x->tr.nn, cudaMemcpyDeviceToDevice, s));
+    x->ranks_ok = false;
+    x->orthogonal = false;
+  }
+  if (rep) {
+    std::vector<int> r(total_nodes);
+    HT_CU(cudaMemcpyAsync(r.data(), d_r, sizeof(int) * total_nodes, cudaMemcpyDeviceToHost, s));
+    std::vector<std::vector<double>> stats(count, std::vector<double>(4)), lam(count);
+    for (int i = 0; i < count; ++i) {
+      const double *st = reinterpret_cast<const double *>(reloc(TS[i].stats, pb, nullptr, nullptr));
+      HT_CU(cudaMemcpyAsync(stats[i].data(), st, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      lam[i].resize(TS[i].lam_off.back() + TS[i].ko.back());
+      const double *lp = reinterpret_cast<const double *>(reloc(TS[i].lam, pb, nullptr, nullptr));
+      HT_CU(cudaMemcpyAsync(lam[i].data(), lp, lam[i].size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    HT_CU(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i) {
+      ht_trunc_report &R = rep[i];
+      R.norm = stats[i][0];
+      R.discarded_sq = stats[i][1];
+      R.bound = std::sqrt(std::max(0.0, stats[i][1]));
+      const int nn = xs[i]->tr.nn;
+      if (R.ranks_out) memcpy(R.ranks_out, r.data() + TS[i].node_base, sizeof(int) * nn);
+      if (R.korth_out) memcpy(R.korth_out, TS[i].ko.data(), sizeof(int) * nn);
+      if (R.sigma_out) {
+        int64_t o2 = 0;
+        for (int t = 1; t < nn; ++t)
+          for (int q = 0; q < TS[i].ko[t]; ++q) {
+            double l = lam[i][TS[i].lam_off[t] + q];
+            R.sigma_out[o2++] = std::sqrt(l > 0.0 ? l : 0.0);
+          }
+      }
+    }
+  }
+  HT_CU(cudaFreeAsync(pb, s));
+  return HT_OK;
+}
+
+ht_status ht_truncate(ht_tensor *x, const ht_trunc_opts *opts, ht_trunc_report *report) {
+  return truncate_many(&x, 1, opts, report);
+}
+
+ht_status ht_truncate_batch(ht_tensor *const *xs, int count, const ht_trunc_opts *opts, ht_trunc_report *reports) {
+  return truncate_many(xs, count, opts, reports);
+}
+
+ht_status ht_norm(const ht_tensor *xc, double *out) {
+  if (!xc || !out) return fail(HT_EINVAL, "null argument");
+  ht_tensor *x = const_cast<ht_tensor *>(xc);
+  HT_TRY(sync_ranks(x));
+  ht_tensor *y = nullptr;
+  HT_TRY(tensor_alloc(x->tr, x->n.data(), x->cap.data(), x->dtype, x->stream, &y));
+  HT_CU(cudaMemcpyAsync(y->arena, x->arena, x->slot[x->tr.nn] * x->esz, cudaMemcpyDeviceToDevice, x->stream));
+  y->k = x->k;
+  ht_status st = upload_ranks(y);
+  if (st == HT_OK) st = ht_orthogonalize(y, x->dtype == HT_F64 ? HT_PREC_FP64 : HT_PREC_FP32);
+  double *d_s = nullptr;
+  if (st == HT_OK) {
+    int64_t c = node_elems(y->tr, y->n, y->k, 0);
+    cudaError_t e = cudaMallocAsync((void **)&d_s, sizeof(double), y->stream);
+    if (e == cudaSuccess)
+      e = (y->dtype == HT_F64) ? launch_sumsq<double>(node_ptr(y, 0), c, d_s, y->stream)
+                               : launch_sumsq<float>(node_ptr(y, 0), c, d_s, y->stream);
+    double h = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_s, sizeof(double), cudaMemcpyDeviceToHost, y->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(y->stream);
+    if (d_s) cudaFreeAsync(d_s, y->stream);
+    if (e != cudaSuccess) st = fail(HT_ECUDA, cudaGetErrorString(e));
+    *out = std::sqrt(h);
+  }
+  ht_tensor_free(y);
+  return st;
+}
+
+ht_status ht_eval_entries(const ht_tensor *xc, const int64_t *idx, int64_t m, double *out) {
+  if (!xc || (!idx && m > 0) || (!out && m > 0) || m < 0) return fail(HT_EINVAL, "null argument");
+  if (m == 0) return HT_OK;
+  ht_tensor *x = const_cast<ht_tensor *>(xc);
+  HT_TRY(sync_ranks(x));
+  const ht_tree &T = x->tr;
+  const int d = T.d, nn = T.nn;
+  for (int64_t e = 0; e < m; ++e)
+    for (int mu = 0; mu < d; ++mu)
+      if (idx[e * d + mu] < 0 || idx[e * d + mu] >= x->n[mu]) return fail(HT_EINVAL, "index out of range");
+  std::vector<int> tree(5 * (size_t)nn);
+  std::vector<int64_t> node_off(nn), row_off(nn);
+  int64_t rows_per = 0;
+  for (int t = 0; t < nn; ++t) {
+    tree[5 * t + 0] = is_leaf(T, t) ? 1 : 0;
+    tree[5 * t + 1] = T.lo[t];
+    tree[5 * t + 2] = T.s1[t];
+    tree[5 * t + 3] = T.s2[t];
+    tree[5 * t + 4] = T.height[t];
+    node_off[t] = x->slot[t];
+    row_off[t] = rows_per;
+    rows_per += (t == 0) ? 1 : x->k[t];
+  }
+  std::vector<int> level_nodes;
+  std::vector<int> level_start(T.max_height + 2, 0);
+  for (int h = 0; h <= T.max_height; ++h) {
+    level_start[h] = (int)level_nodes.size();
+    for (int t = 0; t < nn; ++t)
+      if (T.height[t] == h) level_nodes.push_back(t);
+  }
+  level_start[T.max_height + 1] = (int)level_nodes.size();
+  // one device block: tree | node_off | row_off | n | idx | level_nodes | rows | out
+  size_t b_tree = tree.size() * sizeof(int), b_no = nn * sizeof(int64_t), b_n = d * sizeof(int64_t);
+  size_t b_idx = (size_t)m * d * sizeof(int64_t), b_lv = level_nodes.size() * sizeof(int);
+  size_t b_rows = (size_t)m * rows_per * sizeof(double), b_out = (size_t)m * sizeof(double);
+  auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+  size_t o_tree = 0, o_no = al(b_tree), o_ro = o_no + al(b_no), o_n = o_ro + al(b_no), o_idx = o_n + al(b_n);
+  size_t o_lv = o_idx + al(b_idx), o_rows = o_lv + al(b_lv), o_out = o_rows + al(b_rows), total = o_out + al(b_out);
+  char *blk = nullptr;
+  HT_CU(cudaMallocAsync((void **)&blk, total, x->stream));
+  HT_CU(cudaMemcpyAsync(blk + o_tree, tree.data(), b_tree, cudaMemcpyHostToDevice, x->stream));
+  HT_CU(cudaMemcpyAsync(blk + o_no, node_off.data(), b_no, cudaMemcpyHostToDevice, x->stream));
+  HT_CU(cudaMemcpyAsync(blk + o_ro, row_off.data(), b_no, cudaMemcpyHostToDevice, x->stream));
+  HT_CU(cudaMemcpyAsync(blk + o_n, x->n.data(), b_n, cudaMemcpyHostToDevice, x->stream));
+  HT_CU(cudaMemcpyAsync(blk + o_idx, idx, b_idx, cudaMemcpyHostToDevice, x->stream));
+  HT_CU(cudaMemcpyAsync(blk + o_lv, level_nodes.data(), b_lv, cudaMemcpyHostToDevice, x->stream));
+  for (int h = 0; h <= T.max_height; ++h) {
+    int cnt = level_start[h + 1] - level_start[h];
+    const int *lvp = reinterpret_cast<const int *>(blk + o_lv) + level_start[h];
+    cudaError_t e =
+        (x->dtype == HT_F64)
+            ? launch_eval_level<double>(x->arena, (const int64_t *)(blk + o_no), x->d_ranks, (const int *)(blk + o_tree),
+                                        (const int64_t *)(blk + o_n), (const int64_t *)(blk + o_idx),
+                                        (const int64_t *)(blk + o_ro), rows_per, lvp, cnt, m, d, (double *)(blk + o_rows),
+                                        (double *)(blk + o_out), x->stream)
+            : launch_eval_level<float>(x->arena, (const int64_t *)(blk + o_no), x->d_ranks, (const int *)(blk + o_tree),
+                                       (const int64_t *)(blk + o_n), (const int64_t *)(blk + o_idx),
+                                       (const int64_t *)(blk + o_ro), rows_per, lvp, cnt, m, d, (double *)(blk + o_rows),
+                                       (double *)(blk + o_out), x->stream);
+    if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  }
+  HT_CU(cudaMemcpyAsync(out, blk + o_out, b_out, cudaMemcpyDeviceToHost, x->stream));
+  HT_CU(cudaFreeAsync(blk, x->stream));
+  HT_CU(cudaStreamSynchronize(x->stream));
+  return HT_OK;
+}
+
+}  // extern "C"

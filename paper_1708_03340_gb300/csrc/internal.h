@@ -1,0 +1,131 @@
+// internal.h -- work items and kernel launchers shared by the library's
+// translation units.  Every kernel walks a device array of work items, so
+// one launch covers all nodes of one tree level (or of many tensors).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace htgb {
+
+constexpr int kSmCount = 152;  // GB300: two dies x 76 SMs
+
+// ---------------------------------------------------------------------------
+// Strided batched contraction ("GEMM" item):
+//   C[m,n] (b) = alpha * sum_{ko<Ko} sum_{k<K} A[m,k,ko](b) * B[k,ko,n](b) + beta * C[m,n](b)
+// element addresses:  A + b*sab + m*sam + k*sak + ko*sako
+//                     B + b*sbb + k*sbk + ko*sbko + n*sbn
+//                     C + b*scb + m*scm + n*scn
+// Dimensions marked by a rank reference (>= 0) are read on the device:
+//   dim = min(dim_literal, ranks[ref] * mult)
+// which lets the projection run on ranks decided on the device (eps mode).
+// Split-K: the Ko range is cut into `ksplit` chunks whose partial sums go to
+// `part` (dense M x N per chunk and batch, column-major); a second kernel sums
+// them in a fixed order.
+// ---------------------------------------------------------------------------
+struct GemmItem {
+  const void *A, *B;
+  void *C;
+  void *part;  // split-K partial buffer (ksplit * batch * M * N elements) or null
+  int64_t sam, sak, sako, sab;
+  int64_t sbk, sbko, sbn, sbb;
+  int64_t scm, scn, scb;
+  int M, N, K, Ko, batch;
+  int m_ref, n_ref, b_ref;  // rank refs (-1: none)
+  int n_mult, b_mult;
+  int ksplit;
+  double alpha, beta;
+  int tiles_m, tiles_n;  // tile grid at the literal (maximal) dims
+  int tile0;             // first global tile index of this item
+};
+
+// Householder QR of one row block (m >= n) held in shared memory.
+//   in  A (m x n, column-major, lda)
+//   out Q (m x n, column-major, ldq), R (n x n upper triangular, column-major,
+//   ldr; rows below the diagonal written as zero).  Q may alias A.
+struct QrItem {
+  const void *A;
+  void *Q, *R;
+  int64_t lda, ldq, ldr;
+  int m, n;
+};
+
+// Symmetric eigendecomposition (FP64) of one k x k matrix.
+struct EigItem {
+  const double *G;  // k x k column-major (symmetrised on load)
+  double *V;        // k x k column-major eigenvectors (descending eigenvalues)
+  double *lam;      // k eigenvalues, descending
+  int k;
+};
+
+// 2-D strided copy with optional cast, identity fill, scaling.
+//   dst[r*dr + c*dc] = src ? alpha*src[r*sr + c*sc] : (r == c ? 1 : 0)
+// rows/cols may be rank references like GemmItem dims (-1: literal).
+struct CopyItem {
+  const void *src;
+  void *dst;
+  int64_t sr, sc, dr, dc;
+  int rows, cols;
+  int rows_ref, cols_ref;
+  int src_f64, dst_f64;
+  double alpha;
+};
+
+// Packed copy of an inner node into its truncated, compact layout:
+//   dst[(a*r1 + b)*r2 + c] = src[(a*ld1 + b)*ld2 + c], a<r0, b<r1, c<r2
+// with r0, r1, r2 read from the device rank array.
+struct CompactItem {
+  const void *src;
+  void *dst;
+  int ref0, ref1, ref2;  // rank refs (ref0 < 0: r0 = 1)
+  int ld1, ld2;
+  int max0, max1, max2;
+};
+
+// Rank selection for one tensor.  Nodes are listed in pre-order from node0.
+struct RankItem {
+  const double *lam;      // eigenvalues of all nodes (offset table lam_off)
+  const int64_t *lam_off; // per node (device)
+  const int *korth;       // ranks after orthogonalization (device)
+  const int *target;      // per node target (rank mode) or null
+  int *r_out;             // truncated ranks (device)
+  double *stats;          // [norm, discarded_sq, tail2] out
+  const double *root;     // orthogonalized root matrix (for ||X||)
+  int root_f64;
+  int64_t root_count;
+  int nn, t1, t2, d;
+  int mode, eps_rel, cap;
+  double eps;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (stream-ordered; return cudaGetLastError())
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks,
+                        bool any_split, const GemmItem *h_items, cudaStream_t s);
+template <typename T>
+cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s);
+cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s);
+cudaError_t launch_copy(const CopyItem *d_items, int n_items, const int *d_ranks, int f64_any, cudaStream_t s);
+template <typename T>
+cudaError_t launch_compact(const CompactItem *d_items, int n_items, const int *d_ranks, cudaStream_t s);
+cudaError_t launch_ranks(const RankItem *d_items, int n_items, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pack_add(const void *a, const void *c, void *out, const int64_t *d_desc, int n_nodes,
+                            int64_t max_elems, cudaStream_t s);
+template <typename T>
+cudaError_t launch_eval_level(const void *x, const int64_t *node_off, const int *ranks, const int *tree,
+                              const int64_t *n, const int64_t *idx, const int64_t *row_off, int64_t rows_per,
+                              const int *level_nodes, int n_level, int64_t m, int d, double *rows, double *out,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_sumsq(const void *x, int64_t count, double *out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale(void *x, int64_t count, double alpha, cudaStream_t s);
+
+// maximum rows of one QR block that fit in shared memory for n columns
+int qr_max_rows(int n, int elem_bytes);
+// largest k whose eigenproblem is solved in shared memory (larger k use a global scratch slab)
+int eig_smem_k();
+
+}  // namespace htgb

@@ -236,7 +236,8 @@ def test_truncate_x_plus_x_is_2x():
     idx = np.stack([np.random.default_rng(1).integers(0, 32, 300) for _ in range(d)], axis=1)
     got = O.eval_entries(d, n, res["k"], res["x"], idx)
     ref = 2.0 * O.eval_entries(d, n, ka, xa, idx)
-    scale = np.abs(ref).max()
+    scale = res["norm"]  # ||X + X|| = ||2X||
+    assert abs(scale - 2.0 * O.truncate(d, n, ka, xa, mode="eps", eps=0.0)["norm"]) <= 1e-13 * scale
     assert np.abs(got - ref).max() <= 1e-12 * scale
 
 
