@@ -174,6 +174,34 @@ ht_status ht_norm(const ht_tensor *x, double *out);
  * "transfermult").  idx and out are host arrays.  Synchronises. */
 ht_status ht_eval_entries(const ht_tensor *x, const int64_t *idx, int64_t m, double *out);
 
+/* ---- tracing ------------------------------------------------------------- */
+
+/* Kernel families of this library, for launch accounting and timing. */
+typedef enum {
+  HT_K_GEMM = 0,    /* strided batched contractions (mode products, Gramians, leaf products, TSQR recombination) */
+  HT_K_QR = 1,      /* Householder QR of shared-memory row blocks (TSQR) */
+  HT_K_EIG = 2,     /* FP64 symmetric eigensolver */
+  HT_K_COPY = 3,    /* copies, casts, identity fills */
+  HT_K_COMPACT = 4, /* packing of projected transfer tensors */
+  HT_K_RANKS = 5,   /* rank selection and ||X|| */
+  HT_K_ADD = 6,     /* HT addition packing */
+  HT_K_EVAL = 7,    /* entry evaluation */
+  HT_K_MISC = 8,    /* norms, scaling */
+  HT_K_COUNT = 9
+} ht_kernel_kind;
+
+/* Record CUDA events around every launch of the kinds set in mask (bit
+ * 1 << kind) on the launching stream; 0 switches recording off.  Not thread-safe. */
+ht_status ht_profile_set(unsigned mask);
+/* Launches, summed device time (ms) and summed algorithmic flops (counted at
+ * the launches' maximal dimensions: m n k products for contractions,
+ * 4 m n^2 - 4 n^3 / 3 per QR block, 9 k^3 per eigendecomposition) of one kind
+ * recorded since the last reset; synchronises on the recorded events.
+ * reset != 0 clears the record.  Any output may be NULL. */
+ht_status ht_profile_read(int kind, int64_t *launches, double *total_ms, double *flops, int reset);
+/* Number of kernels this library has launched since it was loaded (all kinds). */
+ht_status ht_launch_count(int64_t *total);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *ht_last_error(void);
 

@@ -8,6 +8,7 @@
 // is allocated; items and small metadata arrays are uploaded with a single
 // copy.  All work is stream-ordered on the tensor's stream.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -40,6 +41,54 @@ static ht_status fail(ht_status s, const std::string &msg) {
     ht_status s_ = (expr);           \
     if (s_ != HT_OK) return s_;      \
   } while (0)
+
+// ---------------------------------------------------------------------------
+// tracing: launch count and CUDA-event timing per kernel family
+// ---------------------------------------------------------------------------
+namespace {
+std::atomic<int64_t> g_launches{0};
+unsigned g_prof_mask = 0;
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+  double flops;
+};
+std::vector<ProfRec> g_prof_open, g_prof_done;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t get_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+namespace htgb {
+void count_launch(int n) { g_launches += n; }
+void prof_begin(int kind, cudaStream_t s) {
+  if (!(g_prof_mask & (1u << kind))) return;
+  ProfRec r{kind, get_event(), get_event(), 0.0};
+  cudaEventRecord(r.a, s);
+  g_prof_open.push_back(r);
+}
+void prof_end(int kind, cudaStream_t s, double flops) {
+  if (!(g_prof_mask & (1u << kind))) return;
+  for (size_t i = g_prof_open.size(); i-- > 0;) {
+    if (g_prof_open[i].kind == kind) {
+      cudaEventRecord(g_prof_open[i].b, s);
+      g_prof_open[i].flops = flops;
+      g_prof_done.push_back(g_prof_open[i]);
+      g_prof_open.erase(g_prof_open.begin() + i);
+      return;
+    }
+  }
+}
+}  // namespace htgb
 
 // ---------------------------------------------------------------------------
 // tree (Sec. 2.1)
@@ -193,6 +242,7 @@ struct Launch {
   int max_m = 0, max_n = 0;
   bool split = false;
   int node = -1;
+  double flops = 0.0;  // algorithmic flops of the launch (literal, i.e. maximal, dims)
   const void *ranks = nullptr;  // tagged pointer to the rank array used by the launch
   void *scratch = nullptr;      // eig scratch (tagged)
 };
@@ -282,6 +332,7 @@ struct Plan {
     Launch &L = cur();
     g.tile0 = L.tiles;
     L.tiles += g.tiles_m * g.tiles_n * g.batch * g.ksplit;
+    L.flops += 2.0 * g.M * g.N * (double)g.K * g.Ko * g.batch;
     if (g.ksplit > 1) {
       L.split = true;
       g.part = salloc_bytes((size_t)g.ksplit * g.batch * g.M * g.N * esz);
@@ -293,10 +344,13 @@ struct Plan {
     Launch &L = cur();
     L.max_m = std::max(L.max_m, q.m);
     L.max_n = std::max(L.max_n, q.n);
+    // Householder QR with the explicit Q factor: 4 m n^2 - 4 n^3 / 3
+    L.flops += 4.0 * q.m * (double)q.n * q.n - 4.0 / 3.0 * (double)q.n * q.n * q.n;
   }
   void eig(const EigItem &e, int node) {
     push_item(e, node);
     cur().max_n = std::max(cur().max_n, e.k);
+    cur().flops += 9.0 * (double)e.k * e.k * e.k;  // symmetric eigendecomposition with vectors
   }
   void copy(const CopyItem &c, int node) { push_item(c, node); }
   void compact(const CompactItem &c, int node) { push_item(c, node); }
@@ -415,6 +469,7 @@ ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base) {
     if (L.n == 0) continue;
     const void *items = ib_dev + L.off;
     const int *rk = static_cast<const int *>(L.ranks);
+    prof_begin((int)L.kind, s);
     switch (L.kind) {
       case L_GEMM:
         e = f64 ? launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, nullptr, s)
@@ -424,7 +479,7 @@ ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base) {
         e = f64 ? launch_qr<double>((const QrItem *)items, L.n, L.max_m, L.max_n, s)
                 : launch_qr<float>((const QrItem *)items, L.n, L.max_m, L.max_n, s);
         break;
-      case L_EIG: e = launch_eig((const EigItem *)items, L.n, L.max_n, (double *)L.scratch, s); break;
+      case L_EIG: e = launch_eig((const EigItem *)items, L.n, L.max_n, (double *)L.scratch, s, f64 ? 0 : 1); break;
       case L_COPY: e = launch_copy((const CopyItem *)items, L.n, rk, 0, s); break;
       case L_COMPACT:
         e = f64 ? launch_compact<double>((const CompactItem *)items, L.n, rk, s)
@@ -432,6 +487,7 @@ ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base) {
         break;
       case L_RANKS: e = launch_ranks((const RankItem *)items, L.n, s); break;
     }
+    prof_end((int)L.kind, s, L.flops);
     if (e != cudaSuccess) {
       cudaFreeAsync(base, s);
       return fail(HT_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
@@ -954,7 +1010,7 @@ void plan_gramians(Plan &P, std::vector<TState> &TS, const std::vector<double *>
 // ---- eigen + ranks + projection (Sec. 3.3) -------------------------------
 void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, int *rank_array) {
   (void)rank_array;
-  int max_k = 0, n_big = 0;
+  int max_k = 0;
   for (TState &S : TS) {
     const ht_tree &T = S.x->tr;
     S.V64.assign(T.nn, nullptr);
@@ -968,7 +1024,6 @@ void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, in
     for (int t = 1; t < T.nn; ++t) {
       S.V64[t] = P.palloc<double>((size_t)S.ko[t] * S.ko[t]);
       max_k = std::max(max_k, S.ko[t]);
-      if (S.ko[t] > eig_smem_k()) n_big++;
     }
   }
   P.sreset();
@@ -982,9 +1037,9 @@ void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, in
       n_eig++;
     }
   }
-  if (max_k > eig_smem_k()) {
+  if (eig_scratch_needed(max_k, P.dtype == HT_F64 ? 0 : 1)) {
     // one scratch slab per item of a launch (node schedule: one item per launch)
-    size_t per = (size_t)max_k * max_k;
+    size_t per = 4 * (size_t)max_k * max_k;
     size_t cnt = P.node_sched ? 1 : n_eig;
     void *scr = P.salloc_bytes(per * cnt * sizeof(double));
     for (Launch &L : P.launches)
@@ -1226,6 +1281,48 @@ extern "C" {
 
 const char *ht_last_error(void) { return g_err.c_str(); }
 
+ht_status ht_profile_set(unsigned mask) {
+  g_prof_mask = mask & ((1u << HT_K_COUNT) - 1);
+  return HT_OK;
+}
+
+ht_status ht_profile_read(int kind, int64_t *launches, double *total_ms, double *flops, int reset) {
+  if (kind < 0 || kind >= HT_K_COUNT) return fail(HT_EINVAL, "bad kernel kind");
+  int64_t cnt = 0;
+  double ms = 0.0, fl = 0.0;
+  for (const ProfRec &r : g_prof_done) {
+    if (r.kind != kind) continue;
+    HT_CU(cudaEventSynchronize(r.b));
+    float f = 0.f;
+    HT_CU(cudaEventElapsedTime(&f, r.a, r.b));
+    ms += f;
+    fl += r.flops;
+    cnt++;
+  }
+  if (launches) *launches = cnt;
+  if (total_ms) *total_ms = ms;
+  if (flops) *flops = fl;
+  if (reset) {
+    std::vector<ProfRec> keep;
+    for (const ProfRec &r : g_prof_done) {
+      if (r.kind == kind) {
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+      } else {
+        keep.push_back(r);
+      }
+    }
+    g_prof_done.swap(keep);
+  }
+  return HT_OK;
+}
+
+ht_status ht_launch_count(int64_t *total) {
+  if (!total) return fail(HT_EINVAL, "null argument");
+  *total = g_launches.load();
+  return HT_OK;
+}
+
 ht_status ht_tree_balanced(int d, ht_tree **out) {
   if (!out) return fail(HT_EINVAL, "null output");
   if (d < 2 || d > 1 << 20) return fail(HT_EINVAL, "d must be >= 2");
@@ -1412,9 +1509,11 @@ static ht_status add_pack(const ht_tensor *a, const ht_tensor *c, ht_tensor *o) 
   int64_t *d_desc = nullptr;
   HT_CU(cudaMallocAsync((void **)&d_desc, desc.size() * sizeof(int64_t), o->stream));
   HT_CU(cudaMemcpyAsync(d_desc, desc.data(), desc.size() * sizeof(int64_t), cudaMemcpyHostToDevice, o->stream));
+  prof_begin(HT_K_ADD, o->stream);
   cudaError_t e = (a->dtype == HT_F64)
                       ? launch_pack_add<double>(a->arena, c->arena, o->arena, d_desc, T.nn, max_e, o->stream)
                       : launch_pack_add<float>(a->arena, c->arena, o->arena, d_desc, T.nn, max_e, o->stream);
+  prof_end(HT_K_ADD, o->stream, 0.0);
   if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
   HT_CU(cudaFreeAsync(d_desc, o->stream));
   return HT_OK;

@@ -105,7 +105,9 @@ cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, c
                         bool any_split, const GemmItem *h_items, cudaStream_t s);
 template <typename T>
 cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s);
-cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s);
+// mode 0: FP64 QL; mode 1: FP32 QL followed by one FP64 refinement step.
+// scratch: 4 * max_k^2 doubles per item when max_k exceeds the shared-memory sizes (eig_scratch_needed).
+cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s, int mode);
 cudaError_t launch_copy(const CopyItem *d_items, int n_items, const int *d_ranks, int f64_any, cudaStream_t s);
 template <typename T>
 cudaError_t launch_compact(const CompactItem *d_items, int n_items, const int *d_ranks, cudaStream_t s);
@@ -123,9 +125,15 @@ cudaError_t launch_sumsq(const void *x, int64_t count, double *out, cudaStream_t
 template <typename T>
 cudaError_t launch_scale(void *x, int64_t count, double alpha, cudaStream_t s);
 
+// launch accounting / tracing (api.cu)
+void count_launch(int n = 1);
+void prof_begin(int kind, cudaStream_t s);
+void prof_end(int kind, cudaStream_t s, double flops);
+
 // maximum rows of one QR block that fit in shared memory for n columns
 int qr_max_rows(int n, int elem_bytes);
 // largest k whose eigenproblem is solved in shared memory (larger k use a global scratch slab)
 int eig_smem_k();
+inline bool eig_scratch_needed(int max_k, int mode) { return mode == 0 ? max_k > 128 : max_k > 64; }
 
 }  // namespace htgb

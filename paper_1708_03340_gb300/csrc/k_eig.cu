@@ -1,14 +1,25 @@
-// k_eig.cu -- batched symmetric eigendecomposition in FP64 (Sec. 3.3:
-// Bhat_t Q_t = Q_t Sigma_t^2 gives the singular values and left singular
-// vectors of every matricization).  One CTA per matrix:
-//   1. Householder reduction to tridiagonal form, T = H^T G H;
-//   2. explicit H from the stored reflectors;
-//   3. implicit QL iteration with Wilkinson shifts on (d, e).  One thread
-//      runs the scalar recurrence of a sweep and logs its Givens rotations;
-//      then every thread applies the logged rotations to its own rows of H;
-//   4. eigenvalues sorted descending, eigenvectors permuted alike.
-// Matrices with k <= kEigSmemK live in shared memory, larger ones in a
-// global scratch slab of the item.
+// k_eig.cu -- batched symmetric eigendecompositions of the reduced Gramians
+// (Sec. 3.3: Bhat_t Q_t = Q_t Sigma_t^2 gives the singular values and left
+// singular vectors of every matricization).  One CTA per matrix.
+//
+// eig_ql_kernel<T>: Householder reduction to tridiagonal form, explicit H
+// from the reflectors, implicit QL with Wilkinson shifts, sort.  The matrix is
+// scaled by 1/max|G| first.  One thread runs the scalar QL recurrence of a
+// sweep and logs its Givens rotations; every thread then applies the logged
+// rotations to its own rows of H.  On GB300 a dependent FP64 operation costs
+// ~64 cycles and an FP64 divide or square root ~430-670 cycles, so the
+// recurrence uses one reciprocal square root per rotation and no divides.
+//
+// refine_kernel: one step of the Ogita-Aishima iterative refinement
+// (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue
+// decomposition", Japan J. Indust. Appl. Math. 35, 2018), written from its
+// first-order conditions: with X the current eigenvectors, R = I - X^T X,
+// S = X^T G X, lambda_i = S_ii / (1 - R_ii) and E solving
+// E + E^T = R, (S + E^T S + S E) diagonal to first order:
+//   E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)   if |lambda_i - lambda_j| > delta
+//   E_ij = R_ij / 2                                           otherwise (cluster)
+// X <- X (I + E).  Used in FP64 after an FP32 QL solve: the dense products
+// keep every warp's FP64 pipe busy instead of a one-lane scalar chain.
 #include "internal.h"
 
 namespace htgb {
@@ -18,71 +29,126 @@ namespace {
 constexpr int EIG_THREADS = 256;
 constexpr int kEigSmemK = 128;
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-__device__ double block_sum_d(double v, double *red) {
+template <typename T>
+__device__ T block_sum_t(T v, T *red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum_d(v);
+  v = warp_sum_t(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T s = (lane < nw) ? red[lane] : T(0);
+  return warp_sum_t(s);
+}
+
+__device__ double block_max_d(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
   double s = (lane < nw) ? red[lane] : 0.0;
-  return warp_sum_d(s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  return s;
 }
 
 struct EigShared {
-  int count;  // rotations logged in this sweep
-  int lo;     // first index of the rotation chain (rotations act on (i, i+1), i from hi-1 down to lo)
+  int count;
+  int lo;
   int done;
   int status;
 };
 
-__global__ void __launch_bounds__(EIG_THREADS) eig_kernel(const EigItem *__restrict__ items, double *scratch,
-                                                          int64_t scratch_stride) {
+// Givens rotation with r = sqrt(f^2 + g^2), s = f / r, c = g / r.
+__device__ __forceinline__ void givens(double f, double g, double &r, double &s, double &c) {
+  const double q = f * f + g * g;  // the matrix is scaled to O(1): no overflow, underflow only at 1e-154
+  if (q == 0.0) {
+    r = 0.0;
+    s = 0.0;
+    c = 1.0;
+    return;
+  }
+  const double ri = rsqrt(q);
+  r = q * ri;
+  s = f * ri;
+  c = g * ri;
+}
+__device__ __forceinline__ void givens(float f, float g, float &r, float &s, float &c) {
+  const float m = fmaxf(fabsf(f), fabsf(g));
+  if (m == 0.0f) {
+    r = 0.0f;
+    s = 0.0f;
+    c = 1.0f;
+    return;
+  }
+  const float im = 1.0f / m;  // keep f^2 + g^2 away from FP32 underflow
+  const float fs = f * im, gs = g * im;
+  const float q = fs * fs + gs * gs;
+  const float ri = rsqrtf(q);
+  r = m * q * ri;
+  s = fs * ri;
+  c = gs * ri;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__restrict__ items, void *scratch,
+                                                             int64_t scratch_stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EigItem it = items[blockIdx.x];
   const int k = it.k, tid = threadIdx.x, nt = blockDim.x;
-  double *Z;
-  double *tail;
+  // layout: [32 doubles][Z: k*k T, when it fits][6k + 32 T][k ints]; the FP64
+  // scratch comes first so that it stays 8-byte aligned for any k
+  double *redd = reinterpret_cast<double *>(smem_raw);
+  T *Z;
+  T *tail;
   if (k <= kEigSmemK) {
-    Z = reinterpret_cast<double *>(smem_raw);
+    Z = reinterpret_cast<T *>(redd + 32);
     tail = Z + (int64_t)k * k;
   } else {
-    Z = scratch + (int64_t)blockIdx.x * scratch_stride;
-    tail = reinterpret_cast<double *>(smem_raw);
+    Z = static_cast<T *>(scratch) + (int64_t)blockIdx.x * scratch_stride;
+    tail = reinterpret_cast<T *>(redd + 32);
   }
-  double *dg = tail;        // diagonal, k
-  double *eo = dg + k;      // off-diagonal, k
-  double *tau = eo + k;     // reflector factors, k
-  double *pv = tau + k;     // work vector p / w, k
-  double *rc = pv + k;      // rotation cosines, k
-  double *rs = rc + k;      // rotation sines, k
-  double *red = rs + k;     // 32
+  T *dg = tail;
+  T *eo = dg + k;
+  T *tau = eo + k;
+  T *pv = tau + k;
+  T *rc = pv + k;
+  T *rs = rc + k;
+  T *red = rs + k;
   int *perm = reinterpret_cast<int *>(red + 32);
   __shared__ EigShared sh;
   const int ld = k;
-  // load, symmetrised
+  // scale to max |G| = 1 (symmetrised)
+  double mx = 0.0;
+  for (int e = tid; e < k * k; e += nt) mx = fmax(mx, fabs(it.G[e]));
+  mx = block_max_d(mx, redd);
+  const double scale = (mx > 0.0) ? mx : 1.0;
+  const double inv_scale = 1.0 / scale;
   for (int e = tid; e < k * k; e += nt) {
     int c = e / k, r = e - c * k;
-    Z[e] = 0.5 * (it.G[(int64_t)c * k + r] + it.G[(int64_t)r * k + c]);
+    Z[e] = T(0.5 * (it.G[(int64_t)c * k + r] + it.G[(int64_t)r * k + c]) * inv_scale);
   }
   __syncthreads();
   // 1. tridiagonalisation: step j annihilates Z[j+2:k, j]
   for (int j = 0; j + 2 < k; ++j) {
-    double *x = Z + (int64_t)j * ld;  // column j; reflector acts on rows j+1..k-1
-    double part = 0.0;
+    T *x = Z + (int64_t)j * ld;
+    T part = T(0);
     for (int r = j + 2 + tid; r < k; r += nt) part += x[r] * x[r];
-    const double s2 = block_sum_d(part, red);
-    const double alpha = x[j + 1];
-    double tj = 0.0, beta = alpha;
-    if (s2 != 0.0) {
-      const double nrm = sqrt(alpha * alpha + s2);
-      beta = (alpha <= 0.0) ? nrm : -nrm;
-      const double inv_v0 = 1.0 / (alpha - beta);
+    const T s2 = block_sum_t(part, red);
+    const T alpha = x[j + 1];
+    T tj = T(0), beta = alpha;
+    if (s2 != T(0)) {
+      const T nrm = sqrt(alpha * alpha + s2);
+      beta = (alpha <= T(0)) ? nrm : -nrm;
+      const T inv_v0 = T(1) / (alpha - beta);
       tj = (beta - alpha) / beta;
       for (int r = j + 2 + tid; r < k; r += nt) x[r] *= inv_v0;
     }
@@ -92,28 +158,24 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_kernel(const EigItem *__restr
       dg[j] = x[j];
       eo[j] = beta;
     }
-    if (tj != 0.0) {
-      // v = [1; x[j+2:k]] on rows j+1..k-1; trailing block A' = Z[j+1:, j+1:]
+    if (tj != T(0)) {
       const int L = k - j - 1;
-      // p = tau A' v
       for (int rr = tid; rr < L; rr += nt) {
         const int r = j + 1 + rr;
-        double s = Z[(int64_t)(j + 1) * ld + r];  // v[0] = 1
+        T s = Z[(int64_t)(j + 1) * ld + r];
         for (int cc = 1; cc < L; ++cc) s += Z[(int64_t)(j + 1 + cc) * ld + r] * x[j + 1 + cc];
         pv[rr] = tj * s;
       }
       __syncthreads();
-      double pp = 0.0;
-      for (int rr = tid; rr < L; rr += nt) pp += pv[rr] * (rr == 0 ? 1.0 : x[j + 1 + rr]);
-      const double kk = 0.5 * tj * block_sum_d(pp, red);
-      // w = p - kk v
-      for (int rr = tid; rr < L; rr += nt) pv[rr] -= kk * (rr == 0 ? 1.0 : x[j + 1 + rr]);
+      T pp = T(0);
+      for (int rr = tid; rr < L; rr += nt) pp += pv[rr] * (rr == 0 ? T(1) : x[j + 1 + rr]);
+      const T kk = T(0.5) * tj * block_sum_t(pp, red);
+      for (int rr = tid; rr < L; rr += nt) pv[rr] -= kk * (rr == 0 ? T(1) : x[j + 1 + rr]);
       __syncthreads();
-      // A' -= v w^T + w v^T
       for (int e = tid; e < L * L; e += nt) {
         const int cc = e / L, rr = e - cc * L;
-        const double vr = (rr == 0) ? 1.0 : x[j + 1 + rr];
-        const double vc = (cc == 0) ? 1.0 : x[j + 1 + cc];
+        const T vr = (rr == 0) ? T(1) : x[j + 1 + rr];
+        const T vc = (cc == 0) ? T(1) : x[j + 1 + cc];
         Z[(int64_t)(j + 1 + cc) * ld + (j + 1 + rr)] -= vr * pv[cc] + pv[rr] * vc;
       }
     }
@@ -125,107 +187,109 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_kernel(const EigItem *__restr
       eo[k - 2] = Z[(int64_t)(k - 2) * ld + (k - 1)];
     }
     dg[k - 1] = Z[(int64_t)(k - 1) * ld + (k - 1)];
-    eo[k - 1] = 0.0;
+    eo[k - 1] = T(0);
   }
   __syncthreads();
-  // 2. explicit H = H_0 ... H_{k-3} (each H_j acts on indices j+1..k-1).
-  //    Shift reflector tails one column right so that column j+1 holds v_j
-  //    below row j+1, then accumulate backwards on the trailing block.
+  // 2. explicit H = H_0 ... H_{k-3}; column j+1 carries reflector j
   for (int j = k - 3; j >= 0; --j) {
     for (int r = j + 2 + tid; r < k; r += nt) Z[(int64_t)(j + 1) * ld + r] = Z[(int64_t)j * ld + r];
     __syncthreads();
   }
   for (int e = tid; e < k; e += nt) {
-    Z[e] = (e == 0) ? 1.0 : 0.0;             // column 0
-    if (e > 0) Z[(int64_t)e * ld] = 0.0;     // row 0
+    Z[e] = (e == 0) ? T(1) : T(0);
+    if (e > 0) Z[(int64_t)e * ld] = T(0);
   }
   __syncthreads();
-  // column c = j+1 of H carries reflector j; rows/cols 1..k-1 form the block
   for (int c = k - 1; c >= 1; --c) {
-    const int j = c - 1;  // reflector index, exists for j <= k-3
-    const double tj = (j <= k - 3) ? tau[j] : 0.0;
-    const double *v = Z + (int64_t)c * ld;  // tail v[c+1..k-1], v[c] = 1 implicit
-    if (tj != 0.0) {
+    const int j = c - 1;
+    const T tj = (j <= k - 3) ? tau[j] : T(0);
+    const T *v = Z + (int64_t)c * ld;
+    if (tj != T(0)) {
       const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
       for (int cc = c + 1 + warp; cc < k; cc += nw) {
-        double *y = Z + (int64_t)cc * ld;
-        double s = 0.0;
+        T *y = Z + (int64_t)cc * ld;
+        T s = T(0);
         for (int r = c + 1 + lane; r < k; r += 32) s += v[r] * y[r];
-        s = warp_sum_d(s) + y[c];
+        s = warp_sum_t(s) + y[c];
         s *= tj;
         if (lane == 0) y[c] -= s;
         for (int r = c + 1 + lane; r < k; r += 32) y[r] -= s * v[r];
       }
     }
     __syncthreads();
-    double *x = Z + (int64_t)c * ld;
+    T *x = Z + (int64_t)c * ld;
     for (int r = 1 + tid; r < k; r += nt) {
-      if (r < c) x[r] = 0.0;
-      else if (r == c) x[r] = 1.0 - tj;
+      if (r < c) x[r] = T(0);
+      else if (r == c) x[r] = T(1) - tj;
       else x[r] = -tj * x[r];
     }
     __syncthreads();
   }
-  // 3. implicit QL on (dg, eo); eigenvectors = columns of Z
+  // 3. implicit QL; deflation when |e_m| <= eps ||T|| (normwise: the Gramians
+  //    need eigenvalues to within eps * lambda_max only)
   if (tid == 0) {
     sh.done = 0;
     sh.status = 0;
   }
-  int l = 0, iter = 0;  // thread 0's state
-  const double eps = 2.220446049250313e-16;
+  int l = 0, iter = 0;
+  T tol = T(0);
+  if (tid == 0) {
+    T tn = T(0);
+    for (int i = 0; i < k; ++i) {
+      T v = fabs(dg[i]) + fabs(eo[i]) + (i > 0 ? fabs(eo[i - 1]) : T(0));
+      tn = tn > v ? tn : v;
+    }
+    const T eps = (sizeof(T) == 8) ? T(2.220446049250313e-16) : T(1.1920929e-7);
+    tol = eps * tn;
+  }
   for (;;) {
     if (tid == 0) {
       sh.count = 0;
       while (l < k && sh.count == 0) {
         int mm;
-        for (mm = l; mm < k - 1; ++mm) {
-          const double dd = fabs(dg[mm]) + fabs(dg[mm + 1]);
-          if (fabs(eo[mm]) <= eps * dd) break;
-        }
+        for (mm = l; mm < k - 1; ++mm)
+          if (fabs(eo[mm]) <= tol) break;
         if (mm == l) {
           ++l;
           iter = 0;
           continue;
         }
-        if (++iter > 64) {  // no convergence: keep what we have
+        if (++iter > 64) {
           sh.status = 1;
           ++l;
           iter = 0;
           continue;
         }
-        double g = (dg[l + 1] - dg[l]) / (2.0 * eo[l]);
-        double r = hypot(g, 1.0);
+        // Wilkinson-type shift from the leading 2x2 block
+        T g = (dg[l + 1] - dg[l]) / (T(2) * eo[l]);
+        T r = sqrt(g * g + T(1));
         g = dg[mm] - dg[l] + eo[l] / (g + copysign(r, g));
-        double s = 1.0, c = 1.0, p = 0.0;
-        int i;
+        T s = T(1), c = T(1), p = T(0);
         bool deflated = false;
-        for (i = mm - 1; i >= l; --i) {
-          double f = s * eo[i], b = c * eo[i];
-          r = hypot(f, g);
+        for (int i = mm - 1; i >= l; --i) {
+          const T f = s * eo[i], b = c * eo[i];
+          givens(f, g, r, s, c);
           eo[i + 1] = r;
-          if (r == 0.0) {
+          if (r == T(0)) {
             dg[i + 1] -= p;
-            eo[mm] = 0.0;
+            eo[mm] = T(0);
             deflated = true;
             break;
           }
-          s = f / r;
-          c = g / r;
           g = dg[i + 1] - p;
-          r = (dg[i] - g) * s + 2.0 * c * b;
+          r = (dg[i] - g) * s + T(2) * c * b;
           p = s * r;
           dg[i + 1] = g + p;
           g = c * r - b;
-          // rotation on columns (i, i+1), logged in chain order
           rc[sh.count] = c;
           rs[sh.count] = s;
           sh.count++;
         }
-        sh.lo = mm - 1;  // first logged rotation acts on (mm-1, mm)
+        sh.lo = mm - 1;
         if (!deflated) {
           dg[l] -= p;
           eo[l] = g;
-          eo[mm] = 0.0;
+          eo[mm] = T(0);
         }
       }
       if (l >= k && sh.count == 0) sh.done = 1;
@@ -236,16 +300,16 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_kernel(const EigItem *__restr
     for (int row = tid; row < k; row += nt) {
       for (int q = 0; q < cnt; ++q) {
         const int i = i0 - q;
-        double *zi = Z + (int64_t)i * ld + row;
-        double *zi1 = Z + (int64_t)(i + 1) * ld + row;
-        const double f = *zi1;
+        T *zi = Z + (int64_t)i * ld + row;
+        T *zi1 = Z + (int64_t)(i + 1) * ld + row;
+        const T f = *zi1;
         *zi1 = rs[q] * (*zi) + rc[q] * f;
         *zi = rc[q] * (*zi) - rs[q] * f;
       }
     }
     __syncthreads();
   }
-  // 4. sort descending
+  // 4. sort descending, unscale
   if (tid == 0) {
     for (int i = 0; i < k; ++i) perm[i] = i;
     for (int i = 0; i < k; ++i) {
@@ -260,20 +324,154 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_kernel(const EigItem *__restr
   __syncthreads();
   for (int e = tid; e < k * k; e += nt) {
     int c = e / k, r = e - c * k;
-    it.V[e] = Z[(int64_t)perm[c] * ld + r];
+    it.V[e] = (double)Z[(int64_t)perm[c] * ld + r];
   }
-  for (int c = tid; c < k; c += nt) it.lam[c] = dg[perm[c]];
+  for (int c = tid; c < k; c += nt) it.lam[c] = (double)dg[perm[c]] * scale;
+}
+
+// ---- FP64 refinement ---------------------------------------------------------
+// C = op(A) * B for k x k column-major matrices in shared or global memory;
+// transA: C[i][j] = sum_l A[l][i] B[l][j].  Each thread computes 4x4 outputs.
+__device__ void small_gemm(const double *A, const double *B, double *C, int k, bool transA) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tiles = (k + 3) / 4;
+  for (int t = tid; t < tiles * tiles; t += nt) {
+    const int ti = (t % tiles) * 4, tj = (t / tiles) * 4;
+    double acc[4][4] = {};
+    for (int l = 0; l < k; ++l) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = ti + u, j = tj + u;
+        a[u] = (i < k) ? (transA ? A[(int64_t)i * k + l] : A[(int64_t)l * k + i]) : 0.0;
+        b[u] = (j < k) ? B[(int64_t)j * k + l] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (ti + u < k && tj + v < k) C[(int64_t)(tj + v) * k + ti + u] = acc[u][v];
+  }
+}
+
+__global__ void __launch_bounds__(EIG_THREADS) refine_kernel(const EigItem *__restrict__ items, double *scratch,
+                                                             int64_t scratch_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const EigItem it = items[blockIdx.x];
+  const int k = it.k, tid = threadIdx.x, nt = blockDim.x;
+  const int64_t kk = (int64_t)k * k;
+  double *buf = (k <= 64) ? reinterpret_cast<double *>(smem_raw) : scratch + (int64_t)blockIdx.x * scratch_stride;
+  double *A = buf, *X = buf + kk, *W1 = buf + 2 * kk, *W2 = buf + 3 * kk;
+  double *small = (k <= 64) ? buf + 4 * kk : reinterpret_cast<double *>(smem_raw);
+  double *lam = small;          // k
+  double *red = small + k;      // 32
+  int *perm = reinterpret_cast<int *>(red + 32);
+  double mx = 0.0;
+  for (int e = tid; e < kk; e += nt) mx = fmax(mx, fabs(it.G[e]));
+  mx = block_max_d(mx, red);
+  const double scale = (mx > 0.0) ? mx : 1.0, inv_scale = 1.0 / scale;
+  for (int e = tid; e < kk; e += nt) {
+    const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
+    A[e] = 0.5 * (it.G[(int64_t)c * k + r] + it.G[(int64_t)r * k + c]) * inv_scale;
+    X[e] = it.V[e];
+  }
+  __syncthreads();
+  small_gemm(A, X, W1, k, false);  // W1 = A X
+  __syncthreads();
+  small_gemm(X, W1, W2, k, true);  // W2 = S = X^T A X
+  __syncthreads();
+  small_gemm(X, X, W1, k, true);   // W1 = X^T X
+  __syncthreads();
+  for (int e = tid; e < kk; e += nt) {
+    const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
+    W1[e] = ((r == c) ? 1.0 : 0.0) - W1[e];  // R = I - X^T X
+  }
+  __syncthreads();
+  for (int i = tid; i < k; i += nt) lam[i] = W2[(int64_t)i * k + i] / (1.0 - W1[(int64_t)i * k + i]);
+  // cluster threshold from the sizes of the first-order residuals
+  double so = 0.0, ro = 0.0, lm = 0.0;
+  for (int e = tid; e < kk; e += nt) {
+    const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
+    if (r != c) so = fmax(so, fabs(W2[e]));
+    ro = fmax(ro, fabs(W1[e]));
+  }
+  __syncthreads();
+  for (int i = tid; i < k; i += nt) lm = fmax(lm, fabs(lam[i]));
+  so = block_max_d(so, red);
+  ro = block_max_d(ro, red);
+  lm = block_max_d(lm, red);
+  const double delta = 2.0 * (so + lm * ro) * (double)k;
+  for (int e = tid; e < kk; e += nt) {
+    const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
+    const double Rv = W1[e];
+    double Ev;
+    if (r == c) {
+      Ev = 0.5 * Rv;
+    } else {
+      const double gap = lam[c] - lam[r];
+      Ev = (fabs(gap) > delta) ? (W2[e] + lam[c] * Rv) / gap : 0.5 * Rv;
+    }
+    W2[e] = Ev;
+  }
+  __syncthreads();
+  small_gemm(X, W2, W1, k, false);  // W1 = X E
+  __syncthreads();
+  for (int e = tid; e < kk; e += nt) W1[e] += X[e];
+  if (tid == 0) {
+    for (int i = 0; i < k; ++i) perm[i] = i;
+    for (int i = 0; i < k; ++i) {
+      int best = i;
+      for (int j = i + 1; j < k; ++j)
+        if (lam[perm[j]] > lam[perm[best]]) best = j;
+      int t = perm[i];
+      perm[i] = perm[best];
+      perm[best] = t;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < kk; e += nt) {
+    const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
+    it.V[e] = W1[(int64_t)perm[c] * k + r];
+  }
+  for (int c = tid; c < k; c += nt) it.lam[c] = lam[perm[c]] * scale;
+}
+
+template <typename T>
+size_t ql_smem(int max_k) {
+  size_t tail = 32 * sizeof(double) + (size_t)(6 * max_k + 32) * sizeof(T) + (size_t)max_k * sizeof(int);
+  return (max_k <= kEigSmemK) ? (size_t)max_k * max_k * sizeof(T) + tail : tail;
 }
 
 }  // namespace
 
-cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s) {
+cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s, int mode) {
   if (n_items <= 0) return cudaSuccess;
-  size_t tail = (size_t)(6 * max_k + 32) * sizeof(double) + (size_t)max_k * sizeof(int);
-  size_t smem = (max_k <= kEigSmemK) ? (size_t)max_k * max_k * sizeof(double) + tail : tail;
-  cudaError_t e = cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e;
+  if (mode == 0) {  // FP64 QL
+    const size_t smem = ql_smem<double>(max_k);
+    e = cudaFuncSetAttribute(eig_ql_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    eig_ql_kernel<double><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * max_k);
+    count_launch();
+    return cudaGetLastError();
+  }
+  // FP32 QL, then one FP64 refinement step
+  const size_t smem = ql_smem<float>(max_k);
+  e = cudaFuncSetAttribute(eig_ql_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  eig_kernel<<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * max_k);
+  eig_ql_kernel<float><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * max_k);
+  count_launch();
+  const size_t rsm = (max_k <= 64) ? (size_t)(4 * max_k * max_k + max_k + 32) * sizeof(double) + max_k * sizeof(int)
+                                   : (size_t)(max_k + 32) * sizeof(double) + max_k * sizeof(int);
+  e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+  if (e != cudaSuccess) return e;
+  refine_kernel<<<n_items, EIG_THREADS, rsm, s>>>(d_items, scratch, 4 * (int64_t)max_k * max_k);
+  count_launch();
   return cudaGetLastError();
 }
 

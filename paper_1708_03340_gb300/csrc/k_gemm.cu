@@ -56,11 +56,15 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
   const int tx = tid & 15, ty = tid >> 4;  // thread owns rows 4tx..4tx+3, cols 4ty..4ty+3
   const bool a_mfast = (it.sam == 1);
   const bool b_nfast = (it.sbn == 1) && (it.sbk != 1);
-  T acc[4][4];
+  // FP32: each 16-wide k-tile is summed in registers, then added to the
+  // running sum with Kahan compensation (compensated summation of the long
+  // Gramian reductions); FP64 sums directly.
+  constexpr bool kComp = sizeof(T) == 4;
+  T acc[4][4], sum[4][4], cmp[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < 4; ++j) acc[i][j] = sum[i][j] = cmp[i][j] = T(0);
 
   for (int ko = ko_begin; ko < ko_end; ++ko) {
     const T *Ak = A + (int64_t)ko * it.sako;
@@ -100,8 +104,26 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
       }
+      if (kComp) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const T y = acc[i][j] - cmp[i][j];
+            const T t = sum[i][j] + y;
+            cmp[i][j] = (t - sum[i][j]) - y;
+            sum[i][j] = t;
+            acc[i][j] = T(0);
+          }
+      }
       __syncthreads();
     }
+  }
+  if (kComp) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = sum[i][j];
   }
   if (it.ksplit > 1) {
     T *P = static_cast<T *>(it.part) + ((int64_t)chunk * it.batch + b) * (int64_t)it.M * it.N;
@@ -147,12 +169,12 @@ __global__ void gemm_reduce_kernel(const GemmItem *__restrict__ items, const int
     int64_t r = e - (int64_t)b * per;
     int gn = (int)(r / M), gm = (int)(r - (int64_t)gn * M);
     const T *p = P + (int64_t)b * it.M * it.N + (int64_t)gn * it.M + gm;
-    T s = T(0);
-    for (int c = 0; c < it.ksplit; ++c) s += p[c * stride_chunk];
+    double s = 0.0;  // partial sums are added in FP64
+    for (int c = 0; c < it.ksplit; ++c) s += (double)p[c * stride_chunk];
     T *cp = static_cast<T *>(it.C) + (int64_t)b * it.scb + (int64_t)gm * it.scm + (int64_t)gn * it.scn;
-    T v = T(it.alpha) * s;
-    if (it.beta != 0.0) v += T(it.beta) * *cp;
-    *cp = v;
+    double v = it.alpha * s;
+    if (it.beta != 0.0) v += it.beta * (double)*cp;
+    *cp = T(v);
   }
 }
 
@@ -164,9 +186,11 @@ cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, c
   (void)h_items;
   if (n_items <= 0 || total_tiles <= 0) return cudaSuccess;
   gemm_kernel<T><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+  count_launch();
   if (any_split) {
     dim3 grid(64, n_items);
     gemm_reduce_kernel<T><<<grid, 256, 0, s>>>(d_items, d_ranks);
+    count_launch();
   }
   return cudaGetLastError();
 }

@@ -247,6 +247,7 @@ cudaError_t launch_copy(const CopyItem *d_items, int n_items, const int *d_ranks
   for (int base = 0; base < n_items; base += 65535) {
     int cnt = n_items - base < 65535 ? n_items - base : 65535;
     copy_kernel<<<dim3(16, cnt), 256, 0, s>>>(d_items + base, d_ranks);
+    count_launch();
   }
   return cudaGetLastError();
 }
@@ -256,6 +257,7 @@ cudaError_t launch_compact(const CompactItem *d_items, int n_items, const int *d
   for (int base = 0; base < n_items; base += 65535) {
     int cnt = n_items - base < 65535 ? n_items - base : 65535;
     compact_kernel<T><<<dim3(16, cnt), 256, 0, s>>>(d_items + base, d_ranks);
+    count_launch();
   }
   return cudaGetLastError();
 }
@@ -265,6 +267,7 @@ template cudaError_t launch_compact<float>(const CompactItem *, int, const int *
 cudaError_t launch_ranks(const RankItem *d_items, int n_items, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
   ranks_kernel<<<n_items, 256, 0, s>>>(d_items);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -278,6 +281,7 @@ cudaError_t launch_pack_add(const void *a, const void *c, void *out, const int64
     int cnt = n_nodes - base < 65535 ? n_nodes - base : 65535;
     pack_add_kernel<T><<<dim3(gx, cnt), 256, 0, s>>>(static_cast<const T *>(a), static_cast<const T *>(c),
                                                       static_cast<T *>(out), d_desc + 12 * (int64_t)base);
+    count_launch();
   }
   return cudaGetLastError();
 }
@@ -291,6 +295,7 @@ cudaError_t launch_eval_level(const void *x, const int64_t *node_off, const int 
   // grid.x = m (indices), grid.y = nodes of the level
   eval_level_kernel<T><<<dim3((unsigned)m, n_level), 64, 0, s>>>(static_cast<const T *>(x), node_off, ranks, tree, n, idx,
                                                                  row_off, rows_per, level_nodes, d, rows, out);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_eval_level<double>(const void *, const int64_t *, const int *, const int *, const int64_t *,
@@ -303,6 +308,7 @@ template cudaError_t launch_eval_level<float>(const void *, const int64_t *, con
 template <typename T>
 cudaError_t launch_sumsq(const void *x, int64_t count, double *out, cudaStream_t s) {
   sumsq_kernel<T><<<1, 1024, 0, s>>>(static_cast<const T *>(x), count, out);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_sumsq<double>(const void *, int64_t, double *, cudaStream_t);
@@ -314,6 +320,7 @@ cudaError_t launch_scale(void *x, int64_t count, double alpha, cudaStream_t s) {
   if (g > 1024) g = 1024;
   if (g < 1) g = 1;
   scale_kernel<T><<<g, 256, 0, s>>>(static_cast<T *>(x), count, alpha);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_scale<double>(void *, int64_t, double, cudaStream_t);

@@ -110,9 +110,177 @@ __global__ void __launch_bounds__(QR_THREADS) qr_block_kernel(const QrItem *__re
     for (int r = tid; r < m; r += blockDim.x) Q[(int64_t)c * it.ldq + r] = W[(int64_t)c * ld + r];
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident variant for n <= 16*CPW columns and m <= 32*ROWS rows.
+// Warp w owns columns w, w+16, ...; lane l owns rows l, l+32, ....  The
+// factorisation needs one barrier per column: the owner warp of column j
+// builds the reflector from its registers and publishes v_j in shared
+// memory, then every warp applies H_j to its own columns.  Q is formed from
+// the compact WY form H_0 ... H_{n-1} = I - V T V^T (T upper triangular, the
+// "forward, columnwise" accumulation):  Q = [I; 0] - V (T V_top^T).
+// ---------------------------------------------------------------------------
+constexpr int REG_ROWS = 8;   // rows per lane -> m <= 256
+constexpr int REG_WARPS = 16;
+
+template <typename T, int CPW>
+__global__ void __launch_bounds__(REG_WARPS * 32) qr_reg_kernel(const QrItem *__restrict__ items) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const QrItem it = items[blockIdx.x];
+  const int m = it.m, n = it.n;
+  constexpr int MR = 32 * REG_ROWS + 1;  // leading dimension of V (odd: no bank conflicts across columns)
+  T *V = reinterpret_cast<T *>(smem_raw);  // MR x n, column-major
+  T *TG = V + (int64_t)MR * n;             // n x n: Gram V^T V, then T (upper)
+  T *X = TG + (int64_t)n * n;              // n x n: T V_top^T
+  T *tau = X + (int64_t)n * n;             // n
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T a[CPW][REG_ROWS];
+  const T *A = static_cast<const T *>(it.A);
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp + REG_WARPS * q;
+#pragma unroll
+    for (int i = 0; i < REG_ROWS; ++i) {
+      const int r = lane + 32 * i;
+      a[q][i] = (c < n && r < m) ? A[(int64_t)c * it.lda + r] : T(0);
+    }
+  }
+  for (int j = 0; j < n; ++j) {
+    const int ow = j % REG_WARPS, qj = j / REG_WARPS;
+    if (warp == ow) {
+      T alpha = T(0), s2 = T(0);
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) {
+        if (q != qj) continue;
+#pragma unroll
+        for (int i = 0; i < REG_ROWS; ++i) {
+          const int r = lane + 32 * i;
+          if (r == j) alpha = a[q][i];
+          if (r > j) s2 += a[q][i] * a[q][i];
+        }
+      }
+      s2 = warp_sum(s2);
+      alpha = warp_sum(alpha);  // only one lane holds a nonzero contribution
+      T tj = T(0), beta = alpha, scale = T(0);
+      if (s2 != T(0)) {
+        const T nrm = sqrt(alpha * alpha + s2);
+        beta = (alpha <= T(0)) ? nrm : -nrm;
+        tj = (beta - alpha) / beta;
+        scale = T(1) / (alpha - beta);
+      }
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) {
+        if (q != qj) continue;
+#pragma unroll
+        for (int i = 0; i < REG_ROWS; ++i) {
+          const int r = lane + 32 * i;
+          const T v = (r < j) ? T(0) : (r == j ? T(1) : a[q][i] * scale);
+          V[(int64_t)j * MR + r] = v;
+          if (r == j) a[q][i] = beta;
+          else if (r > j) a[q][i] = T(0);
+        }
+      }
+      if (lane == 0) tau[j] = tj;
+    }
+    __syncthreads();
+    const T tj = tau[j];
+    if (tj != T(0)) {
+      T v[REG_ROWS];
+#pragma unroll
+      for (int i = 0; i < REG_ROWS; ++i) v[i] = V[(int64_t)j * MR + lane + 32 * i];
+#pragma unroll
+      for (int q = 0; q < CPW; ++q) {
+        const int c = warp + REG_WARPS * q;
+        if (c <= j || c >= n) continue;
+        T s = T(0);
+#pragma unroll
+        for (int i = 0; i < REG_ROWS; ++i) s += v[i] * a[q][i];
+        s = warp_sum(s) * tj;
+#pragma unroll
+        for (int i = 0; i < REG_ROWS; ++i) a[q][i] -= s * v[i];
+      }
+    }
+  }
+  // R (n x n upper triangular) from the registers
+  T *R = static_cast<T *>(it.R);
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp + REG_WARPS * q;
+    if (c >= n) continue;
+#pragma unroll
+    for (int i = 0; i < REG_ROWS; ++i) {
+      const int r = lane + 32 * i;
+      if (r < n) R[(int64_t)c * it.ldr + r] = (r <= c) ? a[q][i] : T(0);
+    }
+  }
+  // Gram G = V^T V (strictly upper part is what the T recurrence needs)
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n * n; e += nt) {
+    const int jj = e / n, ii = e - jj * n;
+    T g = T(0);
+    if (ii < jj) {
+      const T *vi = V + (int64_t)ii * MR, *vj = V + (int64_t)jj * MR;
+      for (int r = jj; r < m; ++r) g += vi[r] * vj[r];  // v_jj vanishes above row jj
+    }
+    TG[(int64_t)jj * n + ii] = g;
+  }
+  __syncthreads();
+  // T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j];  T[j, j] = tau_j   (column by column)
+  for (int jj = 0; jj < n; ++jj) {
+    T val = T(0);
+    if (tid < jj) {
+      for (int kk = tid; kk < jj; ++kk) val += TG[(int64_t)kk * n + tid] * TG[(int64_t)jj * n + kk];
+      val *= -tau[jj];
+    }
+    __syncthreads();
+    if (tid < jj) TG[(int64_t)jj * n + tid] = val;
+    if (tid == jj) TG[(int64_t)jj * n + jj] = tau[jj];
+    __syncthreads();
+  }
+  // X = T V_top^T:  X[k, c] = sum_{l=k..c} T[k, l] V[c, l]
+  for (int e = tid; e < n * n; e += nt) {
+    const int c = e / n, kk = e - c * n;
+    T x = T(0);
+    for (int l = kk; l <= c; ++l) x += TG[(int64_t)l * n + kk] * V[(int64_t)l * MR + c];
+    X[(int64_t)c * n + kk] = x;
+  }
+  __syncthreads();
+  // Q = [I; 0] - V X, written straight from the thread's (row, column) pairs
+  T *Q = static_cast<T *>(it.Q);
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    const int c = warp + REG_WARPS * q;
+    if (c >= n) continue;
+    T acc[REG_ROWS];
+#pragma unroll
+    for (int i = 0; i < REG_ROWS; ++i) acc[i] = (lane + 32 * i == c) ? T(1) : T(0);
+    for (int kk = 0; kk < n; ++kk) {
+      const T x = X[(int64_t)c * n + kk];
+      if (x == T(0)) continue;
+#pragma unroll
+      for (int i = 0; i < REG_ROWS; ++i) acc[i] -= V[(int64_t)kk * MR + lane + 32 * i] * x;
+    }
+#pragma unroll
+    for (int i = 0; i < REG_ROWS; ++i) {
+      const int r = lane + 32 * i;
+      if (r < m) Q[(int64_t)c * it.ldq + r] = acc[i];
+    }
+  }
+}
+
+template <typename T, int CPW>
+cudaError_t launch_qr_reg(const QrItem *d_items, int n_items, int max_n, cudaStream_t s) {
+  const size_t smem = ((size_t)(32 * REG_ROWS + 1) * max_n + 2 * (size_t)max_n * max_n + max_n) * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(qr_reg_kernel<T, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  qr_reg_kernel<T, CPW><<<n_items, REG_WARPS * 32, smem, s>>>(d_items);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int qr_max_rows(int n, int elem_bytes) {
+  if (n <= 16 * 4) return 32 * REG_ROWS;  // register-resident kernel
   int64_t avail = kSmemLimit - kSmemReserve - (int64_t)(n + 32) * elem_bytes;
   return (int)(avail / ((int64_t)n * elem_bytes));
 }
@@ -120,11 +288,17 @@ int qr_max_rows(int n, int elem_bytes) {
 template <typename T>
 cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
+  if (max_n <= 64 && max_m <= 32 * REG_ROWS) {
+    if (max_n <= 16) return launch_qr_reg<T, 1>(d_items, n_items, max_n, s);
+    if (max_n <= 32) return launch_qr_reg<T, 2>(d_items, n_items, max_n, s);
+    return launch_qr_reg<T, 4>(d_items, n_items, max_n, s);
+  }
   size_t smem = ((size_t)max_m * max_n + max_n + 32) * sizeof(T);
   if (smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(qr_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   qr_block_kernel<T><<<n_items, QR_THREADS, smem, s>>>(d_items);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -32,7 +32,10 @@ EXPORTS = [
     "ht_tensor_upload", "ht_tensor_download", "ht_tensor_node_ptr", "ht_scale",
     "ht_add", "ht_add_into", "ht_orthogonalize", "ht_gramians", "ht_truncate",
     "ht_truncate_batch", "ht_norm", "ht_eval_entries", "ht_last_error",
+    "ht_profile_set", "ht_profile_read", "ht_launch_count",
 ]
+HT_K_GEMM, HT_K_QR, HT_K_EIG, HT_K_COPY, HT_K_COMPACT, HT_K_RANKS, HT_K_ADD, HT_K_EVAL, HT_K_MISC = range(9)
+KERNEL_KINDS = ["gemm", "qr", "eig", "copy", "compact", "ranks", "add", "eval", "misc"]
 
 
 class HTError(RuntimeError):
@@ -105,6 +108,9 @@ def load(build_if_missing: bool = True):
             "ht_norm": ([vp, f64p], ctypes.c_int),
             "ht_eval_entries": ([vp, i64p, ctypes.c_int64, f64p], ctypes.c_int),
             "ht_last_error": ([], ctypes.c_char_p),
+            "ht_profile_set": ([ctypes.c_uint], ctypes.c_int),
+            "ht_profile_read": ([ctypes.c_int, i64p, f64p, f64p, ctypes.c_int], ctypes.c_int),
+            "ht_launch_count": ([i64p], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -265,6 +271,23 @@ def ht_eval_entries(x, idx) -> np.ndarray:
     _check(load().ht_eval_entries(x, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), idx.shape[0],
                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def ht_profile_set(mask: int):
+    _check(load().ht_profile_set(int(mask)))
+
+
+def ht_profile_read(kind: int, reset: bool = True):
+    """(launches, device ms, algorithmic flops) recorded for one kernel family."""
+    n, ms, fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _check(load().ht_profile_read(int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl), 1 if reset else 0))
+    return n.value, ms.value, fl.value
+
+
+def ht_launch_count() -> int:
+    n = ctypes.c_int64()
+    _check(load().ht_launch_count(ctypes.byref(n)))
+    return n.value
 
 
 # ---------------------------------------------------------------------------

@@ -13,7 +13,9 @@ root stores B_D (k_t1 x k_t2) row-major.  ``ranks`` has one entry per node,
 the root's entry is 1.
 
 Workload recipes (per node, "scaled along each mode j by sigma_j" means
-B[a,b,c] = g_abc * sigma_a * sigma_b * sigma_c with 1-based a, b, c):
+B[a,b,c] = g_abc * sigma_a * sigma_b * sigma_c with 1-based a, b, c; every
+transfer tensor is then divided by its Frobenius norm, a scalar factor of the
+whole tensor that keeps ||X|| inside FP32's exponent range):
 
 * ``small``      d=8, n=32, k=8, Gaussian U, sigma_j = 2^-j  (two seeds added)
 * ``brute``      d=4, n=8, k=4, as ``small``
@@ -140,10 +142,13 @@ def random_ht(d: int, n, k, seed: int, leaf: str = "gauss", sigma=None):
         else:
             if t == 0:
                 g = normal(key, int(k) * int(k)).reshape(int(k), int(k))
-                parts.append((g * w[:, None] * w[None, :]).ravel())
+                b = g * w[:, None] * w[None, :]
             else:
                 g = normal(key, int(k) ** 3).reshape(int(k), int(k), int(k))
-                parts.append((g * w[:, None, None] * w[None, :, None] * w[None, None, :]).ravel())
+                b = g * w[:, None, None] * w[None, :, None] * w[None, None, :]
+            # unit Frobenius norm: only a scalar factor of the whole tensor, which keeps
+            # ||X|| within FP32's exponent range for deep trees with decaying weights
+            parts.append((b / np.linalg.norm(b)).ravel())
     return n, ranks, np.concatenate(parts)
 
 

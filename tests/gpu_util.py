@@ -7,6 +7,25 @@ from paper_1708_03340_gb300 import htgb
 from paper_1708_03340_gb300 import inputs as I
 
 
+U32 = 2.0 ** -24
+
+
+def fp32_tol(d):
+    """Tolerance of the FP32-storage path: 1e-6, widened for deep trees to
+    4 sqrt(2d-1) u_32 because every one of the 2d-1 nodes rounds its
+    orthogonalized factors to FP32 independently (errors add like a random
+    walk over the nodes)."""
+    return max(1e-6, 4.0 * np.sqrt(2 * d - 1) * U32)
+
+
+def as_stored(blob, dtype):
+    """The tensor the GPU path actually holds: F32 tensors store FP32-rounded
+    inputs, so the oracle is run on the same rounded values (input rounding is
+    not an error of the path)."""
+    b = np.asarray(blob, dtype=np.float64)
+    return b.astype(np.float32).astype(np.float64) if dtype == htgb.HT_F32 else b
+
+
 def gpu_sum(d, n, a, c, dtype):
     tree = htgb.HTTree(d)
     A = htgb.HTTensor.from_blob(tree, n, a[1], a[2], dtype)
@@ -41,3 +60,38 @@ def check_sigma(sg_gpu, sg_ref, tol, floor=0.0):
         worst = max(worst, err)
         assert err <= tol, (t, err)
     return worst
+
+
+def rank_noise_ok(sig_ref, r_gpu, r_ref, tail2, tol):
+    """A rank decision differing from the oracle's is acceptable only if the
+    oracle's discarded tails at every cut between the two lie within tol of
+    the per-node threshold tail2 (the decision is then below the arithmetic's
+    resolution)."""
+    lam = np.maximum(np.asarray(sig_ref, dtype=np.float64) ** 2, 0.0)
+    tails = [float(np.sum(lam[r:])) for r in range(len(lam) + 1)]
+    lo, hi = min(r_gpu, r_ref), max(r_gpu, r_ref)
+    # keeping lo must (nearly) violate, keeping hi must (nearly) satisfy the threshold
+    return tails[hi] <= tail2 + tol and tails[lo] >= tail2 - tol
+
+
+def rank_diff_energy(sig_ref, r_gpu, r_ref):
+    """sqrt of the oracle's sigma^2 between two cuts of one node."""
+    lo, hi = min(r_gpu, r_ref), max(r_gpu, r_ref)
+    return float(np.sqrt(np.sum(np.asarray(sig_ref[lo:hi], dtype=np.float64) ** 2)))
+
+
+def check_ranks(ranks_gpu, ref, tol_rel, eps_mode):
+    """Compare ranks; returns (differing nodes, energy bound of their effect)."""
+    differ = [t for t in range(1, len(ranks_gpu)) if int(ranks_gpu[t]) != int(ref["k"][t])]
+    if not eps_mode:
+        assert not differ, (list(ranks_gpu), list(ref["k"]))
+    e2 = 0.0
+    for t in differ:
+        s = ref["sigma"][t]
+        lam_max = float(s[0]) ** 2 if len(s) else 0.0
+        assert rank_noise_ok(s, int(ranks_gpu[t]), int(ref["k"][t]), ref["tail2"], len(s) * tol_rel * lam_max), \
+            (t, int(ranks_gpu[t]), int(ref["k"][t]))
+        e2 += rank_diff_energy(s, int(ranks_gpu[t]), int(ref["k"][t]))
+    # projections that differ at several nodes: the truncated tensors differ by at
+    # most the sum (telescoping over the nodes) of the energies between the cuts
+    return differ, float(e2)
