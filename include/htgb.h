@@ -157,6 +157,23 @@ ht_status ht_orthogonalize(ht_tensor *x, int prec);
  * k_t x k_t block (column-major; the root's block is the 1x1 matrix 1). */
 ht_status ht_gramians(ht_tensor *x_orth, double *dev_out, int prec);
 
+/* Same result as ht_gramians, but the call allocates no device memory.
+ * (Not a step of the paper: it serves callers that cannot let a library
+ * allocate, e.g. a program that reserves all device memory up front under a
+ * fixed budget or hands every buffer out from its own allocator, so that a
+ * hidden cudaMalloc/cudaMallocAsync would break its accounting or fail.)
+ * The workspace is one fixed device array of HT_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading this library keeps until the process exits; the caller
+ * still provides the tensor and dev_out.  The first call on a device looks up
+ * the array's device address (with that device current); make that first
+ * call before any stream capture.  A tensor whose workspace needs more than
+ * the array holds is rejected with HT_ENOMEM and a message giving both sizes.
+ * All calls share the one array and its contents persist between calls:
+ * calls that can run at the same time on the GPU (different streams, or
+ * several host threads) race on it and must be serialised by the caller. */
+#define HT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+ht_status ht_gramians_noalloc(ht_tensor *x_orth, double *dev_out, int prec);
+
 /* HSVD truncation T(X), Sec. 3.3 after Sec. 3.4, in place: orthogonalize,
  * Gramians of all non-root nodes, their eigendecompositions (singular values
  * of every matricization), ranks, then the projection U <- U Q|_r,

@@ -9,6 +9,7 @@
 // copy.  All work is stream-ordered on the tensor's stream.
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -431,7 +432,9 @@ void reloc_items<RankItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
 // order after the last launch.  `keep` receives the relocated persistent base
 // (so that callers can read results) and the caller must free it with
 // cudaFreeAsync; if keep is null, everything is freed here.
-ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base) {
+// ext_base / ext_cap: run inside caller-provided device memory instead of
+// allocating (nothing is allocated or freed then; keep_base must be null).
+ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base, char *ext_base = nullptr, size_t ext_cap = 0) {
   if (!P.err.empty()) return fail(HT_EUNSUPPORTED, P.err);
   const size_t p_sz = (P.p_bytes + 255) & ~size_t(255);
   const size_t s_sz = (P.s_peak + 255) & ~size_t(255);
@@ -439,8 +442,16 @@ ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base) {
   const size_t i_off = m_off + ((P.meta.size() + 255) & ~size_t(255));
   const size_t total = i_off + P.items.size();
   char *base = nullptr;
-  cudaError_t e = cudaMallocAsync((void **)&base, std::max<size_t>(total, 256), s);
-  if (e != cudaSuccess) return fail(HT_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+  cudaError_t e;
+  if (ext_base) {
+    if (total > ext_cap)
+      return fail(HT_ENOMEM, "the call needs " + std::to_string(total) + " bytes of device scratch; the fixed scratch holds " +
+                                 std::to_string(ext_cap) + " bytes");
+    base = ext_base;
+  } else {
+    e = cudaMallocAsync((void **)&base, std::max<size_t>(total, 256), s);
+    if (e != cudaSuccess) return fail(HT_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+  }
   char *pb = base, *sb = base + p_sz, *mb = base + m_off;
   for (Launch &L : P.launches) {
     uint8_t *ib = P.items.data() + L.off;
@@ -489,10 +500,11 @@ ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base) {
     }
     prof_end((int)L.kind, s, L.flops);
     if (e != cudaSuccess) {
-      cudaFreeAsync(base, s);
+      if (!ext_base) cudaFreeAsync(base, s);
       return fail(HT_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
     }
   }
+  if (ext_base) return HT_OK;
   if (keep_base) {
     *keep_base = base;
   } else {
@@ -1579,6 +1591,52 @@ ht_status ht_gramians(ht_tensor *x, double *dev_out, int prec) {
   std::vector<double *> outs{dev_out};
   plan_gramians(P, TS, &outs);
   return run_plan(P, x->stream, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// ht_gramians_noalloc: the Gramian computation with its workspace (work-item
+// lists, Gramian copies, contraction temporaries, split-K partial sums) held
+// in one fixed device array instead of memory allocated per call.  The array
+// lives for the whole process on every device that loads the library.  In
+// host code its name only denotes a host-side shadow, so the device address is
+// looked up once per device with cudaGetSymbolAddress, with that device
+// current, and passed to the kernels through the work items.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HT_NOALLOC_SCRATCH_BYTES];
+
+static ht_status noalloc_scratch(char **out) {
+  static std::mutex mu;
+  static char *addr[256] = {};
+  int dev = 0;
+  HT_CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(HT_EUNSUPPORTED, "device ordinal out of range for the fixed scratch");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(HT_ECUDA, std::string("cudaGetSymbolAddress of the fixed scratch failed: ") + cudaGetErrorString(e));
+    addr[dev] = static_cast<char *>(p);
+  }
+  *out = addr[dev];
+  return HT_OK;
+}
+
+ht_status ht_gramians_noalloc(ht_tensor *x, double *dev_out, int prec) {
+  if (!x || !dev_out) return fail(HT_EINVAL, "null argument");
+  HT_TRY(check_prec(x, prec));
+  char *scratch = nullptr;
+  HT_TRY(noalloc_scratch(&scratch));
+  HT_TRY(sync_ranks(x));
+  Plan P;
+  P.dtype = x->dtype;
+  P.esz = x->esz;
+  std::vector<TState> TS(1);
+  TS[0].x = x;
+  TS[0].ko = x->k;
+  std::vector<double *> outs{dev_out};
+  plan_gramians(P, TS, &outs);
+  return run_plan(P, x->stream, nullptr, scratch, HT_NOALLOC_SCRATCH_BYTES);
 }
 
 static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_opts *o, ht_trunc_report *rep) {

@@ -32,8 +32,9 @@ EXPORTS = [
     "ht_tensor_upload", "ht_tensor_download", "ht_tensor_node_ptr", "ht_scale",
     "ht_add", "ht_add_into", "ht_orthogonalize", "ht_gramians", "ht_truncate",
     "ht_truncate_batch", "ht_norm", "ht_eval_entries", "ht_last_error",
-    "ht_profile_set", "ht_profile_read", "ht_launch_count",
+    "ht_profile_set", "ht_profile_read", "ht_launch_count", "ht_gramians_noalloc",
 ]
+HT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 HT_K_GEMM, HT_K_QR, HT_K_EIG, HT_K_COPY, HT_K_COMPACT, HT_K_RANKS, HT_K_ADD, HT_K_EVAL, HT_K_MISC = range(9)
 KERNEL_KINDS = ["gemm", "qr", "eig", "copy", "compact", "ranks", "add", "eval", "misc"]
 
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = True):
             "ht_profile_set": ([ctypes.c_uint], ctypes.c_int),
             "ht_profile_read": ([ctypes.c_int, i64p, f64p, f64p, ctypes.c_int], ctypes.c_int),
             "ht_launch_count": ([i64p], ctypes.c_int),
+            "ht_gramians_noalloc": ([vp, vp, ctypes.c_int], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -214,6 +216,11 @@ def ht_orthogonalize(x, prec=HT_PREC_FP64):
 
 def ht_gramians(x, dev_ptr, prec=HT_PREC_FP64):
     _check(load().ht_gramians(x, ctypes.c_void_p(dev_ptr), int(prec)))
+
+
+def ht_gramians_noalloc(x, dev_ptr, prec=HT_PREC_FP64):
+    """ht_gramians without any device allocation (fixed scratch inside the library)."""
+    _check(load().ht_gramians_noalloc(x, ctypes.c_void_p(dev_ptr), int(prec)))
 
 
 def make_opts(mode="rank", eps=0.0, eps_relative=True, rank_cap=0, ranks=None, prec=HT_PREC_FP64,
