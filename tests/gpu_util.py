@@ -11,11 +11,19 @@ U32 = 2.0 ** -24
 
 
 def fp32_tol(d):
-    """Tolerance of the FP32-storage path: 1e-6, widened for deep trees to
-    4 sqrt(2d-1) u_32 because every one of the 2d-1 nodes rounds its
-    orthogonalized factors to FP32 independently (errors add like a random
-    walk over the nodes)."""
+    """Tolerance of the FP32-storage path on ||X|| and on the truncated tensor:
+    1e-6, widened for deep trees to 4 sqrt(2d-1) u_32 because every one of the
+    2d-1 nodes rounds its orthogonalized factors to FP32 independently (the
+    errors add like a random walk over the nodes)."""
     return max(1e-6, 4.0 * np.sqrt(2 * d - 1) * U32)
+
+
+def fp32_tol_sigma(d):
+    """Tolerance of the FP32-storage path on sigma^2 (normwise per node): every
+    Gramian carries twice the relative error of ||X||^2's scale, plus one FP32
+    contraction error per level of the top-down recursion (depth = ceil(log2 d))."""
+    depth = int(np.ceil(np.log2(d)))
+    return max(1e-6, 2.0 * fp32_tol(d) + 4.0 * depth * U32)
 
 
 def as_stored(blob, dtype):

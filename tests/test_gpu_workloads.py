@@ -18,7 +18,7 @@ import pytest
 from oracle import oracle as O
 from paper_1708_03340_gb300 import htgb
 from paper_1708_03340_gb300 import inputs as I
-from tests.gpu_util import as_stored, check_ranks, check_sigma, fp32_tol, gpu_sum, split_sigma
+from tests.gpu_util import as_stored, check_ranks, check_sigma, fp32_tol, fp32_tol_sigma, gpu_sum, split_sigma
 
 pytestmark = pytest.mark.gpu
 
@@ -62,14 +62,15 @@ def test_single_workload(single):
     print(f"dtype={dtype} tol={tol:.2e} norm rel err={norm_err:.2e}")
     assert norm_err <= tol
     sg = split_sigma(rep["korth"], rep["sigma"])
-    worst = check_sigma(sg, ref["sigma"], tol, floor=1e-5)
+    tol_sig = 1e-12 if dtype == htgb.HT_F64 else fp32_tol_sigma(D)
+    worst = check_sigma(sg, ref["sigma"], tol_sig, floor=1e-5)
     kt = X.ranks()
     xt = X.download().astype(np.float64)
     differ, energy = check_ranks(kt, ref, tol, eps_mode=True)
     dist = diff_norm(n, kt, xt, ref["k"], ref["x"]) / nrm
     err_gpu = diff_norm(n, k, x, kt, xt) / nrm
     err_ref = diff_norm(n, k, x, ref["k"], ref["x"]) / nrm
-    print(f"dtype={dtype} sigma worst={worst:.2e} rank_diffs={len(differ)} energy={energy / nrm:.2e} "
+    print(f"dtype={dtype} sigma worst={worst:.2e} (tol {tol_sig:.2e}) rank_diffs={len(differ)} energy={energy / nrm:.2e} "
           f"dist={dist:.2e} err_gpu={err_gpu:.3e} err_ref={err_ref:.3e}")
     # the HSVD error bound: ||X - T(X)|| <= sqrt(sum of the discarded sigma^2)
     assert err_ref <= np.sqrt(ref["discarded_sq"]) / nrm * (1 + 1e-9)
