@@ -69,10 +69,13 @@ typedef enum { HT_SCHED_LEVEL = 0, HT_SCHED_NODE = 1 } ht_schedule;
  * to prescribed accuracy"; Sec. 5: absolute eps with a rank cap).
  *  mode = HT_TRUNC_RANK: r_t = min(ranks[t] (or rank_cap if ranks == NULL),
  *         rank_cap if > 0, rank available after orthogonalization).
- *  mode = HT_TRUNC_EPS:  r_t = smallest r >= 1 with sum_{i>r} sigma_{t,i}^2 <=
- *         eps_abs^2 / (2d-3), eps_abs = eps * ||X|| if eps_relative, then
- *         capped as above.  The two sons of the root have the same singular
- *         values and share one rank (decided on the first son).
+ *  mode = HT_TRUNC_EPS:  r_t = smallest r >= 1 with sum_{i>r} (sigma_{t,i}^2 + nu_t)
+ *         <= eps_abs^2 / (2d-3), eps_abs = eps * ||X|| if eps_relative, then
+ *         capped as above.  nu_t = 4 sqrt(2d-1) u sigma_{t,1}^2 is the noise
+ *         floor of a computed eigenvalue (u = 2^-53 for HT_PREC_FP64, 2^-24 for
+ *         HT_PREC_FP32): an eps below what the arithmetic resolves keeps rank.
+ *         The two sons of the root have the same singular values and share
+ *         one rank (decided on the first son).
  *  prec: HT_PREC_FP64 needs an F64 tensor, HT_PREC_FP32 an F32 tensor. */
 typedef struct {
   int mode;

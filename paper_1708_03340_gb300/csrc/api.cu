@@ -1081,6 +1081,9 @@ void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, in
     r.eps_rel = o.eps_relative;
     r.cap = o.rank_cap;
     r.eps = o.eps;
+    // noise floor of a computed Gramian eigenvalue: 4 sqrt(2d-1) u lambda_max,
+    // u the unit roundoff of the path (every node's rounding perturbs X independently)
+    r.noise = 4.0 * std::sqrt(2.0 * T.d - 1.0) * (P.dtype == HT_F64 ? 0x1p-53 : 0x1p-24);
     P.rank(r, S.node_base);
   }
 }

@@ -95,6 +95,7 @@ struct RankItem {
   int nn, t1, t2, d;
   int mode, eps_rel, cap;
   double eps;
+  double noise;  // per-eigenvalue noise floor, relative to the node's largest eigenvalue
 };
 
 // ---------------------------------------------------------------------------

@@ -95,10 +95,14 @@ __global__ void ranks_kernel(const RankItem *__restrict__ items) {
     const double *lam = it.lam + it.lam_off[t];
     int r;
     if (it.mode == 1) {
+      // a dropped eigenvalue is charged its computed value plus the noise
+      // floor of the arithmetic that produced it, so that an eigenvalue at
+      // rounding level is never taken for a negligible one
+      const double nu = it.noise * (lam[0] > 0.0 ? lam[0] : 0.0);
       double tail = 0.0;
       r = avail;
       for (int i = avail - 1; i >= 1; --i) {
-        const double l = lam[i] > 0.0 ? lam[i] : 0.0;
+        const double l = (lam[i] > 0.0 ? lam[i] : 0.0) + nu;
         if (tail + l <= tail2) {
           tail += l;
           r = i;

@@ -70,16 +70,11 @@ def check_sigma(sg_gpu, sg_ref, tol, floor=0.0):
     return worst
 
 
-def rank_noise_ok(sig_ref, r_gpu, r_ref, tail2, tol):
-    """A rank decision differing from the oracle's is acceptable only if the
-    oracle's discarded tails at every cut between the two lie within tol of
-    the per-node threshold tail2 (the decision is then below the arithmetic's
-    resolution)."""
-    lam = np.maximum(np.asarray(sig_ref, dtype=np.float64) ** 2, 0.0)
-    tails = [float(np.sum(lam[r:])) for r in range(len(lam) + 1)]
-    lo, hi = min(r_gpu, r_ref), max(r_gpu, r_ref)
-    # keeping lo must (nearly) violate, keeping hi must (nearly) satisfy the threshold
-    return tails[hi] <= tail2 + tol and tails[lo] >= tail2 - tol
+def noise_floor(d, dtype):
+    """Per-eigenvalue noise floor (relative to the node's largest eigenvalue)
+    that the library charges to every dropped eigenvalue in eps mode."""
+    u = 2.0 ** -53 if dtype == htgb.HT_F64 else 2.0 ** -24
+    return 4.0 * np.sqrt(2 * d - 1) * u
 
 
 def rank_diff_energy(sig_ref, r_gpu, r_ref):
@@ -88,18 +83,28 @@ def rank_diff_energy(sig_ref, r_gpu, r_ref):
     return float(np.sqrt(np.sum(np.asarray(sig_ref[lo:hi], dtype=np.float64) ** 2)))
 
 
-def check_ranks(ranks_gpu, ref, tol_rel, eps_mode):
-    """Compare ranks; returns (differing nodes, energy bound of their effect)."""
+def check_ranks(ranks_gpu, ref, tol_rel, eps_mode, d=None, dtype=None):
+    """Compare ranks with the oracle's.
+
+    Rank mode: equal.  Eps mode: the library charges each dropped eigenvalue
+    its noise floor nu, so it never cuts below the oracle (r_gpu >= r_oracle),
+    and where it keeps more, dropping one more eigenvalue must fail the
+    threshold within the noise floor plus the path's eigenvalue tolerance.
+    Returns (differing nodes, bound on the effect on the truncated tensor:
+    the sum over those nodes of the oracle's energy between the two cuts)."""
     differ = [t for t in range(1, len(ranks_gpu)) if int(ranks_gpu[t]) != int(ref["k"][t])]
     if not eps_mode:
         assert not differ, (list(ranks_gpu), list(ref["k"]))
-    e2 = 0.0
+        return differ, 0.0
+    nu = noise_floor(d, dtype)
+    energy = 0.0
     for t in differ:
-        s = ref["sigma"][t]
-        lam_max = float(s[0]) ** 2 if len(s) else 0.0
-        assert rank_noise_ok(s, int(ranks_gpu[t]), int(ref["k"][t]), ref["tail2"], len(s) * tol_rel * lam_max), \
-            (t, int(ranks_gpu[t]), int(ref["k"][t]))
-        e2 += rank_diff_energy(s, int(ranks_gpu[t]), int(ref["k"][t]))
-    # projections that differ at several nodes: the truncated tensors differ by at
-    # most the sum (telescoping over the nodes) of the energies between the cuts
-    return differ, float(e2)
+        s = np.asarray(ref["sigma"][t], dtype=np.float64)
+        rg, rr = int(ranks_gpu[t]), int(ref["k"][t])
+        lam = np.maximum(s, 0.0) ** 2
+        lam_max = lam[0] if len(lam) else 0.0
+        assert rg >= rr, (t, rg, rr)
+        tail_more = float(np.sum(lam[rg - 1:]))  # the oracle's tail if one more were dropped
+        assert tail_more + (len(lam) - rg + 1) * (nu + tol_rel) * lam_max >= ref["tail2"], (t, rg, rr)
+        energy += rank_diff_energy(s, rg, rr)
+    return differ, float(energy)

