@@ -115,12 +115,44 @@ __global__ void __launch_bounds__(QR_THREADS) qr_block_kernel(const QrItem *__re
 // Warp w owns columns w, w+16, ...; lane l owns rows l, l+32, ....  The
 // factorisation needs one barrier per column: the owner warp of column j
 // builds the reflector from its registers and publishes v_j in shared
-// memory, then every warp applies H_j to its own columns.  Q is formed from
-// the compact WY form H_0 ... H_{n-1} = I - V T V^T (T upper triangular, the
-// "forward, columnwise" accumulation):  Q = [I; 0] - V (T V_top^T).
+// memory, then every warp applies H_j to its own columns (the dot products of
+// its active columns reduced together).  Q = H_0 ... H_{n-1} [I; 0] is then
+// accumulated backwards by every warp on its own columns, from the stored
+// reflectors, without further barriers.
 // ---------------------------------------------------------------------------
 constexpr int REG_ROWS = 8;   // rows per lane -> m <= 256
 constexpr int REG_WARPS = 16;
+
+// a[q] <- (I - tau v v^T) a[q] for the owned columns q >= q0 (warp-uniform),
+// v read from shared memory (one column of V, rows lane + 32 i); the dot
+// products of the active columns are reduced together.
+template <typename T, int CPW>
+__device__ __forceinline__ void qr_apply_reflector(T (&a)[CPW][REG_ROWS], const T *vcol, T tj, int q0, int lane) {
+  T v[REG_ROWS];
+#pragma unroll
+  for (int i = 0; i < REG_ROWS; ++i) v[i] = vcol[lane + 32 * i];
+  T sd[CPW];
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    sd[q] = T(0);
+    if (q >= q0) {
+#pragma unroll
+      for (int i = 0; i < REG_ROWS; ++i) sd[q] += v[i] * a[q][i];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < CPW; ++q)
+      if (q >= q0) sd[q] += __shfl_xor_sync(0xffffffffu, sd[q], o);
+#pragma unroll
+  for (int q = 0; q < CPW; ++q) {
+    if (q < q0) continue;
+    const T sq = sd[q] * tj;
+#pragma unroll
+    for (int i = 0; i < REG_ROWS; ++i) a[q][i] -= sq * v[i];
+  }
+}
 
 template <typename T, int CPW>
 __global__ void __launch_bounds__(REG_WARPS * 32) qr_reg_kernel(const QrItem *__restrict__ items) {
@@ -129,9 +161,7 @@ __global__ void __launch_bounds__(REG_WARPS * 32) qr_reg_kernel(const QrItem *__
   const int m = it.m, n = it.n;
   constexpr int MR = 32 * REG_ROWS + 1;  // leading dimension of V (odd: no bank conflicts across columns)
   T *V = reinterpret_cast<T *>(smem_raw);  // MR x n, column-major
-  T *TG = V + (int64_t)MR * n;             // n x n: Gram V^T V, then T (upper)
-  T *X = TG + (int64_t)n * n;              // n x n: T V_top^T
-  T *tau = X + (int64_t)n * n;             // n
+  T *tau = V + (int64_t)MR * n;            // n
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T a[CPW][REG_ROWS];
   const T *A = static_cast<const T *>(it.A);
@@ -158,8 +188,11 @@ __global__ void __launch_bounds__(REG_WARPS * 32) qr_reg_kernel(const QrItem *__
           if (r > j) s2 += a[q][i] * a[q][i];
         }
       }
-      s2 = warp_sum(s2);
-      alpha = warp_sum(alpha);  // only one lane holds a nonzero contribution
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {  // both sums in one butterfly; one lane holds alpha, the others 0
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+      }
       T tj = T(0), beta = alpha, scale = T(0);
       if (s2 != T(0)) {
         const T nrm = sqrt(alpha * alpha + s2);
@@ -183,22 +216,8 @@ __global__ void __launch_bounds__(REG_WARPS * 32) qr_reg_kernel(const QrItem *__
     }
     __syncthreads();
     const T tj = tau[j];
-    if (tj != T(0)) {
-      T v[REG_ROWS];
-#pragma unroll
-      for (int i = 0; i < REG_ROWS; ++i) v[i] = V[(int64_t)j * MR + lane + 32 * i];
-#pragma unroll
-      for (int q = 0; q < CPW; ++q) {
-        const int c = warp + REG_WARPS * q;
-        if (c <= j || c >= n) continue;
-        T s = T(0);
-#pragma unroll
-        for (int i = 0; i < REG_ROWS; ++i) s += v[i] * a[q][i];
-        s = warp_sum(s) * tj;
-#pragma unroll
-        for (int i = 0; i < REG_ROWS; ++i) a[q][i] -= s * v[i];
-      }
-    }
+    const int q0 = (j - warp + REG_WARPS) / REG_WARPS;  // first owned column right of j (j - warp + 16 >= 1)
+    if (tj != T(0) && q0 < CPW) qr_apply_reflector<T, CPW>(a, V + (int64_t)j * MR, tj, q0, lane);
   }
   // R (n x n upper triangular) from the registers
   T *R = static_cast<T *>(it.R);
@@ -212,64 +231,35 @@ __global__ void __launch_bounds__(REG_WARPS * 32) qr_reg_kernel(const QrItem *__
       if (r < n) R[(int64_t)c * it.ldr + r] = (r <= c) ? a[q][i] : T(0);
     }
   }
-  // Gram G = V^T V (strictly upper part is what the T recurrence needs)
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < n * n; e += nt) {
-    const int jj = e / n, ii = e - jj * n;
-    T g = T(0);
-    if (ii < jj) {
-      const T *vi = V + (int64_t)ii * MR, *vj = V + (int64_t)jj * MR;
-      for (int r = jj; r < m; ++r) g += vi[r] * vj[r];  // v_jj vanishes above row jj
-    }
-    TG[(int64_t)jj * n + ii] = g;
+  // Explicit Q = H_0 H_1 ... H_{n-1} [I; 0], accumulated backwards: every
+  // warp applies H_{n-1}, ..., H_0 to its own columns of [I; 0] in registers.
+  // Column c is untouched by H_j for j > c (rows above j are zero in v_j, and
+  // column c of the partial product is e_c there), so H_j acts on c >= j only.
+#pragma unroll
+  for (int q = 0; q < CPW; ++q)
+#pragma unroll
+    for (int i = 0; i < REG_ROWS; ++i) a[q][i] = (lane + 32 * i == warp + REG_WARPS * q) ? T(1) : T(0);
+  for (int j = n - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    const int q0 = (j - warp + REG_WARPS - 1) / REG_WARPS;  // first owned column >= j (j - warp + 15 >= 0)
+    if (tj != T(0) && q0 < CPW) qr_apply_reflector<T, CPW>(a, V + (int64_t)j * MR, tj, q0, lane);
   }
-  __syncthreads();
-  // T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j];  T[j, j] = tau_j   (column by column)
-  for (int jj = 0; jj < n; ++jj) {
-    T val = T(0);
-    if (tid < jj) {
-      for (int kk = tid; kk < jj; ++kk) val += TG[(int64_t)kk * n + tid] * TG[(int64_t)jj * n + kk];
-      val *= -tau[jj];
-    }
-    __syncthreads();
-    if (tid < jj) TG[(int64_t)jj * n + tid] = val;
-    if (tid == jj) TG[(int64_t)jj * n + jj] = tau[jj];
-    __syncthreads();
-  }
-  // X = T V_top^T:  X[k, c] = sum_{l=k..c} T[k, l] V[c, l]
-  for (int e = tid; e < n * n; e += nt) {
-    const int c = e / n, kk = e - c * n;
-    T x = T(0);
-    for (int l = kk; l <= c; ++l) x += TG[(int64_t)l * n + kk] * V[(int64_t)l * MR + c];
-    X[(int64_t)c * n + kk] = x;
-  }
-  __syncthreads();
-  // Q = [I; 0] - V X, written straight from the thread's (row, column) pairs
   T *Q = static_cast<T *>(it.Q);
 #pragma unroll
   for (int q = 0; q < CPW; ++q) {
     const int c = warp + REG_WARPS * q;
     if (c >= n) continue;
-    T acc[REG_ROWS];
-#pragma unroll
-    for (int i = 0; i < REG_ROWS; ++i) acc[i] = (lane + 32 * i == c) ? T(1) : T(0);
-    for (int kk = 0; kk < n; ++kk) {
-      const T x = X[(int64_t)c * n + kk];
-      if (x == T(0)) continue;
-#pragma unroll
-      for (int i = 0; i < REG_ROWS; ++i) acc[i] -= V[(int64_t)kk * MR + lane + 32 * i] * x;
-    }
 #pragma unroll
     for (int i = 0; i < REG_ROWS; ++i) {
       const int r = lane + 32 * i;
-      if (r < m) Q[(int64_t)c * it.ldq + r] = acc[i];
+      if (r < m) Q[(int64_t)c * it.ldq + r] = a[q][i];
     }
   }
 }
 
 template <typename T, int CPW>
 cudaError_t launch_qr_reg(const QrItem *d_items, int n_items, int max_n, cudaStream_t s) {
-  const size_t smem = ((size_t)(32 * REG_ROWS + 1) * max_n + 2 * (size_t)max_n * max_n + max_n) * sizeof(T);
+  const size_t smem = ((size_t)(32 * REG_ROWS + 1) * max_n + max_n) * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(qr_reg_kernel<T, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   qr_reg_kernel<T, CPW><<<n_items, REG_WARPS * 32, smem, s>>>(d_items);
