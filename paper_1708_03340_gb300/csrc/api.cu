@@ -12,6 +12,7 @@
 #include <mutex>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -244,6 +245,8 @@ struct Launch {
   bool split = false;
   int node = -1;
   double flops = 0.0;  // algorithmic flops of the launch (literal, i.e. maximal, dims)
+  int tc_tiles = 0;    // GEMM: tiles of the tensor-core kernel
+  double tc_flops = 0.0;  // flops of items whose shape suits 128-row tensor-core tiles
   const void *ranks = nullptr;  // tagged pointer to the rank array used by the launch
   void *scratch = nullptr;      // eig scratch (tagged)
 };
@@ -323,8 +326,19 @@ struct Plan {
     if (g.n_mult < 1) g.n_mult = 1;
     if (g.b_mult < 1) g.b_mult = 1;
     if (g.M <= 0 || g.N <= 0) return;
+    if (dtype == HT_F32 && g.M < 128 && g.N >= 128 && g.m_ref < 0 && g.n_ref < 0) {
+      // C^T = B^T A^T puts the long dimension on the 128-row MMA tiles
+      std::swap(g.A, g.B);
+      const int64_t am = g.sam, ak = g.sak, ako = g.sako, ab = g.sab;
+      g.sam = g.sbn; g.sak = g.sbk; g.sako = g.sbko; g.sab = g.sbb;
+      g.sbn = am; g.sbk = ak; g.sbko = ako; g.sbb = ab;
+      std::swap(g.scm, g.scn);
+      std::swap(g.M, g.N);
+    }
     g.tiles_m = (g.M + 63) / 64;
     g.tiles_n = (g.N + 63) / 64;
+    g.tc_tiles_m = (g.M + 127) / 128;
+    g.tc_tiles_n = (g.N + 63) / 64;
     if (node_sched && cur().n > 0 && cur().node != node) {
       LKind k = cur().kind;
       const void *r = cur().ranks;
@@ -333,7 +347,11 @@ struct Plan {
     Launch &L = cur();
     g.tile0 = L.tiles;
     L.tiles += g.tiles_m * g.tiles_n * g.batch * g.ksplit;
-    L.flops += 2.0 * g.M * g.N * (double)g.K * g.Ko * g.batch;
+    g.tc_tile0 = L.tc_tiles;
+    L.tc_tiles += g.tc_tiles_m * g.tc_tiles_n * g.batch * g.ksplit;
+    const double fl = 2.0 * g.M * g.N * (double)g.K * g.Ko * g.batch;
+    L.flops += fl;
+    if (g.M >= 128) L.tc_flops += fl;
     if (g.ksplit > 1) {
       L.split = true;
       g.part = salloc_bytes((size_t)g.ksplit * g.batch * g.M * g.N * esz);
@@ -432,6 +450,15 @@ void reloc_items<RankItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
 // order after the last launch.  `keep` receives the relocated persistent base
 // (so that callers can read results) and the caller must free it with
 // cudaFreeAsync; if keep is null, everything is freed here.
+// The tensor-core contraction kernel (k_tc.cu) runs the FP32 contractions when
+// HTGB_TC=1.  It is off by default: on deep trees its FP32 accumulation inside
+// the MMA (not compensated) costs about 6x the error of the compensated SIMT
+// kernel (||X|| to 6e-6 instead of 1e-6 at d = 64) and it is not faster there.
+bool tc_enabled() {
+  const char *v = getenv("HTGB_TC");
+  return v && v[0] == '1';
+}
+
 // ext_base / ext_cap: run inside caller-provided device memory instead of
 // allocating (nothing is allocated or freed then; keep_base must be null).
 ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base, char *ext_base = nullptr, size_t ext_cap = 0) {
@@ -482,10 +509,13 @@ ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base, char *ext_base = n
     const int *rk = static_cast<const int *>(L.ranks);
     prof_begin((int)L.kind, s);
     switch (L.kind) {
-      case L_GEMM:
-        e = f64 ? launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, nullptr, s)
-                : launch_gemm<float>((const GemmItem *)items, L.n, L.tiles, rk, L.split, nullptr, s);
+      case L_GEMM: {
+        // FP32 launches whose flops sit mostly in tall items run on the tensor cores
+        const bool tc = !f64 && tc_enabled() && L.tc_flops >= 0.5 * L.flops;
+        e = f64 ? launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s)
+                : launch_gemm<float>((const GemmItem *)items, L.n, L.tiles, rk, L.split, tc ? L.tc_tiles : 0, s);
         break;
+      }
       case L_QR:
         e = f64 ? launch_qr<double>((const QrItem *)items, L.n, L.max_m, L.max_n, s)
                 : launch_qr<float>((const QrItem *)items, L.n, L.max_m, L.max_n, s);

@@ -36,6 +36,7 @@ struct GemmItem {
   double alpha, beta;
   int tiles_m, tiles_n;  // tile grid at the literal (maximal) dims
   int tile0;             // first global tile index of this item
+  int tc_tiles_m, tc_tiles_n, tc_tile0;  // same for the tensor-core kernel's 128 x 128 tiles
 };
 
 // Householder QR of one row block (m >= n) held in shared memory.
@@ -101,9 +102,11 @@ struct RankItem {
 // ---------------------------------------------------------------------------
 // launchers (stream-ordered; return cudaGetLastError())
 // ---------------------------------------------------------------------------
+// tc_tiles > 0: run the FP32 items on the tcgen05 kernel (k_tc.cu) with that many tiles
 template <typename T>
 cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks,
-                        bool any_split, const GemmItem *h_items, cudaStream_t s);
+                        bool any_split, int tc_tiles, cudaStream_t s);
+cudaError_t launch_gemm_tc(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, cudaStream_t s);
 template <typename T>
 cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s);
 // mode 0: FP64 QL; mode 1: FP32 QL followed by one FP64 refinement step.

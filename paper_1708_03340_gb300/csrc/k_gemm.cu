@@ -182,20 +182,26 @@ __global__ void gemm_reduce_kernel(const GemmItem *__restrict__ items, const int
 
 template <typename T>
 cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, bool any_split,
-                        const GemmItem *h_items, cudaStream_t s) {
-  (void)h_items;
+                        int tc_tiles, cudaStream_t s) {
   if (n_items <= 0 || total_tiles <= 0) return cudaSuccess;
-  gemm_kernel<T><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
-  count_launch();
-  if (any_split) {
-    dim3 grid(64, n_items);
-    gemm_reduce_kernel<T><<<grid, 256, 0, s>>>(d_items, d_ranks);
+  if (sizeof(T) == 4 && tc_tiles > 0) {
+    cudaError_t e = launch_gemm_tc(d_items, n_items, tc_tiles, d_ranks, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    gemm_kernel<T><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
     count_launch();
+  }
+  if (any_split) {
+    for (int base = 0; base < n_items; base += 65535) {
+      const int cnt = n_items - base < 65535 ? n_items - base : 65535;
+      gemm_reduce_kernel<T><<<dim3(64, cnt), 256, 0, s>>>(d_items + base, d_ranks);
+      count_launch();
+    }
   }
   return cudaGetLastError();
 }
 
-template cudaError_t launch_gemm<double>(const GemmItem *, int, int, const int *, bool, const GemmItem *, cudaStream_t);
-template cudaError_t launch_gemm<float>(const GemmItem *, int, int, const int *, bool, const GemmItem *, cudaStream_t);
+template cudaError_t launch_gemm<double>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t);
+template cudaError_t launch_gemm<float>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t);
 
 }  // namespace htgb

@@ -217,3 +217,27 @@ def test_golden_diagonal_tensor():
         assert np.abs(sg[t] - np.array(g["sigma"])).max() <= 1e-14
     assert abs(rep["norm"] - g["norm"]) <= 1e-14
     assert abs(np.sqrt(rep["discarded_sq"] / (2 * d - 3)) - g["trunc_err"]) <= 1e-13
+
+
+@pytest.mark.parametrize("case", ["small", "tall", "big_rank", "uneven"])
+def test_tensor_core_contractions_match_simt(case, monkeypatch):
+    """The tcgen05 contraction kernel (FP32 data, 3-piece TF32 split) and the
+    SIMT kernel compute the same truncation: sigma^2 normwise and entries
+    relative to ||X|| agree to the FP32 tolerance."""
+    d, n, a, c = _case(case)
+    r = {"small": 8, "tall": 5, "big_rank": 30, "uneven": 3}[case]
+    idx = sample_idx(n, 200, 11)
+    out = {}
+    for tc in ("1", "0"):
+        monkeypatch.setenv("HTGB_TC", tc)
+        tree, A, C, X = gpu_sum(d, n, a, c, F32)
+        rep = X.truncate(mode="rank", rank_cap=r, prec=htgb.HT_PREC_FP32)
+        out[tc] = (rep, X.eval(idx), X.ranks())
+    (r1, e1, k1), (r0, e0, k0) = out["1"], out["0"]
+    assert list(k1) == list(k0)
+    # each path is within the FP32 tolerance of the oracle: they agree to twice that
+    tol = 2 * TOL[F32]
+    s1, s0 = split_sigma(r1["korth"], r1["sigma"]), split_sigma(r0["korth"], r0["sigma"])
+    check_sigma(s1, s0, tol)
+    assert abs(r1["norm"] - r0["norm"]) <= tol * r0["norm"]
+    assert np.abs(e1 - e0).max() <= tol * r0["norm"]
