@@ -572,6 +572,7 @@ inline GemmItem gemm0() {
   g.ksplit = 1;
   g.alpha = 1.0;
   g.beta = 0.0;
+  g.k_total = -1;
   return g;
 }
 
@@ -595,7 +596,168 @@ struct Mat {
   int node;
 };
 
+void plan_tsqr_narrow(Plan &P, const std::vector<Mat> &mats);
+
+constexpr int kPanel = 64;  // widest matrix the register-resident QR blocks factor
+
+// Reduced QR of matrices wider than one panel: columns are taken in panels
+// of kPanel; panel p is projected twice against the finished Q columns
+// (block Gram-Schmidt, "twice is enough": R[<p, p] = C1 + C2 with
+// C = Q_<p^T A_p, A_p -= Q_<p C) and then factored by the TSQR of
+// plan_tsqr_narrow.  A (the matrix, overwritten by the projections) and Q
+// (the output) may be the same buffer.
+void plan_tsqr_panels(Plan &P, const std::vector<Mat> &mats) {
+  const size_t esz = P.esz;
+  const bool f64 = (P.dtype == HT_F64);
+  int max_panels = 0;
+  for (const Mat &M : mats) max_panels = std::max(max_panels, (M.n + kPanel - 1) / kPanel);
+  // R starts as zero below the diagonal blocks
+  P.begin(L_COPY);
+  for (const Mat &M : mats) {
+    CopyItem z = copy0();
+    z.dst = M.R;
+    z.dr = 1;
+    z.dc = M.ldr;
+    z.rows = M.n;
+    z.cols = M.n;
+    z.zero = 1;
+    z.dst_f64 = f64;
+    P.copy(z, M.node);
+  }
+  constexpr int kChunk = 256;  // rows per chunk of the long reductions Q^T A
+  for (int p = 0; p < max_panels; ++p) {
+    struct PJ {
+      const Mat *M;
+      int c0, w;
+      void *C1, *C2;
+    };
+    std::vector<PJ> pj;
+    for (const Mat &M : mats) {
+      const int np = (M.n + kPanel - 1) / kPanel;
+      if (p >= np) continue;
+      PJ j;
+      j.M = &M;
+      j.c0 = p * kPanel;
+      j.w = std::min(kPanel, M.n - j.c0);
+      j.C1 = j.C2 = nullptr;
+      if (p > 0) {
+        j.C1 = P.salloc_bytes((size_t)j.c0 * j.w * esz);
+        j.C2 = P.salloc_bytes((size_t)j.c0 * j.w * esz);
+      }
+      pj.push_back(j);
+    }
+    if (p > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        // C = Q_<p^T A_p   ((c0 x w), reduction over the m rows in chunks)
+        P.begin(L_GEMM);
+        int tiles = 0;
+        for (PJ &j : pj) tiles += ((j.c0 + 63) / 64) * ((j.w + 63) / 64);
+        for (PJ &j : pj) {
+          const Mat &M = *j.M;
+          const int ko = (M.m + kChunk - 1) / kChunk;
+          GemmItem g = gemm0();
+          g.A = M.Q;
+          g.sam = M.ldq;
+          g.sak = 1;
+          g.sako = kChunk;
+          g.B = static_cast<const char *>(M.A) + (int64_t)j.c0 * M.lda * esz;
+          g.sbk = 1;
+          g.sbko = kChunk;
+          g.sbn = M.lda;
+          g.C = pass == 0 ? j.C1 : j.C2;
+          g.scm = 1;
+          g.scn = j.c0;
+          g.M = j.c0;
+          g.N = j.w;
+          g.K = kChunk;
+          g.Ko = ko;
+          g.k_total = M.m;
+          g.ksplit = std::max(1, std::min(ko, (2 * kSmCount + tiles - 1) / std::max(tiles, 1)));
+          P.gemm(g, M.node);
+        }
+        // A_p -= Q_<p C
+        P.begin(L_GEMM);
+        for (PJ &j : pj) {
+          const Mat &M = *j.M;
+          GemmItem g = gemm0();
+          g.A = M.Q;
+          g.sam = 1;
+          g.sak = M.ldq;
+          g.B = pass == 0 ? j.C1 : j.C2;
+          g.sbk = 1;
+          g.sbn = j.c0;
+          g.C = const_cast<char *>(static_cast<const char *>(M.A)) + (int64_t)j.c0 * M.lda * esz;
+          g.scm = 1;
+          g.scn = M.lda;
+          g.M = M.m;
+          g.N = j.w;
+          g.K = j.c0;
+          g.alpha = -1.0;
+          g.beta = 1.0;
+          P.gemm(g, M.node);
+        }
+      }
+      // R[0:c0, c0:c0+w] = C1 + C2
+      P.begin(L_COPY);
+      for (PJ &j : pj) {
+        const Mat &M = *j.M;
+        CopyItem c = copy0();
+        c.src = j.C1;
+        c.dst = static_cast<char *>(M.R) + (int64_t)j.c0 * M.ldr * esz;
+        c.sr = 1;
+        c.sc = j.c0;
+        c.dr = 1;
+        c.dc = M.ldr;
+        c.rows = j.c0;
+        c.cols = j.w;
+        c.src_f64 = c.dst_f64 = f64;
+        P.copy(c, M.node);
+      }
+      P.begin(L_COPY);
+      for (PJ &j : pj) {
+        const Mat &M = *j.M;
+        CopyItem c = copy0();
+        c.src = j.C2;
+        c.dst = static_cast<char *>(M.R) + (int64_t)j.c0 * M.ldr * esz;
+        c.sr = 1;
+        c.sc = j.c0;
+        c.dr = 1;
+        c.dc = M.ldr;
+        c.rows = j.c0;
+        c.cols = j.w;
+        c.beta = 1.0;
+        c.src_f64 = c.dst_f64 = f64;
+        P.copy(c, M.node);
+      }
+    }
+    // TSQR of the (projected) panel: Q columns c0.., R diagonal block
+    std::vector<Mat> panel;
+    for (PJ &j : pj) {
+      const Mat &M = *j.M;
+      Mat q;
+      q.A = static_cast<const char *>(M.A) + (int64_t)j.c0 * M.lda * esz;
+      q.lda = M.lda;
+      q.m = M.m;
+      q.n = j.w;
+      q.Q = static_cast<char *>(M.Q) + (int64_t)j.c0 * M.ldq * esz;
+      q.ldq = M.ldq;
+      q.R = static_cast<char *>(M.R) + ((int64_t)j.c0 * M.ldr + j.c0) * esz;
+      q.ldr = M.ldr;
+      q.node = M.node;
+      panel.push_back(q);
+    }
+    plan_tsqr_narrow(P, panel);
+  }
+}
+
 void plan_tsqr(Plan &P, const std::vector<Mat> &mats) {
+  std::vector<Mat> narrow, wide;
+  for (const Mat &M : mats) (M.n > kPanel ? wide : narrow).push_back(M);
+  if (!narrow.empty()) plan_tsqr_narrow(P, narrow);
+  if (!wide.empty()) plan_tsqr_panels(P, wide);
+}
+
+void plan_tsqr_narrow(Plan &P, const std::vector<Mat> &mats) {
   struct Blk {
     int64_t r0;
     int m;

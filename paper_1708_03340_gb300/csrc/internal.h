@@ -36,7 +36,8 @@ struct GemmItem {
   double alpha, beta;
   int tiles_m, tiles_n;  // tile grid at the literal (maximal) dims
   int tile0;             // first global tile index of this item
-  int tc_tiles_m, tc_tiles_n, tc_tile0;  // same for the tensor-core kernel's 128 x 128 tiles
+  int tc_tiles_m, tc_tiles_n, tc_tile0;  // same for the tensor-core kernel's 128 x 64 tiles
+  int64_t k_total;  // >= 0: only flat reduction indices ko * K + k < k_total take part (ragged last chunk)
 };
 
 // Householder QR of one row block (m >= n) held in shared memory.
@@ -58,8 +59,8 @@ struct EigItem {
   int k;
 };
 
-// 2-D strided copy with optional cast, identity fill, scaling.
-//   dst[r*dr + c*dc] = src ? alpha*src[r*sr + c*sc] : (r == c ? 1 : 0)
+// 2-D strided copy with optional cast, identity or zero fill, scaling.
+//   dst[r*dr + c*dc] = (src ? alpha*src[r*sr + c*sc] : (zero ? 0 : (r == c ? 1 : 0))) + beta*dst[...]
 // rows/cols may be rank references like GemmItem dims (-1: literal).
 struct CopyItem {
   const void *src;
@@ -68,7 +69,8 @@ struct CopyItem {
   int rows, cols;
   int rows_ref, cols_ref;
   int src_f64, dst_f64;
-  double alpha;
+  double alpha, beta;
+  int zero;
 };
 
 // Packed copy of an inner node into its truncated, compact layout:

@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
         if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
         int gm = m0 + mm, gk = k0 + kk;
         T v = T(0);
-        if (gm < M && gk < K) v = Ak[(int64_t)gm * it.sam + (int64_t)gk * it.sak];
+        if (gm < M && gk < K && (it.k_total < 0 || (int64_t)ko * K + gk < it.k_total))
+          v = Ak[(int64_t)gm * it.sam + (int64_t)gk * it.sak];
         As[kk][mm] = v;
       }
 #pragma unroll
@@ -88,7 +89,8 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
         if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
         int gn = n0 + nn, gk = k0 + kk;
         T v = T(0);
-        if (gn < N && gk < K) v = Bk[(int64_t)gk * it.sbk + (int64_t)gn * it.sbn];
+        if (gn < N && gk < K && (it.k_total < 0 || (int64_t)ko * K + gk < it.k_total))
+          v = Bk[(int64_t)gk * it.sbk + (int64_t)gn * it.sbn];
         Bs[kk][nn] = v;
       }
       __syncthreads();

@@ -32,10 +32,16 @@ __global__ void copy_kernel(const CopyItem *__restrict__ items, const int *__res
                      : (double)static_cast<const float *>(it.src)[r * it.sr + c * it.sc];
       v *= it.alpha;
     } else {
-      v = (r == c) ? 1.0 : 0.0;
+      v = (!it.zero && r == c) ? 1.0 : 0.0;
     }
-    if (it.dst_f64) static_cast<double *>(it.dst)[r * it.dr + c * it.dc] = v;
-    else static_cast<float *>(it.dst)[r * it.dr + c * it.dc] = (float)v;
+    const int64_t o = r * it.dr + c * it.dc;
+    if (it.dst_f64) {
+      double *d = static_cast<double *>(it.dst) + o;
+      *d = (it.beta != 0.0) ? v + it.beta * *d : v;
+    } else {
+      float *d = static_cast<float *>(it.dst) + o;
+      *d = (it.beta != 0.0) ? (float)(v + it.beta * (double)*d) : (float)v;
+    }
   }
 }
 

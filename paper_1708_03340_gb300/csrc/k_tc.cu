@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmItem *__r
           int r, k;
           if (a_mfast) { r = e % TCM; k = e / TCM; } else { k = e % TCK; r = e / TCK; }
           const int gm = m0 + r, gk = k0 + k;
-          x[q] = (gm < M && gk < K) ? Ak[(int64_t)gm * it.sam + (int64_t)gk * it.sak] : 0.0f;
+          const bool kin = gk < K && (it.k_total < 0 || (int64_t)ko * K + gk < it.k_total);
+          x[q] = (gm < M && kin) ? Ak[(int64_t)gm * it.sam + (int64_t)gk * it.sak] : 0.0f;
         }
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
@@ -195,7 +196,8 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmItem *__r
           int nn, k;
           if (b_nfast) { nn = e % NT; k = e / NT; } else { k = e % TCK; nn = e / TCK; }
           const int gn = n0 + nn, gk = k0 + k;
-          x[q] = (gn < N && gk < K) ? Bk[(int64_t)gk * it.sbk + (int64_t)gn * it.sbn] : 0.0f;
+          const bool kin = gk < K && (it.k_total < 0 || (int64_t)ko * K + gk < it.k_total);
+          x[q] = (gn < N && kin) ? Bk[(int64_t)gk * it.sbk + (int64_t)gn * it.sbn] : 0.0f;
         }
 #pragma unroll
         for (int q = 0; q < PERB; ++q) {

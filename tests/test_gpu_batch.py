@@ -1,0 +1,77 @@
+"""ht_truncate_batch: many HT tensors of uneven d, n and rank, each level of
+all tensors in one batched launch, against the oracle tensor by tensor.
+
+The tensors follow the batched recipe at reduced size (d in 4..9, n in
+12..90, k in 3..16; each the sum of 4 tensors with sigma_j = 2^-j, truncated
+back to its k), so that the oracle finishes in seconds."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1708_03340_gb300 import htgb
+from paper_1708_03340_gb300 import inputs as I
+from tests.gpu_util import as_stored, check_sigma, sample_idx, split_sigma
+
+pytestmark = pytest.mark.gpu
+
+
+def _sum4(spec, dtype):
+    d, n, k, s = spec
+    terms = I.batched_terms(spec)
+    tree = htgb.HTTree(d)
+    X = None
+    ko, xo = None, None
+    for (nv, kv, xv) in terms:
+        T = htgb.HTTensor.from_blob(tree, nv, kv, xv, dtype)
+        X = T if X is None else X.add(T)
+        xs = as_stored(xv, dtype)
+        if ko is None:
+            ko, xo = kv, xs
+        else:
+            ko, xo = O.add(d, nv, ko, xo, kv, xs)
+    return tree, terms[0][0], X, ko, xo
+
+
+@pytest.mark.parametrize("dtype", [htgb.HT_F64, htgb.HT_F32])
+def test_truncate_batch_uneven(dtype):
+    specs = I.batched_specs(count=7, seed=5, d_range=(4, 9), n_range=(12, 90), k_range=(3, 16))
+    built = [_sum4(sp, dtype) for sp in specs]
+    xs = [b[2] for b in built]
+    k_target = specs[0][2]
+    # every tensor goes back to its own k: the batch call takes one option set, so
+    # truncate in groups of equal k
+    groups = {}
+    for i, sp in enumerate(specs):
+        groups.setdefault(sp[2], []).append(i)
+    prec = htgb.HT_PREC_FP64 if dtype == htgb.HT_F64 else htgb.HT_PREC_FP32
+    tol = 1e-12 if dtype == htgb.HT_F64 else 1e-6
+    for k_target, idxs in groups.items():
+        opts = htgb.make_opts(mode="rank", rank_cap=k_target, prec=prec)
+        reps = htgb.ht_truncate_batch([xs[i].handle for i in idxs], opts, report=True)
+        for i, rep in zip(idxs, reps):
+            d, n, k, s = specs[i]
+            tree, nvec, X, kin, xin = built[i]
+            ref = O.truncate(d, nvec, kin, xin, mode="rank", rank_cap=k_target)
+            assert list(X.ranks()) == list(ref["k"])
+            assert abs(rep["norm"] - ref["norm"]) <= tol * ref["norm"]
+            idx = sample_idx(nvec, 150, i)
+            got = X.eval(idx)
+            want = O.eval_entries(d, nvec, ref["k"], ref["x"], idx)
+            assert np.abs(got - want).max() <= 10 * tol * ref["norm"], (i, specs[i])
+
+
+def test_batch_equals_single_calls():
+    """One batched call gives the same tensors as one call per tensor."""
+    specs = I.batched_specs(count=5, seed=9, d_range=(4, 7), n_range=(10, 40), k_range=(4, 8))
+    out = []
+    for mode in ("batch", "single"):
+        built = [_sum4(sp, htgb.HT_F64) for sp in specs]
+        opts = htgb.make_opts(mode="rank", rank_cap=4, prec=htgb.HT_PREC_FP64)
+        if mode == "batch":
+            htgb.ht_truncate_batch([b[2].handle for b in built], opts)
+        else:
+            for b in built:
+                htgb.ht_truncate(b[2].handle, opts)
+        out.append([b[2].eval(sample_idx(b[1], 60, 2)) for b in built])
+    for a, b in zip(*out):
+        assert np.abs(a - b).max() <= 1e-13 * max(np.abs(b).max(), 1e-300)

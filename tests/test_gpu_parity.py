@@ -44,7 +44,7 @@ def test_eval_entries():
 
 
 @pytest.mark.parametrize("dtype", [F64, F32])
-@pytest.mark.parametrize("case", ["small", "uneven", "tall", "wide_leaf", "d2", "big_rank"])
+@pytest.mark.parametrize("case", ["small", "uneven", "tall", "wide_leaf", "d2", "big_rank", "rank128", "rank200"])
 def test_orthogonalize(dtype, case):
     d, n, a, c = _case(case)
     tree, A, C, X = gpu_sum(d, n, a, c, dtype)
@@ -86,9 +86,15 @@ def _case(case):
     if case == "d2":
         nn = [40, 33]
         return 2, np.array(nn), I.random_ht(2, nn, 6, 61), I.random_ht(2, nn, 5, 62)
-    if case == "big_rank":  # rank 81 > 64 after the addition: shared-memory QR blocks
+    if case == "big_rank":  # rank 81 > 64 after the addition: two QR panels
         nn = [700, 200, 450, 180]
         return 4, np.array(nn), I.random_ht(4, nn, 40, 71), I.random_ht(4, nn, 41, 72)
+    if case == "rank128":  # rank 128: two full panels, leaves taller than one block
+        nn = [600, 300, 520, 400]
+        return 4, np.array(nn), I.random_ht(4, nn, 64, 81), I.random_ht(4, nn, 64, 82)
+    if case == "rank200":  # rank 200: four panels (64, 64, 64, 8), n < k at one leaf
+        nn = [700, 150, 420, 640]
+        return 4, np.array(nn), I.random_ht(4, nn, 100, 91), I.random_ht(4, nn, 100, 92)
     raise ValueError(case)
 
 
@@ -145,10 +151,11 @@ def _trunc_compare(d, n, a, c, dtype, opts, entries_tol_scale=10.0, floor=0.0):
 
 
 @pytest.mark.parametrize("dtype", [F64, F32])
-@pytest.mark.parametrize("case", ["small", "uneven", "tall", "wide_leaf", "d2", "big_rank"])
+@pytest.mark.parametrize("case", ["small", "uneven", "tall", "wide_leaf", "d2", "big_rank", "rank128", "rank200"])
 def test_truncate_rank(dtype, case):
     d, n, a, c = _case(case)
-    r = {"small": 8, "uneven": 3, "tall": 5, "wide_leaf": 3, "d2": 4, "big_rank": 30}[case]
+    r = {"small": 8, "uneven": 3, "tall": 5, "wide_leaf": 3, "d2": 4, "big_rank": 30, "rank128": 64,
+         "rank200": 100}[case]
     _trunc_compare(d, n, a, c, dtype, dict(mode="rank", rank_cap=r))
 
 
