@@ -13,6 +13,7 @@ namespace {
 constexpr int QR_THREADS = 512;
 constexpr int kSmemLimit = 232448;  // opt-in shared memory per CTA on sm_103
 constexpr int kSmemReserve = 2048;
+constexpr int kRegRows = 256;  // rows of a register-resident block (32 x NI)
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -111,158 +112,267 @@ __global__ void __launch_bounds__(QR_THREADS) qr_block_kernel(const QrItem *__re
 }
 
 // ---------------------------------------------------------------------------
-// Register-resident variant for n <= 16*CPW columns and m <= 32*ROWS rows.
-// Warp w owns columns w, w+16, ...; lane l owns rows l, l+32, ....  The
-// factorisation needs one barrier per column: the owner warp of column j
-// builds the reflector from its registers and publishes v_j in shared
-// memory, then every warp applies H_j to its own columns (the dot products of
-// its active columns reduced together).  Q = H_0 ... H_{n-1} [I; 0] is then
-// accumulated backwards by every warp on its own columns, from the stored
-// reflectors, without further barriers.
+// Register-resident variant for n <= 4*NW columns and m <= 32*NI rows.
+//
+// Warp w owns columns 4w..4w+3, one per group of 8 lanes; lane s of a group
+// holds rows 32i + 4s + e (i < NI, e < 4) of its column, so a column's dot
+// products reduce over the 8 lanes of its group (3 shuffles) and shared
+// vectors are read four rows at a time.
+//
+// Column j's reflector H_j = I - tau_j v_j v_j^T, v_j = [0; 1; scl_j w_j],
+// where w_j is the part of column j below the diagonal (after H_0..H_{j-1}).
+// The group owning column j publishes w_j (rows <= j zero) and alpha_j (the
+// diagonal entry) in shared memory; after one barrier every warp forms
+// ||w_j||, beta_j, tau_j and scl_j itself (the same sums in the same order,
+// so the same bits everywhere) and applies H_j to its columns right of j.
+// The owner of column j+1 then publishes w_{j+1}.  The critical path per
+// column is one shared-memory round trip, one reduction, a square root and
+// a division; no warp waits for another to build the reflector.
+//
+// The w_j stay in shared memory, so Q = H_0 ... H_{n-1} [I; 0] is then
+// accumulated backwards on the columns in registers without barriers.
 // ---------------------------------------------------------------------------
-constexpr int REG_ROWS = 8;   // rows per lane -> m <= 256
-constexpr int REG_WARPS = 16;
+constexpr int REG_MR = kRegRows;  // leading dimension of the reflector array (rows)
 
-// a[q] <- (I - tau v v^T) a[q] for the owned columns q >= q0 (warp-uniform),
-// v read from shared memory (one column of V, rows lane + 32 i); the dot
-// products of the active columns are reduced together.
-template <typename T, int CPW>
-__device__ __forceinline__ void qr_apply_reflector(T (&a)[CPW][REG_ROWS], const T *vcol, T tj, int q0, int lane) {
-  T v[REG_ROWS];
+__device__ __forceinline__ void ld4(const float *p, float (&x)[4]) {
+  const float4 t = *reinterpret_cast<const float4 *>(p);
+  x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&x)[4]) {
+  const double2 t0 = reinterpret_cast<const double2 *>(p)[0], t1 = reinterpret_cast<const double2 *>(p)[1];
+  x[0] = t0.x; x[1] = t0.y; x[2] = t1.x; x[3] = t1.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&x)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&x)[4]) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(x[0], x[1]);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(x[2], x[3]);
+}
+
+// Sum over the 8 lanes of a group (lanes 8g .. 8g+7).
+template <typename T>
+__device__ __forceinline__ T group_sum(T v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  return v;
+}
+
+// Row j (< 64) of the lane's column, or 0 if the lane does not hold it.
+template <typename T, int NI>
+__device__ __forceinline__ T row_of(const T (&a)[NI][4], int j, int s) {
+  T x = T(0);
 #pragma unroll
-  for (int i = 0; i < REG_ROWS; ++i) v[i] = vcol[lane + 32 * i];
-  T sd[CPW];
+  for (int i = 0; i < 2 && i < NI; ++i)
 #pragma unroll
-  for (int q = 0; q < CPW; ++q) {
-    sd[q] = T(0);
-    if (q >= q0) {
+    for (int e = 0; e < 4; ++e)
+      if (32 * i + 4 * s + e == j) x = a[i][e];
+  return x;
+}
+
+template <typename T, int NI>
+__device__ __forceinline__ void row_sub(T (&a)[NI][4], int j, int s, T d) {
 #pragma unroll
-      for (int i = 0; i < REG_ROWS; ++i) sd[q] += v[i] * a[q][i];
+  for (int i = 0; i < 2 && i < NI; ++i)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (32 * i + 4 * s + e == j) a[i][e] -= d;
+}
+
+// Publish w_j of column j (rows <= j zero) into wj and alpha_j; only the
+// lanes with me set (the owner group) write.  Called by the whole warp.
+template <typename T, int NI>
+__device__ __forceinline__ void publish(const T (&a)[NI][4], T *wj, T *alpha_j, int j, int s, bool me) {
+  const T al = group_sum(row_of<T, NI>(a, j, s));
+  if (!me) return;
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    T x[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = 32 * i + 4 * s + e;
+      x[e] = (i >= 2 || r > j) ? a[i][e] : T(0);  // j < 64: rows of chunks i >= 2 lie below j
+    }
+    st4(wj + 32 * i + 4 * s, x);
+  }
+  if (s == 0) *alpha_j = al;
+}
+
+// a <- H_j a for the lane's column: d = a_j + scl (w^T a), a -= tau d v.
+// Every lane takes part in the reductions; upd says whether this lane's
+// column takes the update.  kKeep keeps w in registers between the passes.
+template <typename T, int NI, bool kKeep>
+__device__ __forceinline__ void reg_apply(T (&a)[NI][4], const T *wj, int j, T tj, T scl, bool upd, int s) {
+  T v[kKeep ? NI : 1][4];
+  T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    T x[4];
+    ld4(wj + 32 * i + 4 * s, x);
+    d0 += x[0] * a[i][0];
+    d1 += x[1] * a[i][1];
+    d2 += x[2] * a[i][2];
+    d3 += x[3] * a[i][3];
+    if (kKeep) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[kKeep ? i : 0][e] = x[e];
     }
   }
+  const T aj = group_sum(row_of<T, NI>(a, j, s));
+  const T sw = group_sum((d0 + d1) + (d2 + d3));
+  if (!upd) return;
+  const T d = tj * (aj + scl * sw);  // tau (v^T a)
+  const T ds = d * scl;
+  row_sub<T, NI>(a, j, s, d);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
+  for (int i = 0; i < NI; ++i) {
+    T x[4];
+    if (kKeep) {
 #pragma unroll
-    for (int q = 0; q < CPW; ++q)
-      if (q >= q0) sd[q] += __shfl_xor_sync(0xffffffffu, sd[q], o);
+      for (int e = 0; e < 4; ++e) x[e] = v[kKeep ? i : 0][e];
+    } else {
+      ld4(wj + 32 * i + 4 * s, x);
+    }
 #pragma unroll
-  for (int q = 0; q < CPW; ++q) {
-    if (q < q0) continue;
-    const T sq = sd[q] * tj;
-#pragma unroll
-    for (int i = 0; i < REG_ROWS; ++i) a[q][i] -= sq * v[i];
+    for (int e = 0; e < 4; ++e) a[i][e] -= ds * x[e];
   }
 }
 
-template <typename T, int CPW>
-__global__ void __launch_bounds__(REG_WARPS * 32) qr_reg_kernel(const QrItem *__restrict__ items) {
+template <typename T, int NW, int NI, bool KEEP>
+__global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restrict__ items) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const QrItem it = items[blockIdx.x];
   const int m = it.m, n = it.n;
-  constexpr int MR = 32 * REG_ROWS + 1;  // leading dimension of V (odd: no bank conflicts across columns)
-  T *V = reinterpret_cast<T *>(smem_raw);  // MR x n, column-major
-  T *tau = V + (int64_t)MR * n;            // n
+  T *W = reinterpret_cast<T *>(smem_raw);  // REG_MR x n: w_j in column j
+  T *tau = W + (int64_t)REG_MR * n;        // n
+  T *scl = tau + n;                        // n
+  T *alp = scl + n;                        // n
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T a[CPW][REG_ROWS];
-  const T *A = static_cast<const T *>(it.A);
+  const int g = lane >> 3, s = lane & 7;
+  const int c = 4 * warp + g;  // this lane's column
+  T a[NI][4];
+  const T *A = static_cast<const T *>(it.A) + (int64_t)c * it.lda;
 #pragma unroll
-  for (int q = 0; q < CPW; ++q) {
-    const int c = warp + REG_WARPS * q;
+  for (int i = 0; i < NI; ++i)
 #pragma unroll
-    for (int i = 0; i < REG_ROWS; ++i) {
-      const int r = lane + 32 * i;
-      a[q][i] = (c < n && r < m) ? A[(int64_t)c * it.lda + r] : T(0);
+    for (int e = 0; e < 4; ++e) {
+      const int r = 32 * i + 4 * s + e;
+      a[i][e] = (c < n && r < m) ? A[r] : T(0);
     }
-  }
+  if (warp == 0) publish<T, NI>(a, W, alp, 0, s, g == 0);
   for (int j = 0; j < n; ++j) {
-    const int ow = j % REG_WARPS, qj = j / REG_WARPS;
-    if (warp == ow) {
-      T alpha = T(0), s2 = T(0);
-#pragma unroll
-      for (int q = 0; q < CPW; ++q) {
-        if (q != qj) continue;
-#pragma unroll
-        for (int i = 0; i < REG_ROWS; ++i) {
-          const int r = lane + 32 * i;
-          if (r == j) alpha = a[q][i];
-          if (r > j) s2 += a[q][i] * a[q][i];
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {  // both sums in one butterfly; one lane holds alpha, the others 0
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
-      }
-      T tj = T(0), beta = alpha, scale = T(0);
-      if (s2 != T(0)) {
-        const T nrm = sqrt(alpha * alpha + s2);
-        beta = (alpha <= T(0)) ? nrm : -nrm;
-        tj = (beta - alpha) / beta;
-        scale = T(1) / (alpha - beta);
-      }
-#pragma unroll
-      for (int q = 0; q < CPW; ++q) {
-        if (q != qj) continue;
-#pragma unroll
-        for (int i = 0; i < REG_ROWS; ++i) {
-          const int r = lane + 32 * i;
-          const T v = (r < j) ? T(0) : (r == j ? T(1) : a[q][i] * scale);
-          V[(int64_t)j * MR + r] = v;
-          if (r == j) a[q][i] = beta;
-          else if (r > j) a[q][i] = T(0);
-        }
-      }
-      if (lane == 0) tau[j] = tj;
-    }
     __syncthreads();
-    const T tj = tau[j];
-    const int q0 = (j - warp + REG_WARPS) / REG_WARPS;  // first owned column right of j (j - warp + 16 >= 1)
-    if (tj != T(0) && q0 < CPW) qr_apply_reflector<T, CPW>(a, V + (int64_t)j * MR, tj, q0, lane);
+    if (4 * warp + 3 < j) continue;  // every column of this warp is finished
+    const T *wj = W + (int64_t)j * REG_MR;
+    // one pass over w_j: ||w_j||^2 and w_j^T a
+    T v[KEEP ? NI : 1][4];
+    T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
+    T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      T x[4];
+      ld4(wj + 32 * i + 4 * s, x);
+      q0 += x[0] * x[0];
+      q1 += x[1] * x[1];
+      q2 += x[2] * x[2];
+      q3 += x[3] * x[3];
+      d0 += x[0] * a[i][0];
+      d1 += x[1] * a[i][1];
+      d2 += x[2] * a[i][2];
+      d3 += x[3] * a[i][3];
+      if (KEEP) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[KEEP ? i : 0][e] = x[e];
+      }
+    }
+    const T s2 = group_sum((q0 + q1) + (q2 + q3));
+    const T sw = group_sum((d0 + d1) + (d2 + d3));
+    const T aj = group_sum(row_of<T, NI>(a, j, s));
+    // the reflector of column j, formed by every warp from the same sums
+    const T alpha = alp[j];
+    T tj = T(0), beta = alpha, sc = T(0);
+    if (s2 != T(0)) {
+      const T nrm = sqrt(alpha * alpha + s2);
+      beta = (alpha <= T(0)) ? nrm : -nrm;
+      tj = (beta - alpha) / beta;
+      sc = T(1) / (alpha - beta);
+    }
+    if (c == j) {  // the owner: R(j, j) = beta; rows below j are not read again
+#pragma unroll
+      for (int i = 0; i < 2 && i < NI; ++i)
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (32 * i + 4 * s + e == j) a[i][e] = beta;
+      if (s == 0) {
+        tau[j] = tj;
+        scl[j] = sc;
+      }
+    }
+    if (c > j && tj != T(0)) {  // H_j on the columns right of j: a -= tau (a_j + scl w^T a) [e_j + scl w]
+      const T d = tj * (aj + sc * sw);
+      const T ds = d * sc;
+      row_sub<T, NI>(a, j, s, d);
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        T x[4];
+        if (KEEP) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) x[e] = v[KEEP ? i : 0][e];
+        } else {
+          ld4(wj + 32 * i + 4 * s, x);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) a[i][e] -= ds * x[e];
+      }
+    }
+    if (j + 1 < n && warp == ((j + 1) >> 2))  // the owner warp of column j+1 publishes w_{j+1}
+      publish<T, NI>(a, W + (int64_t)(j + 1) * REG_MR, alp + j + 1, j + 1, s, g == ((j + 1) & 3));
   }
+  __syncthreads();
   // R (n x n upper triangular) from the registers
-  T *R = static_cast<T *>(it.R);
+  T *R = static_cast<T *>(it.R) + (int64_t)c * it.ldr;
+  if (c < n) {
 #pragma unroll
-  for (int q = 0; q < CPW; ++q) {
-    const int c = warp + REG_WARPS * q;
-    if (c >= n) continue;
+    for (int i = 0; i < 2 && i < NI; ++i)
 #pragma unroll
-    for (int i = 0; i < REG_ROWS; ++i) {
-      const int r = lane + 32 * i;
-      if (r < n) R[(int64_t)c * it.ldr + r] = (r <= c) ? a[q][i] : T(0);
-    }
+      for (int e = 0; e < 4; ++e) {
+        const int r = 32 * i + 4 * s + e;
+        if (r < n) R[r] = (r <= c) ? a[i][e] : T(0);
+      }
   }
-  // Explicit Q = H_0 H_1 ... H_{n-1} [I; 0], accumulated backwards: every
-  // warp applies H_{n-1}, ..., H_0 to its own columns of [I; 0] in registers.
-  // Column c is untouched by H_j for j > c (rows above j are zero in v_j, and
-  // column c of the partial product is e_c there), so H_j acts on c >= j only.
+  // Explicit Q = H_0 H_1 ... H_{n-1} [I; 0], accumulated backwards on the
+  // columns of [I; 0].  Column c is untouched by H_j for j > c (v_j is zero
+  // above row j, column c is e_c there), so a warp whose columns all lie
+  // left of j skips H_j.
 #pragma unroll
-  for (int q = 0; q < CPW; ++q)
+  for (int i = 0; i < NI; ++i)
 #pragma unroll
-    for (int i = 0; i < REG_ROWS; ++i) a[q][i] = (lane + 32 * i == warp + REG_WARPS * q) ? T(1) : T(0);
+    for (int e = 0; e < 4; ++e) a[i][e] = (32 * i + 4 * s + e == c) ? T(1) : T(0);
   for (int j = n - 1; j >= 0; --j) {
+    if (4 * warp + 3 < j) continue;
     const T tj = tau[j];
-    const int q0 = (j - warp + REG_WARPS - 1) / REG_WARPS;  // first owned column >= j (j - warp + 15 >= 0)
-    if (tj != T(0) && q0 < CPW) qr_apply_reflector<T, CPW>(a, V + (int64_t)j * MR, tj, q0, lane);
+    if (tj != T(0)) reg_apply<T, NI, KEEP>(a, W + (int64_t)j * REG_MR, j, tj, scl[j], true, s);
   }
-  T *Q = static_cast<T *>(it.Q);
+  T *Q = static_cast<T *>(it.Q) + (int64_t)c * it.ldq;
+  if (c < n) {
 #pragma unroll
-  for (int q = 0; q < CPW; ++q) {
-    const int c = warp + REG_WARPS * q;
-    if (c >= n) continue;
+    for (int i = 0; i < NI; ++i)
 #pragma unroll
-    for (int i = 0; i < REG_ROWS; ++i) {
-      const int r = lane + 32 * i;
-      if (r < m) Q[(int64_t)c * it.ldq + r] = a[q][i];
-    }
+      for (int e = 0; e < 4; ++e) {
+        const int r = 32 * i + 4 * s + e;
+        if (r < m) Q[r] = a[i][e];
+      }
   }
 }
 
-template <typename T, int CPW>
+template <typename T, int NW, int NI>
 cudaError_t launch_qr_reg(const QrItem *d_items, int n_items, int max_n, cudaStream_t s) {
-  const size_t smem = ((size_t)(32 * REG_ROWS + 1) * max_n + max_n) * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(qr_reg_kernel<T, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr bool kKeep = sizeof(T) * NI <= 32;  // FP32 keeps w in registers, FP64 reads it twice
+  const size_t smem = ((size_t)REG_MR * max_n + 3 * max_n) * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(qr_reg_kernel<T, NW, NI, kKeep>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  qr_reg_kernel<T, CPW><<<n_items, REG_WARPS * 32, smem, s>>>(d_items);
+  qr_reg_kernel<T, NW, NI, kKeep><<<n_items, NW * 32, smem, s>>>(d_items);
   count_launch();
   return cudaGetLastError();
 }
@@ -270,7 +380,7 @@ cudaError_t launch_qr_reg(const QrItem *d_items, int n_items, int max_n, cudaStr
 }  // namespace
 
 int qr_max_rows(int n, int elem_bytes) {
-  if (n <= 16 * 4) return 32 * REG_ROWS;  // register-resident kernel
+  if (n <= 64) return kRegRows;  // register-resident kernel
   int64_t avail = kSmemLimit - kSmemReserve - (int64_t)(n + 32) * elem_bytes;
   return (int)(avail / ((int64_t)n * elem_bytes));
 }
@@ -278,10 +388,10 @@ int qr_max_rows(int n, int elem_bytes) {
 template <typename T>
 cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  if (max_n <= 64 && max_m <= 32 * REG_ROWS) {
-    if (max_n <= 16) return launch_qr_reg<T, 1>(d_items, n_items, max_n, s);
-    if (max_n <= 32) return launch_qr_reg<T, 2>(d_items, n_items, max_n, s);
-    return launch_qr_reg<T, 4>(d_items, n_items, max_n, s);
+  if (max_n <= 64 && max_m <= kRegRows) {
+    if (max_n <= 16) return launch_qr_reg<T, 4, kRegRows / 32>(d_items, n_items, max_n, s);
+    if (max_n <= 32) return launch_qr_reg<T, 8, kRegRows / 32>(d_items, n_items, max_n, s);
+    return launch_qr_reg<T, 16, kRegRows / 32>(d_items, n_items, max_n, s);
   }
   size_t smem = ((size_t)max_m * max_n + max_n + 32) * sizeof(T);
   if (smem > (size_t)kSmemLimit) return cudaErrorInvalidValue;
