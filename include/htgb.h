@@ -188,6 +188,30 @@ ht_status ht_truncate(ht_tensor *x, const ht_trunc_opts *opts, ht_trunc_report *
  * array of count reports. */
 ht_status ht_truncate_batch(ht_tensor *const *xs, int count, const ht_trunc_opts *opts, ht_trunc_report *reports);
 
+/* CUDA graph of the hot path: out[i] = T(a[i] + c[i]) for i < count, i.e.
+ * the addition of Sec. 3.5 (Lemma "sum of two H-tensors": leaf frames side by
+ * side, transfer tensors block-diagonal) followed by the truncation of
+ * ht_truncate_batch with options opts, recorded once and replayed by
+ * ht_graph_launch without host work.
+ * a, c: count summand pairs (same d, n, dtype per pair).  out: count tensors
+ * created with capacities a[i] ranks + c[i] ranks (as ht_add_into requires);
+ * each replay overwrites them (their ranks become the truncated ranks).
+ * All tensors must use one stream, on which every replay is enqueued.  The
+ * graph borrows the tensors: they must outlive it and keep their ranks
+ * (a[i], c[i] unchanged between replays).  Its device workspace (the
+ * truncation workspace plus descriptors) is allocated here, once, and freed
+ * by ht_graph_free.  Errors: HT_EINVAL (shapes, streams, options),
+ * HT_ENOMEM, HT_ECUDA (capture or instantiation refused by the driver). */
+typedef struct ht_graph ht_graph;
+ht_status ht_graph_add_truncate(const ht_tensor *const *a, const ht_tensor *const *c, ht_tensor *const *out, int count,
+                                const ht_trunc_opts *opts, ht_graph **graph);
+/* Enqueue one replay on the tensors' stream (asynchronous). */
+ht_status ht_graph_launch(ht_graph *graph);
+/* Number of kernel nodes one replay launches. */
+ht_status ht_graph_kernels(const ht_graph *graph, int *kernels);
+/* Wait for the graph's stream, then release the graph and its workspace. */
+ht_status ht_graph_free(ht_graph *graph);
+
 /* ||X||: orthogonalizes a copy, returns ||B_D||_F (Sec. 3.4).  Synchronises. */
 ht_status ht_norm(const ht_tensor *x, double *out);
 /* Entries X[idx[e*d + 0], ..., idx[e*d + d-1]] for e < m (Sec. 3.1, eq.

@@ -459,26 +459,23 @@ bool tc_enabled() {
   return v && v[0] == '1';
 }
 
-// ext_base / ext_cap: run inside caller-provided device memory instead of
-// allocating (nothing is allocated or freed then; keep_base must be null).
-ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base, char *ext_base = nullptr, size_t ext_cap = 0) {
-  if (!P.err.empty()) return fail(HT_EUNSUPPORTED, P.err);
+// Workspace size of a plan: persistent | scratch | metadata | items.
+size_t plan_bytes(const Plan &P) {
   const size_t p_sz = (P.p_bytes + 255) & ~size_t(255);
   const size_t s_sz = (P.s_peak + 255) & ~size_t(255);
   const size_t m_off = p_sz + s_sz;
   const size_t i_off = m_off + ((P.meta.size() + 255) & ~size_t(255));
-  const size_t total = i_off + P.items.size();
-  char *base = nullptr;
-  cudaError_t e;
-  if (ext_base) {
-    if (total > ext_cap)
-      return fail(HT_ENOMEM, "the call needs " + std::to_string(total) + " bytes of device scratch; the fixed scratch holds " +
-                                 std::to_string(ext_cap) + " bytes");
-    base = ext_base;
-  } else {
-    e = cudaMallocAsync((void **)&base, std::max<size_t>(total, 256), s);
-    if (e != cudaSuccess) return fail(HT_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
-  }
+  return i_off + P.items.size();
+}
+
+// Relocate the plan's tagged pointers into the workspace at base and upload
+// the metadata and the work items (stream-ordered copies from host memory
+// that stays alive in P).
+ht_status prepare_plan(Plan &P, cudaStream_t s, char *base, char **ib_dev_out) {
+  const size_t p_sz = (P.p_bytes + 255) & ~size_t(255);
+  const size_t s_sz = (P.s_peak + 255) & ~size_t(255);
+  const size_t m_off = p_sz + s_sz;
+  const size_t i_off = m_off + ((P.meta.size() + 255) & ~size_t(255));
   char *pb = base, *sb = base + p_sz, *mb = base + m_off;
   for (Launch &L : P.launches) {
     uint8_t *ib = P.items.data() + L.off;
@@ -493,6 +490,7 @@ ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base, char *ext_base = n
     L.ranks = reloc(L.ranks, pb, sb, mb);
     L.scratch = reloc(L.scratch, pb, sb, mb);
   }
+  cudaError_t e;
   if (!P.meta.empty()) {
     e = cudaMemcpyAsync(mb, P.meta.data(), P.meta.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
@@ -502,11 +500,21 @@ ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base, char *ext_base = n
     e = cudaMemcpyAsync(ib_dev, P.items.data(), P.items.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
   }
+  *ib_dev_out = ib_dev;
+  return HT_OK;
+}
+
+// Enqueue the plan's kernels (items already at ib_dev).  Returns the number
+// of kernel launches through n_kernels.
+ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n_kernels) {
   const bool f64 = (P.dtype == HT_F64);
+  int kernels = 0;
   for (const Launch &L : P.launches) {
     if (L.n == 0) continue;
     const void *items = ib_dev + L.off;
     const int *rk = static_cast<const int *>(L.ranks);
+    const int64_t before = g_launches;
+    cudaError_t e = cudaSuccess;
     prof_begin((int)L.kind, s);
     switch (L.kind) {
       case L_GEMM: {
@@ -529,16 +537,45 @@ ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base, char *ext_base = n
       case L_RANKS: e = launch_ranks((const RankItem *)items, L.n, s); break;
     }
     prof_end((int)L.kind, s, L.flops);
-    if (e != cudaSuccess) {
-      if (!ext_base) cudaFreeAsync(base, s);
-      return fail(HT_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
-    }
+    kernels += (int)(g_launches - before);
+    if (e != cudaSuccess) return fail(HT_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+  }
+  if (n_kernels) *n_kernels = kernels;
+  return HT_OK;
+}
+
+// Execute a plan on a stream: allocate the workspace, relocate, upload,
+// launch.  The workspace is released in stream order after the last launch.
+// keep_base receives the workspace base (so that callers can read results)
+// and the caller frees it with cudaFreeAsync; if keep_base is null,
+// everything is freed here.  ext_base / ext_cap: run inside caller-provided
+// device memory instead of allocating (nothing is allocated or freed then;
+// keep_base must be null).
+ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base, char *ext_base = nullptr, size_t ext_cap = 0) {
+  if (!P.err.empty()) return fail(HT_EUNSUPPORTED, P.err);
+  const size_t total = plan_bytes(P);
+  char *base = nullptr;
+  if (ext_base) {
+    if (total > ext_cap)
+      return fail(HT_ENOMEM, "the call needs " + std::to_string(total) + " bytes of device scratch; the fixed scratch holds " +
+                                 std::to_string(ext_cap) + " bytes");
+    base = ext_base;
+  } else {
+    cudaError_t e = cudaMallocAsync((void **)&base, std::max<size_t>(total, 256), s);
+    if (e != cudaSuccess) return fail(HT_ENOMEM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+  }
+  char *ib_dev = nullptr;
+  ht_status st = prepare_plan(P, s, base, &ib_dev);
+  if (st == HT_OK) st = enqueue_plan(P, s, ib_dev, nullptr);
+  if (st != HT_OK) {
+    if (!ext_base) cudaFreeAsync(base, s);
+    return st;
   }
   if (ext_base) return HT_OK;
   if (keep_base) {
     *keep_base = base;
   } else {
-    e = cudaFreeAsync(base, s);
+    cudaError_t e = cudaFreeAsync(base, s);
     if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
   }
   return HT_OK;
@@ -1687,17 +1724,19 @@ static ht_status add_check(const ht_tensor *a, const ht_tensor *c) {
   return HT_OK;
 }
 
-static ht_status add_pack(const ht_tensor *a, const ht_tensor *c, ht_tensor *o) {
+// Descriptor of the addition packing: 12 int64 per node (kind, the three
+// slot offsets, shapes of the two summands, element count of the sum).
+static std::vector<int64_t> add_desc(const ht_tensor *a, const ht_tensor *c, const ht_tensor *o, int64_t *max_e) {
   const ht_tree &T = a->tr;
   std::vector<int64_t> desc(12 * (size_t)T.nn, 0);
-  int64_t max_e = 0;
+  *max_e = 0;
   for (int t = 0; t < T.nn; ++t) {
     int64_t *ds = &desc[12 * (size_t)t];
     ds[1] = a->slot[t];
     ds[2] = c->slot[t];
     ds[3] = o->slot[t];
     ds[11] = node_elems(T, o->n, o->k, t);
-    max_e = std::max(max_e, ds[11]);
+    *max_e = std::max(*max_e, ds[11]);
     if (is_leaf(T, t)) {
       ds[0] = 0;
       ds[4] = a->n[T.lo[t]];
@@ -1713,14 +1752,25 @@ static ht_status add_pack(const ht_tensor *a, const ht_tensor *c, ht_tensor *o) 
       ds[10] = c->k[T.s2[t]];
     }
   }
+  return desc;
+}
+
+static cudaError_t add_launch(const ht_tensor *a, const ht_tensor *c, ht_tensor *o, const int64_t *d_desc, int64_t max_e,
+                              cudaStream_t s) {
+  prof_begin(HT_K_ADD, s);
+  cudaError_t e = (a->dtype == HT_F64) ? launch_pack_add<double>(a->arena, c->arena, o->arena, d_desc, a->tr.nn, max_e, s)
+                                       : launch_pack_add<float>(a->arena, c->arena, o->arena, d_desc, a->tr.nn, max_e, s);
+  prof_end(HT_K_ADD, s, 0.0);
+  return e;
+}
+
+static ht_status add_pack(const ht_tensor *a, const ht_tensor *c, ht_tensor *o) {
+  int64_t max_e = 0;
+  std::vector<int64_t> desc = add_desc(a, c, o, &max_e);
   int64_t *d_desc = nullptr;
   HT_CU(cudaMallocAsync((void **)&d_desc, desc.size() * sizeof(int64_t), o->stream));
   HT_CU(cudaMemcpyAsync(d_desc, desc.data(), desc.size() * sizeof(int64_t), cudaMemcpyHostToDevice, o->stream));
-  prof_begin(HT_K_ADD, o->stream);
-  cudaError_t e = (a->dtype == HT_F64)
-                      ? launch_pack_add<double>(a->arena, c->arena, o->arena, d_desc, T.nn, max_e, o->stream)
-                      : launch_pack_add<float>(a->arena, c->arena, o->arena, d_desc, T.nn, max_e, o->stream);
-  prof_end(HT_K_ADD, o->stream, 0.0);
+  cudaError_t e = add_launch(a, c, o, d_desc, max_e, o->stream);
   if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
   HT_CU(cudaFreeAsync(d_desc, o->stream));
   return HT_OK;
@@ -1915,6 +1965,193 @@ ht_status ht_truncate(ht_tensor *x, const ht_trunc_opts *opts, ht_trunc_report *
 
 ht_status ht_truncate_batch(ht_tensor *const *xs, int count, const ht_trunc_opts *opts, ht_trunc_report *reports) {
   return truncate_many(xs, count, opts, reports);
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graph of addition + truncation (replayed without host work)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct ht_graph {
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  char *work = nullptr;  // plan workspace, addition descriptors, rank vectors
+  std::vector<ht_tensor *> outs;
+  int kernels = 0;
+};
+
+static void graph_destroy(ht_graph *g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->work) cudaFree(g->work);
+  delete g;
+}
+
+extern "C" {
+
+ht_status ht_graph_add_truncate(const ht_tensor *const *a, const ht_tensor *const *c, ht_tensor *const *out, int count,
+                                const ht_trunc_opts *o, ht_graph **gout) {
+  if (!a || !c || !out || count < 1 || !o || !gout) return fail(HT_EINVAL, "null argument");
+  *gout = nullptr;
+  if (o->mode != HT_TRUNC_RANK && o->mode != HT_TRUNC_EPS) return fail(HT_EINVAL, "bad mode");
+  if (o->mode == HT_TRUNC_EPS && !(o->eps >= 0.0)) return fail(HT_EINVAL, "eps must be >= 0");
+  if (count > 1 && o->ranks) return fail(HT_EINVAL, "per-node target ranks are only accepted for a single tensor");
+  cudaStream_t s = out[0] ? out[0]->stream : nullptr;
+  for (int i = 0; i < count; ++i) {
+    HT_TRY(add_check(a[i], c[i]));
+    ht_tensor *x = out[i];
+    if (!x) return fail(HT_EINVAL, "null output");
+    if (x->stream != s || a[i]->stream != s || c[i]->stream != s)
+      return fail(HT_EINVAL, "all tensors of a graph must use one stream");
+    if (x->tr.d != a[i]->tr.d || x->dtype != a[i]->dtype || x->dtype != out[0]->dtype)
+      return fail(HT_EINVAL, "output does not match");
+    for (int m = 0; m < x->tr.d; ++m)
+      if (x->n[m] != a[i]->n[m]) return fail(HT_EINVAL, "output mode sizes do not match");
+    HT_TRY(check_prec(x, o->prec));
+    HT_TRY(sync_ranks(const_cast<ht_tensor *>(a[i])));
+    HT_TRY(sync_ranks(const_cast<ht_tensor *>(c[i])));
+    for (int t = 1; t < x->tr.nn; ++t)
+      if (x->cap[t] != a[i]->k[t] + c[i]->k[t]) return fail(HT_EINVAL, "output capacity must equal k + kbar");
+  }
+  // the outputs take the ranks of the sums; the plan is built for them
+  for (int i = 0; i < count; ++i) {
+    ht_tensor *x = out[i];
+    HT_TRY(sync_ranks(x));
+    x->k = x->cap;
+    x->k[0] = 1;
+    x->orthogonal = false;
+    HT_TRY(upload_ranks(x));
+  }
+  Plan P;
+  P.dtype = out[0]->dtype;
+  P.esz = (P.dtype == HT_F64) ? 8 : 4;
+  P.node_sched = (o->schedule == HT_SCHED_NODE);
+  std::vector<TState> TS(count);
+  int total_nodes = 0;
+  for (int i = 0; i < count; ++i) {
+    TS[i].x = out[i];
+    TS[i].node_base = total_nodes;
+    total_nodes += out[i]->tr.nn;
+  }
+  int *rank_array = P.palloc<int>((size_t)total_nodes);
+  for (int i = 0; i < count; ++i) TS[i].r = rank_array + TS[i].node_base;
+  plan_orthogonalize(P, TS);
+  plan_gramians(P, TS, nullptr);
+  plan_eig_ranks(P, TS, *o, rank_array);
+  plan_project(P, TS, rank_array);
+  if (!P.err.empty()) return fail(HT_EUNSUPPORTED, P.err);
+  // one device buffer: plan workspace | per tensor: addition descriptor, sum ranks
+  const size_t plan_sz = (plan_bytes(P) + 255) & ~size_t(255);
+  std::vector<size_t> desc_off(count), rk_off(count);
+  std::vector<int64_t> max_e(count);
+  std::vector<std::vector<int64_t>> descs(count);
+  size_t total = plan_sz;
+  for (int i = 0; i < count; ++i) {
+    descs[i] = add_desc(a[i], c[i], out[i], &max_e[i]);
+    desc_off[i] = total;
+    total += (descs[i].size() * sizeof(int64_t) + 255) & ~size_t(255);
+    rk_off[i] = total;
+    total += (out[i]->tr.nn * sizeof(int) + 255) & ~size_t(255);
+  }
+  ht_graph *g = new ht_graph();
+  g->stream = s;
+  g->outs.assign(out, out + count);
+  cudaError_t e = cudaMalloc((void **)&g->work, total);
+  if (e != cudaSuccess) {
+    graph_destroy(g);
+    return fail(HT_ENOMEM, std::string("graph workspace allocation failed: ") + cudaGetErrorString(e));
+  }
+  char *ib_dev = nullptr;
+  ht_status st = prepare_plan(P, s, g->work, &ib_dev);
+  for (int i = 0; i < count && st == HT_OK; ++i) {
+    e = cudaMemcpyAsync(g->work + desc_off[i], descs[i].data(), descs[i].size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g->work + rk_off[i], out[i]->k.data(), out[i]->tr.nn * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) st = fail(HT_ECUDA, cudaGetErrorString(e));
+  }
+  if (st == HT_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = fail(HT_ECUDA, cudaGetErrorString(e));
+  if (st != HT_OK) {
+    graph_destroy(g);
+    return st;
+  }
+  // capture (on a private stream: the tensors' stream may be the legacy
+  // default stream, which cannot be captured): per tensor the rank reset and
+  // the addition, then the truncation plan, then the new ranks into every
+  // output's rank vector.  Replays are launched on the tensors' stream.
+  const cudaStream_t tensor_stream = s;
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    graph_destroy(g);
+    return fail(HT_ECUDA, std::string("stream creation failed: ") + cudaGetErrorString(e));
+  }
+  s = cs;
+  const unsigned prof_saved = g_prof_mask;
+  g_prof_mask = 0;
+  const int64_t launches_saved = g_launches;
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    g_prof_mask = prof_saved;
+    cudaStreamDestroy(cs);
+    graph_destroy(g);
+    return fail(HT_ECUDA, std::string("stream capture failed: ") + cudaGetErrorString(e));
+  }
+  for (int i = 0; i < count && st == HT_OK; ++i) {
+    ht_tensor *x = out[i];
+    e = cudaMemcpyAsync(x->d_ranks, g->work + rk_off[i], x->tr.nn * sizeof(int), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = add_launch(a[i], c[i], x, reinterpret_cast<const int64_t *>(g->work + desc_off[i]), max_e[i], s);
+    if (e != cudaSuccess) st = fail(HT_ECUDA, cudaGetErrorString(e));
+  }
+  if (st == HT_OK) st = enqueue_plan(P, s, ib_dev, nullptr);
+  const int *d_r = reinterpret_cast<const int *>(reloc(rank_array, g->work, nullptr, nullptr));
+  for (int i = 0; i < count && st == HT_OK; ++i) {
+    e = cudaMemcpyAsync(out[i]->d_ranks, d_r + TS[i].node_base, sizeof(int) * out[i]->tr.nn, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) st = fail(HT_ECUDA, cudaGetErrorString(e));
+  }
+  e = cudaStreamEndCapture(s, &g->graph);
+  g->kernels = (int)(g_launches - launches_saved);
+  g_launches = launches_saved;
+  g_prof_mask = prof_saved;
+  cudaStreamDestroy(cs);
+  s = tensor_stream;
+  if (st == HT_OK && e != cudaSuccess) st = fail(HT_ECUDA, std::string("stream capture failed: ") + cudaGetErrorString(e));
+  if (st == HT_OK && (e = cudaGraphInstantiate(&g->exec, g->graph, 0)) != cudaSuccess)
+    st = fail(HT_ECUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
+  if (st != HT_OK) {
+    graph_destroy(g);
+    return st;
+  }
+  for (ht_tensor *x : g->outs) x->ranks_ok = false;
+  *gout = g;
+  return HT_OK;
+}
+
+ht_status ht_graph_launch(ht_graph *g) {
+  if (!g) return fail(HT_EINVAL, "null graph");
+  cudaError_t e = cudaGraphLaunch(g->exec, g->stream);
+  if (e != cudaSuccess) return fail(HT_ECUDA, std::string("graph launch failed: ") + cudaGetErrorString(e));
+  g_launches += g->kernels;
+  for (ht_tensor *x : g->outs) {
+    x->ranks_ok = false;
+    x->orthogonal = false;
+  }
+  return HT_OK;
+}
+
+ht_status ht_graph_kernels(const ht_graph *g, int *kernels) {
+  if (!g || !kernels) return fail(HT_EINVAL, "null argument");
+  *kernels = g->kernels;
+  return HT_OK;
+}
+
+ht_status ht_graph_free(ht_graph *g) {
+  if (!g) return HT_OK;
+  cudaError_t e = cudaStreamSynchronize(g->stream);
+  graph_destroy(g);
+  if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  return HT_OK;
 }
 
 ht_status ht_norm(const ht_tensor *xc, double *out) {

@@ -33,6 +33,7 @@ EXPORTS = [
     "ht_add", "ht_add_into", "ht_orthogonalize", "ht_gramians", "ht_truncate",
     "ht_truncate_batch", "ht_norm", "ht_eval_entries", "ht_last_error",
     "ht_profile_set", "ht_profile_read", "ht_launch_count", "ht_gramians_noalloc",
+    "ht_graph_add_truncate", "ht_graph_launch", "ht_graph_kernels", "ht_graph_free",
 ]
 HT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 HT_K_GEMM, HT_K_QR, HT_K_EIG, HT_K_COPY, HT_K_COMPACT, HT_K_RANKS, HT_K_ADD, HT_K_EVAL, HT_K_MISC = range(9)
@@ -113,6 +114,11 @@ def load(build_if_missing: bool = True):
             "ht_profile_read": ([ctypes.c_int, i64p, f64p, f64p, ctypes.c_int], ctypes.c_int),
             "ht_launch_count": ([i64p], ctypes.c_int),
             "ht_gramians_noalloc": ([vp, vp, ctypes.c_int], ctypes.c_int),
+            "ht_graph_add_truncate": ([ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
+                                       ctypes.POINTER(TruncOpts), ctypes.POINTER(vp)], ctypes.c_int),
+            "ht_graph_launch": ([vp], ctypes.c_int),
+            "ht_graph_kernels": ([vp, i32p], ctypes.c_int),
+            "ht_graph_free": ([vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -266,6 +272,31 @@ def ht_truncate_batch(xs, opts: TruncOpts, report: bool = False):
     return [dict(norm=r.norm, discarded_sq=r.discarded_sq, bound=r.bound) for r in reps]
 
 
+def ht_graph_add_truncate(a, c, out, opts: TruncOpts):
+    """Record out[i] = T(a[i] + c[i]) as one CUDA graph; returns its handle."""
+    n = len(out)
+    if len(a) != n or len(c) != n:
+        raise ValueError("a, c and out must have the same length")
+    arr = lambda hs: (ctypes.c_void_p * n)(*hs)
+    g = ctypes.c_void_p()
+    _check(load().ht_graph_add_truncate(arr(a), arr(c), arr(out), n, ctypes.byref(opts), ctypes.byref(g)))
+    return g.value
+
+
+def ht_graph_launch(g):
+    _check(load().ht_graph_launch(g))
+
+
+def ht_graph_kernels(g) -> int:
+    k = ctypes.c_int()
+    _check(load().ht_graph_kernels(g, ctypes.byref(k)))
+    return k.value
+
+
+def ht_graph_free(g):
+    _check(load().ht_graph_free(g))
+
+
 def ht_norm(x) -> float:
     v = ctypes.c_double()
     _check(load().ht_norm(x, ctypes.byref(v)))
@@ -350,6 +381,10 @@ class HTTensor:
 
     def add(self, other: "HTTensor") -> "HTTensor":
         return HTTensor(self.tree, ht_add(self.handle, other.handle), self.n, self.dtype)
+
+    def add_into(self, a: "HTTensor", c: "HTTensor"):
+        """self = a + c (self created with capacities a.ranks + c.ranks)."""
+        ht_add_into(a.handle, c.handle, self.handle)
 
     def orthogonalize(self, prec=None):
         ht_orthogonalize(self.handle, self.default_prec() if prec is None else prec)
