@@ -1,17 +1,27 @@
 #!/usr/bin/env python3
 """HT truncation throughput on GB300: HT addition + HSVD truncation per step.
 
-One step = ht_add (Lemma "sum of two H-tensors") of two seeded HT tensors
-followed by ht_truncate (orthogonalization, reduced Gramians, FP64
-eigendecompositions, rank selection, projection).  Default workload: d=64,
-n=1000, k=32 (rank 64 after the addition), orthonormalised Gaussian leaves,
-transfer tensors with mode weights sigma_j = 10^(-8j/32), truncation to
-relative eps = 1e-8 with rank cap 32.
+One step = ht_add (Lemma "sum of two H-tensors") of seeded HT tensor pairs
+followed by the truncation of each sum (orthogonalization, reduced Gramians,
+FP64 eigendecompositions, rank selection, projection), replayed as one CUDA
+graph (ht_graph_add_truncate / ht_graph_launch).  Workloads (--config):
+
+  single   d=64, n=1000, k=32 -> rank 64, orthonormal Gaussian leaves,
+           sigma_j = 10^(-8j/32), eps = 1e-8 relative, rank cap 32 (default)
+  small    256 pairs of d=8, n=32, k=8 -> rank 16, Gaussian leaves,
+           sigma_j = 2^-j, truncated to rank 8
+  batched  a wave of uneven tensors, d~U{4..32}, n~U{16..512}, k~U{4..48},
+           each the sum of 4 tensors (sigma_j = 2^-j) truncated to its own k
+  deep     d=256, n=4096, k=64 -> rank 128, Gaussian leaves,
+           sigma_j = 10^(-10j/64), eps = 1e-6 relative
+  wide     8 pairs of d=16, n=2048, k=128 -> rank 256, orthonormal leaves,
+           sigma_j = j^-2, truncated to rank 128
 
 Arms:
-  default            the GB300 library (FP32 storage/contractions + FP64
-                     eigensolves, batched per tree level), with the plain FP64
-                     path (per level and one launch per node) timed beside it
+  default            the GB300 library (FP32 storage and contractions, FP64
+                     eigensolves, one batched launch per tree level); for
+                     `single` the plain FP64 path (per level and one launch per
+                     node) is timed beside it
   --impl reference   the CPU FP64 oracle on the host cores (rank 0 only)
 
 Multi-GPU (torchrun): every rank truncates its own tensors (independent
@@ -21,7 +31,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -35,28 +44,84 @@ sys.path.insert(0, ROOT)
 
 from paper_1708_03340_gb300 import inputs as I  # noqa: E402
 
-WORKLOADS = {
-    "single": dict(d=64, n=1000, k=32, make=I.single_pair, opts=I.SINGLE_OPTS,
-                   desc="d=64, n=1000, k=32 -> rank 64 after the addition, orthonormal Gaussian leaves, "
-                        "sigma_j=10^(-8j/32), eps=1e-8 relative, rank cap 32"),
-    "small": dict(d=8, n=32, k=8, make=I.small_pair, opts=dict(mode="rank", rank_cap=8),
-                  desc="d=8, n=32, k=8 -> rank 16, Gaussian leaves, sigma_j=2^-j, truncated to rank 8"),
-    "deep": dict(d=256, n=4096, k=64, make=I.deep_pair, opts=I.DEEP_OPTS,
-                 desc="d=256, n=4096, k=64 -> rank 128, Gaussian leaves, sigma_j=10^(-10j/64), eps=1e-6 relative"),
-}
 METRIC = "HT truncations/s + roofline fraction, mixed vs plain FP64 GPU at stated rel err"
 FP64_PEAK = 152 * 2 * 2 * 2.070e9   # SMs x FP64 FMA/clk/SM x 2 flop x max clock (recipe: 1.25 TFLOP/s)
-FP32_PEAK = 152 * 128 * 2 * 2.070e9  # SMs x FP32 lanes x 2 flop x max clock
+FP32_PEAK = 152 * 128 * 2 * 2.070e9  # SMs x FP32 lanes x 2 flop x max clock (80.5 TFLOP/s)
+
+
+# ---------------------------------------------------------------------------
+# workloads: each yields, per rank, a list of pairs (d, n, (ka, xa), (kc, xc), cap)
+# ---------------------------------------------------------------------------
+
+def _pairs_single(rank, args):
+    (n, ka, xa), (_, kc, xc) = I.single_pair(11 + 1000 * rank)
+    return [(64, n, (ka, xa), (kc, xc), 32)]
+
+
+def _pairs_small(rank, args):
+    out = []
+    for i in range(args.pairs or 256):
+        (n, ka, xa), (_, kc, xc) = I.small_pair(1 + 2 * i + 100000 * rank)
+        out.append((8, n, (ka, xa), (kc, xc), 8))
+    return out
+
+
+def _pairs_deep(rank, args):
+    (n, ka, xa), (_, kc, xc) = I.deep_pair(21 + 1000 * rank)
+    return [(256, n, (ka, xa), (kc, xc), 0)]
+
+
+def _pairs_wide(rank, args):
+    out = []
+    for i in range(args.pairs or 8):
+        (n, ka, xa), (_, kc, xc) = I.wide_pair(31 + 2 * i + 1000 * rank)
+        out.append((16, n, (ka, xa), (kc, xc), 128))
+    return out
+
+
+def _batched_specs(rank, args):
+    wave = args.pairs or 64
+    specs = I.batched_specs(count=4096, seed=41)
+    return [specs[(rank * wave + i) % len(specs)] for i in range(wave)]
+
+
+WORKLOADS = {
+    "single": dict(pairs=_pairs_single, opts=I.SINGLE_OPTS,
+                   desc="d=64, n=1000, k=32 -> rank 64 after the addition, orthonormal Gaussian leaves, "
+                        "sigma_j=10^(-8j/32), eps=1e-8 relative, rank cap 32"),
+    "small": dict(pairs=_pairs_small, opts=dict(mode="rank", rank_cap=8),
+                  desc="pairs of d=8, n=32, k=8 -> rank 16, Gaussian leaves, sigma_j=2^-j, truncated to rank 8"),
+    "batched": dict(pairs=None, opts=dict(mode="rank"),
+                    desc="uneven tensors d~U{4..32}, n~U{16..512}, k~U{4..48}, each the sum of 4 tensors "
+                         "(Gaussian leaves, sigma_j=2^-j, rank 4k) truncated to its own k"),
+    "deep": dict(pairs=_pairs_deep, opts=I.DEEP_OPTS,
+                 desc="d=256, n=4096, k=64 -> rank 128, Gaussian leaves, sigma_j=10^(-10j/64), eps=1e-6 relative"),
+    "wide": dict(pairs=_pairs_wide, opts=I.WIDE_OPTS,
+                 desc="pairs of d=16, n=2048, k=128 -> rank 256, orthonormal Gaussian leaves, sigma_j=j^-2, "
+                      "truncated to rank 128"),
+}
+
+# DRAM bytes per launch of the dominant kernel family on the default workload,
+# from the committed ncu launch list (profiles/); None when not captured for
+# the current kernels.
+TRAFFIC_PER_LAUNCH = {}
 
 
 def model_flops(d, n, K, r):
-    """Algorithmic work of one truncation (SURVEY work model): 12 K^4 per
-    non-root inner node + n K (K + 2r) per leaf; eigen counted separately
-    (9 K^3 per non-root node)."""
+    """Algorithmic work of one truncation: 12 K^4 per non-root inner node +
+    n K (K + 2r) per leaf; eigen counted separately (9 K^3 per non-root node)."""
     inner = (d - 2) * 12.0 * K ** 4
     leaves = d * n * K * (K + 2 * r)
     eig = (2 * d - 2) * 9.0 * K ** 3
     return inner + leaves, eig
+
+
+def job_value(local_ms, tensors_per_step, steps, ws, reduce_max):
+    """Whole-job throughput of a weak-scaled run: every rank truncates its own
+    tensors_per_step tensors per step; the job's time is the slowest rank's
+    (reduce_max: max over ranks).  Returns (truncations/s, job ms)."""
+    ms = reduce_max(local_ms)
+    return ws * tensors_per_step * steps / (ms / 1e3), ms
 
 
 def dist_env():
@@ -109,41 +174,356 @@ def read_clocks(proc, f, path, gpu_index):
             "samples": len(mhz)}
 
 
-def oracle_truncations(wl, seed, count, threads=0):
-    """Run the CPU oracle on `count` add+truncate steps; returns (seconds, cores)."""
+# ---------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(config, rank, args):
+    """A bounded sample of the workload for the CPU oracle: a list of
+    (d, n, (ka, xa), (kc, xc), opts) summand pairs, its description, and the
+    number of workload tensors one pass over it stands for."""
     from oracle import oracle as O
-    cores = O.set_threads(threads)
-    (n, ka, xa), (_, kc, xc) = wl["make"](seed)
-    d = wl["d"]
+    wl = WORKLOADS[config]
+    items = []
+    if config == "batched":
+        # tensors of the wave in order, skipping those above twice the mean
+        # modelled cost, until about 15 GFLOP; the rate is rescaled to the
+        # wave's mean tensor by modelled flops
+        wave = _batched_specs(rank, args)
+        cost = lambda sp: model_flops(sp[0], sp[1], 4 * sp[2], sp[2])[0]
+        mean = float(np.mean([cost(sp) for sp in wave]))
+        picked, total = [], 0.0
+        for sp in wave:
+            if cost(sp) <= 2 * mean:
+                picked.append(sp)
+                total += cost(sp)
+            if total >= 15e9 or len(picked) == 4:
+                break
+        for (d, n, k, s) in picked:
+            terms = I.batched_terms((d, n, k, s))
+            nv = terms[0][0]
+            a = O.add(d, nv, terms[0][1], terms[0][2], terms[1][1], terms[1][2])
+            c = O.add(d, nv, terms[2][1], terms[2][2], terms[3][1], terms[3][2])
+            items.append((d, nv, a, c, dict(mode="rank", rank_cap=k)))
+        desc = (f"{len(picked)} tensors of the batched wave ((d, n, k) = {[sp[:3] for sp in picked]}, each "
+                f"(T1+T2)+(T3+T4), add + truncate, FP64), rate rescaled to the wave's mean tensor by modelled flops")
+        return items, desc, total / mean
+    for (d, n, (ka, xa), (kc, xc), cap) in wl["pairs"](rank, argparse.Namespace(pairs=1))[:1]:
+        items.append((d, n, (ka, xa), (kc, xc), wl["opts"]))
+    return items, "1 add + truncate of the workload's first pair, FP64", float(len(items))
+
+
+def oracle_time(items, reps):
+    """Seconds for `reps` passes of add + truncate over the sample."""
+    from oracle import oracle as O
     t0 = time.perf_counter()
-    for _ in range(count):
-        k, x = O.add(d, n, ka, xa, kc, xc)
-        O.truncate(d, n, k, x, **wl["opts"])
-    return time.perf_counter() - t0, cores
+    for _ in range(reps):
+        for (d, n, (ka, xa), (kc, xc), opts) in items:
+            k, x = O.add(d, n, ka, xa, kc, xc)
+            O.truncate(d, n, k, x, **opts)
+    return time.perf_counter() - t0
 
 
-def accuracy_vs_fp64(htgb, tree, n, ka, xa, kc, xc, wl, stream):
+def run_reference(args):
+    from oracle import oracle as O
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cores = O.set_threads(0)
+    items, sample, equiv = oracle_sample(args.config, 0, args)
+    for _ in range(args.warmup):
+        oracle_time(items, 1)
+    secs = oracle_time(items, args.steps)
+    value = args.steps * equiv / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "truncations/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.config, "shape": WORKLOADS[args.config]["desc"]},
+        "cpu_baseline": {"value": value, "unit": "truncations/s", "cores": cores, "kind": "oracle",
+                         "sample": f"each step: {sample}"},
+        "e2e": {"value": value, "unit": "truncations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arms
+# ---------------------------------------------------------------------------
+
+def build_pairs(htgb, config, rank, args, dtype, stream):
+    """Device tensors: summands A_i, C_i and outputs X_i (capacity = sum of ranks);
+    returns (trees, A, C, X, caps, shapes) with shapes (d, n, K) per output."""
+    trees, A, C, X, caps, shapes = {}, [], [], [], [], []
+    if config == "batched":
+        for (d, n, k, s) in _batched_specs(rank, args):
+            tr = trees.setdefault(d, htgb.HTTree(d))
+            T = [htgb.HTTensor.from_blob(tr, nv, kv, xv, dtype, stream) for (nv, kv, xv) in I.batched_terms((d, n, k, s))]
+            A.append(T[0].add(T[1]))
+            C.append(T[2].add(T[3]))
+            caps.append(k)
+            shapes.append((d, n, 4 * k))
+    else:
+        for (d, n, (ka, xa), (kc, xc), cap) in WORKLOADS[config]["pairs"](rank, args):
+            tr = trees.setdefault(d, htgb.HTTree(d))
+            A.append(htgb.HTTensor.from_blob(tr, n, ka, xa, dtype, stream))
+            C.append(htgb.HTTensor.from_blob(tr, n, kc, xc, dtype, stream))
+            caps.append(cap)
+            shapes.append((d, int(np.asarray(n).flat[0]), int(np.max(ka)) + int(np.max(kc))))
+    for a, c in zip(A, C):
+        k = np.asarray(a.ranks()) + np.asarray(c.ranks())
+        k[0] = 1
+        X.append(htgb.HTTensor.create(a.tree, a.n, k, dtype, stream))
+    return trees, A, C, X, caps, shapes
+
+
+def make_opts(htgb, config, prec, caps, sched=None):
+    kw = dict(WORKLOADS[config]["opts"])
+    if config == "batched":
+        kw["tensor_caps"] = caps
+    if sched is not None:
+        kw["schedule"] = sched
+    return htgb.make_opts(prec=prec, **kw)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="single", choices=sorted(WORKLOADS))
+    ap.add_argument("--pairs", type=int, default=0, help="tensors per step (small: 256, batched: 64, wide: 8)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison arms")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1708_03340_gb300 import htgb
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2 (129 MB)
+
+    def max_over_ranks(v):
+        if ws == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def graph_arm(dtype, prec, steps, warmup, sched=None):
+        """Timed graph replays: per step, L2 flush then one replay between CUDA events."""
+        trees, A, C, X, caps, shapes = build_pairs(htgb, args.config, rank, args, dtype, stream)
+        opts = make_opts(htgb, args.config, prec, caps, sched)
+        g = htgb.ht_graph_add_truncate([a.handle for a in A], [c.handle for c in C], [x.handle for x in X], opts)
+        for _ in range(warmup):
+            htgb.ht_graph_launch(g)
+        barrier()
+        l0 = htgb.ht_launch_count()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            htgb.ht_graph_launch(g)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        launches = htgb.ht_launch_count() - l0
+        value, ms = job_value(sum(a.elapsed_time(b) for a, b in evs), len(X), steps, ws, max_over_ranks)
+        return dict(ms=ms, value=value, launches=launches, g=g, A=A, C=C, X=X, caps=caps, shapes=shapes, opts=opts,
+                    trees=trees)
+
+    def profiled_arm(dtype, prec, steps, sched=None):
+        """Direct calls (ht_add_into + ht_truncate_batch) with per-kernel-family CUDA events."""
+        trees, A, C, X, caps, shapes = build_pairs(htgb, args.config, rank, args, dtype, stream)
+        opts = make_opts(htgb, args.config, prec, caps, sched)
+
+        def step():
+            for x, a, c in zip(X, A, C):
+                x.add_into(a, c)
+            htgb.ht_truncate_batch([x.handle for x in X], opts)
+
+        step()
+        barrier()
+        mask = (1 << len(htgb.KERNEL_KINDS)) - 1
+        htgb.ht_profile_set(mask)
+        for kind in range(len(htgb.KERNEL_KINDS)):
+            htgb.ht_profile_read(kind, reset=True)
+        l0 = htgb.ht_launch_count()
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        htgb.ht_profile_set(0)
+        prof = {}
+        for kind, name in enumerate(htgb.KERNEL_KINDS):
+            cnt, tms, fl = htgb.ht_profile_read(kind, reset=True)
+            if cnt:
+                prof[name] = {"launches": cnt, "ms": tms, "flops": fl}
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs))
+        return dict(ms=ms, launches=htgb.ht_launch_count() - l0, prof=prof, X=X)
+
+    # ---- headline: graph replays of the FP32-storage path (FP64 eigensolves)
+    clk_path = os.path.join(tempfile.gettempdir(), f"htgb_clocks_{os.getpid()}.csv")
+    proc, fh = start_clock_sampler(clk_path)
+    main_arm = graph_arm(htgb.HT_F32, htgb.HT_PREC_FP32, args.steps, args.warmup)
+    clocks = read_clocks(proc, fh, clk_path, local)
+    per_step = len(main_arm["X"])
+    value = main_arm["value"]
+    ms_per_step = main_arm["ms"] / args.steps
+    work = 0.0
+    for (d, n, K), cap in zip(main_arm["shapes"], main_arm["caps"]):
+        w, _ = model_flops(d, n, K, cap or K // 2)
+        work += w
+
+    # ---- kernel breakdown and the roofline of the dominant kernel family
+    psteps = max(2, min(args.steps, 5))
+    prof = profiled_arm(htgb.HT_F32, htgb.HT_PREC_FP32, psteps)
+    roofline = None
+    if prof["prof"]:
+        name, rec = max(prof["prof"].items(), key=lambda kv: kv[1]["ms"])
+        per_launch_ms = rec["ms"] / rec["launches"]
+        per_launch_flops = rec["flops"] / rec["launches"]
+        ach = per_launch_flops / (per_launch_ms / 1e3)
+        kernel = {"qr": "qr_reg_kernel (FP32 TSQR blocks)", "gemm": "gemm_kernel (FP32 SIMT, compensated)",
+                  "eig": "eig_ql_kernel<float> + refine_kernel (FP64)"}.get(name, name)
+        peak = FP64_PEAK if name == "eig" else FP32_PEAK
+        roofline = {"kernel": kernel, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
+                    "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": TRAFFIC_PER_LAUNCH.get((args.config, name)),
+                    "peak_source": ("FP64" if name == "eig" else "FP32") + " unit count x max SM clock (recipe)",
+                    "launches_per_step": rec["launches"] / psteps, "ms_per_launch": per_launch_ms,
+                    "flops_per_launch": per_launch_flops}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "truncations/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded SplitMix64/Box-Muller HT tensors)",
+        "config": {"workload": args.config, "tensors_per_step": per_step, "shape": WORKLOADS[args.config]["desc"],
+                   "l2": "flushed between steps (256 MB write)",
+                   "path": "FP32 storage and contractions, FP64 eigensolves, one batched launch per level, "
+                           "CUDA-graph replay"},
+        "gflops": work / (ms_per_step / 1e3) / 1e9,
+        "direct_calls_ms_per_step": prof["ms"] / psteps,
+        "kernel_ms_per_step": {k: v["ms"] / psteps for k, v in prof["prof"].items()},
+        "kernel_tflops": {k: v["flops"] / max(v["ms"], 1e-9) / 1e9 for k, v in prof["prof"].items() if v["flops"] > 0},
+        "ranks_first_nodes": [int(v) for v in main_arm["X"][0].ranks()[:8]],
+        "gpu_launches": main_arm["launches"],
+        "roofline": roofline,
+        "clocks": clocks,
+    }
+
+    # ---- plain FP64 GPU arms (default workload): per level, and one launch per node
+    if args.config == "single" and not args.no_plain:
+        ps = max(3, args.steps // 4)
+        plain = profiled_arm(htgb.HT_F64, htgb.HT_PREC_FP64, ps)
+        line["plain_fp64_level"] = {"value": ws * ps / (plain["ms"] / 1e3), "unit": "truncations/s",
+                                    "ms_per_step": plain["ms"] / ps,
+                                    "kernel_ms_per_step": {k: v["ms"] / ps for k, v in plain["prof"].items()}}
+        node = graph_arm(htgb.HT_F64, htgb.HT_PREC_FP64, 3, 3, sched=htgb.HT_SCHED_NODE)
+        line["plain_fp64_per_node"] = {"value": node["value"], "unit": "truncations/s",
+                                       "ms_per_step": node["ms"] / 3, "launches_per_step": node["launches"] / 3}
+        htgb.ht_graph_free(node["g"])
+        line["speedup_vs_plain_per_node"] = value / line["plain_fp64_per_node"]["value"]
+        line["speedup_vs_plain_level"] = value / line["plain_fp64_level"]["value"]
+        line["rel_err_vs_fp64"] = accuracy_vs_fp64(htgb, stream)
+
+    # ---- end to end through the public API: pinned host blobs in, truncated blobs out, every step
+    A, C, X, g = main_arm["A"], main_arm["C"], main_arm["X"], main_arm["g"]
+    hA = [torch.from_numpy(a.download()).pin_memory() for a in A]
+    hC = [torch.from_numpy(c.download()).pin_memory() for c in C]
+    cap_sz = []
+    for a, c in zip(A, C):  # room for the largest possible output: the capacity of the sum
+        k = np.asarray(a.ranks()) + np.asarray(c.ranks())
+        k[0] = 1
+        cap_sz.append(int(I.blob_size(a.tree.d, a.n, k)))
+    hX = [torch.empty(max(s_, 1), dtype=torch.float32).pin_memory() for s_ in cap_sz]
+    e2e_steps = max(3, args.steps // 2)
+    h2d = sum(t.numel() * 4 for t in hA + hC)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        for a, c, ha, hc in zip(A, C, hA, hC):
+            htgb.ht_tensor_upload(a.handle, ha.numpy())
+            htgb.ht_tensor_upload(c.handle, hc.numpy())
+        htgb.ht_graph_launch(g)
+        d2h = 0
+        for x, hx in zip(X, hX):
+            sz = htgb.ht_tensor_blob_size(x.handle)
+            htgb.ht_tensor_download(x.handle, hx.numpy()[:sz])
+            d2h += sz * 4
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    line["e2e"] = {"value": ws * per_step * e2e_steps / e2e_s, "unit": "truncations/s",
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    htgb.ht_graph_free(g)
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only), a bounded sample
+    if ws == 1 and not args.no_cpu:
+        from oracle import oracle as O
+        cores = O.set_threads(0)
+        items, sample, equiv = oracle_sample(args.config, 0, args)
+        secs = oracle_time(items, 1)
+        reps = 1
+        while secs * (reps + 1) / reps < 10.0 and reps < 8:  # about 10 s of CPU work
+            secs += oracle_time(items, 1)
+            reps += 1
+        line["cpu_baseline"] = {"value": reps * equiv / secs, "unit": "truncations/s", "cores": cores,
+                                "kind": "oracle", "sample": f"{reps} x {sample}, OpenMP over tree nodes"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def accuracy_vs_fp64(htgb, stream):
     """Errors of the FP32-storage path relative to the FP64 GPU path on the same
-    (FP32-representable) inputs, all computed by the library on the GPU:
-    sigma^2 normwise per node, ||X||, and ||T32(X) - T64(X)|| / ||X|| and the
-    truncation errors ||X - T(X)|| / ||X|| of both paths (norms of HT
+    (FP32-representable) inputs of the default workload, all computed by the
+    library on the GPU: sigma^2 normwise per node, ||X||, ||T32(X) - T64(X)|| / ||X||
+    and the truncation errors ||X - T(X)|| / ||X|| of both paths (norms of HT
     differences via orthogonalization, never via inner products)."""
+    (n, ka, xa), (_, kc, xc) = I.single_pair(11)
+    opts = I.SINGLE_OPTS
+    tree = htgb.HTTree(64)
     xa32 = np.asarray(xa, np.float32).astype(np.float64)
     xc32 = np.asarray(xc, np.float32).astype(np.float64)
-    out = {}
     res = {}
     for name, dt in (("fp32", htgb.HT_F32), ("fp64", htgb.HT_F64)):
         A = htgb.HTTensor.from_blob(tree, n, ka, xa32, dt, stream)
         C = htgb.HTTensor.from_blob(tree, n, kc, xc32, dt, stream)
         X = A.add(C)
-        rep = X.truncate(prec=htgb.HT_PREC_FP32 if dt == htgb.HT_F32 else htgb.HT_PREC_FP64, **wl["opts"])
+        rep = X.truncate(prec=htgb.HT_PREC_FP32 if dt == htgb.HT_F32 else htgb.HT_PREC_FP64, **opts)
         res[name] = (rep, X.ranks(), X.download().astype(np.float64))
     X64 = htgb.HTTensor.from_blob(tree, n, ka, xa32, htgb.HT_F64, stream).add(
         htgb.HTTensor.from_blob(tree, n, kc, xc32, htgb.HT_F64, stream))
     nrm = res["fp64"][0]["norm"]
 
     def diff_norm(ya, ka_, yb, kb_):
-        P = htgb.HTTensor.from_blob(tree, n, ka_, ya, htgb.HT_F64, stream) if not isinstance(ya, htgb.HTTensor) else ya
+        P = ya if isinstance(ya, htgb.HTTensor) else htgb.HTTensor.from_blob(tree, n, ka_, ya, htgb.HT_F64, stream)
         Q = htgb.HTTensor.from_blob(tree, n, kb_, yb, htgb.HT_F64, stream)
         Q.scale(-1.0)
         return P.add(Q).norm()
@@ -159,217 +539,11 @@ def accuracy_vs_fp64(htgb, tree, n, ka, xa, kc, xc, wl, stream):
         if len(b) and b[0] > 0:
             sel = b >= 1e-5 * b[0]
             worst = max(worst, float(np.max(np.abs(a[sel] ** 2 - b[sel] ** 2)) / b[0] ** 2))
-    out["sigma2_normwise"] = worst
-    out["norm"] = abs(r32["norm"] - nrm) / nrm
-    out["truncated_tensor"] = diff_norm(x32, k32, x64, k64) / nrm
-    out["trunc_err_fp32"] = diff_norm(X64, None, x32, k32) / nrm
-    out["trunc_err_fp64"] = diff_norm(X64, None, x64, k64) / nrm
-    out["ranks_fp32_ge_fp64"] = bool(np.all(np.asarray(k32) >= np.asarray(k64)))
-    return out
-
-
-def run_reference(args, wl):
-    ws, rank, _ = dist_env()
-    if rank != 0:
-        return 0
-    for _ in range(args.warmup):
-        oracle_truncations(wl, 11, 1)
-    secs, cores = oracle_truncations(wl, 11, args.steps)
-    value = args.steps / secs
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "truncations/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.config, "shape": wl["desc"]},
-        "cpu_baseline": {"value": value, "unit": "truncations/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} add+truncate steps of the full workload"},
-        "e2e": {"value": value, "unit": "truncations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="single", choices=sorted(WORKLOADS))
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison arms")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    wl = WORKLOADS[args.config]
-    if args.impl == "reference":
-        return run_reference(args, wl)
-
-    import torch
-    from paper_1708_03340_gb300 import htgb
-
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    d, k = wl["d"], wl["k"]
-    seed = 11 + 1000 * rank  # each rank truncates its own tensors
-    (n, ka, xa), (_, kc, xc) = wl["make"](seed)
-    tree = htgb.HTTree(d)
-    ksum = np.asarray(ka) + np.asarray(kc)
-    ksum[0] = 1
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2 (129 MB)
-    stream = torch.cuda.current_stream()
-
-    def setup(dtype):
-        A = htgb.HTTensor.from_blob(tree, n, ka, xa, dtype, stream)
-        C = htgb.HTTensor.from_blob(tree, n, kc, xc, dtype, stream)
-        X = htgb.HTTensor.create(tree, n, ksum, dtype, stream)
-        return A, C, X
-
-    def timed(dtype, prec, sched, steps, warmup, prof_mask=0):
-        A, C, X = setup(dtype)
-        opts = htgb.make_opts(prec=prec, schedule=sched, **wl["opts"])
-        for _ in range(warmup):
-            htgb.ht_add_into(A.handle, C.handle, X.handle)
-            htgb.ht_truncate(X.handle, opts)
-        torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        htgb.ht_profile_set(prof_mask)
-        for kind in range(len(htgb.KERNEL_KINDS)):
-            htgb.ht_profile_read(kind, reset=True)
-        l0 = htgb.ht_launch_count()
-        evs = []
-        for _ in range(steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            htgb.ht_add_into(A.handle, C.handle, X.handle)
-            htgb.ht_truncate(X.handle, opts)
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        launches = htgb.ht_launch_count() - l0
-        htgb.ht_profile_set(0)
-        ms = sum(a.elapsed_time(b) for a, b in evs)
-        prof = {}
-        for kind, name in enumerate(htgb.KERNEL_KINDS):
-            cnt, tms, fl = htgb.ht_profile_read(kind, reset=True)
-            if cnt:
-                prof[name] = {"launches": cnt, "ms": tms, "flops": fl}
-        if ws > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        ranks = X.ranks()
-        return dict(ms=ms, launches=launches, prof=prof, X=X, ranks=ranks, A=A, C=C)
-
-    # ---- the headline arm: FP32 storage + FP32 SIMT contractions + FP64 eigen, per-level launches
-    clk_path = os.path.join(tempfile.gettempdir(), f"htgb_clocks_{os.getpid()}.csv")
-    proc, fh = start_clock_sampler(clk_path)
-    all_mask = (1 << len(htgb.KERNEL_KINDS)) - 1
-    main = timed(htgb.HT_F32, htgb.HT_PREC_FP32, htgb.HT_SCHED_LEVEL, args.steps, args.warmup, all_mask)
-    clocks = read_clocks(proc, fh, clk_path, local)
-    K = 2 * k
-    r_cap = wl["opts"].get("rank_cap", 0) or k
-    work, eig_work = model_flops(d, wl["n"], K, r_cap)
-    value = ws * args.steps / (main["ms"] / 1e3)
-    ms_per_step = main["ms"] / args.steps
-
-    # dominant kernel family by device time, with its roofline: algorithmic
-    # flops per launch (counted by the library at plan time) / CUDA-event time
-    dom = max(main["prof"].items(), key=lambda kv: kv[1]["ms"]) if main["prof"] else (None, None)
-    roofline = None
-    if dom[0] is not None:
-        name, rec = dom
-        per_launch_ms = rec["ms"] / rec["launches"]
-        per_launch_flops = rec["flops"] / rec["launches"]
-        ach = per_launch_flops / (per_launch_ms / 1e3)
-        kernel = {"qr": "qr_reg_kernel / qr_block_kernel (FP32 TSQR blocks)", "gemm": "gemm_kernel (FP32 SIMT)",
-                  "eig": "eig_ql_kernel<float> + refine_kernel (FP64)"}.get(name, name)
-        peak = FP64_PEAK if name == "eig" else FP32_PEAK
-        roofline = {"kernel": kernel, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                    "peak_source": ("FP64" if name == "eig" else "FP32") + " unit count x max SM clock (recipe)",
-                    "launches_per_step": rec["launches"] / args.steps, "ms_per_launch": per_launch_ms,
-                    "flops_per_launch": per_launch_flops}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": "truncations/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic (seeded SplitMix64/Box-Muller HT tensors)",
-        "config": {"workload": args.config, "shape": wl["desc"], "l2": "flushed between steps (256 MB write)",
-                   "path": "FP32 storage and contractions, FP64 eigensolves, one batched launch per level"},
-        "gflops": work / (ms_per_step / 1e3) / 1e9,
-        "kernel_ms_per_step": {kname: v["ms"] / args.steps for kname, v in main["prof"].items()},
-        "kernel_tflops": {kname: v["flops"] / max(v["ms"], 1e-9) / 1e9 for kname, v in main["prof"].items()
-                          if v["flops"] > 0},
-        "ranks_first_nodes": [int(v) for v in main["ranks"][:8]],
-        "gpu_launches": main["launches"],
-        "roofline": roofline,
-        "clocks": clocks,
-    }
-
-    # ---- plain FP64 GPU arms (per level, and one launch per node)
-    if not args.no_plain:
-        ps = max(3, args.steps // 4)
-        plain = timed(htgb.HT_F64, htgb.HT_PREC_FP64, htgb.HT_SCHED_LEVEL, ps, 3, all_mask)
-        line["plain_fp64_level"] = {"value": ws * ps / (plain["ms"] / 1e3), "unit": "truncations/s",
-                                    "ms_per_step": plain["ms"] / ps, "launches_per_step": plain["launches"] / ps,
-                                    "kernel_ms_per_step": {kn: v["ms"] / ps for kn, v in plain["prof"].items()}}
-        node = timed(htgb.HT_F64, htgb.HT_PREC_FP64, htgb.HT_SCHED_NODE, 3, 3)
-        line["plain_fp64_per_node"] = {"value": ws * 3 / (node["ms"] / 1e3), "unit": "truncations/s",
-                                       "ms_per_step": node["ms"] / 3, "launches_per_step": node["launches"] / 3}
-        line["speedup_vs_plain_per_node"] = value / line["plain_fp64_per_node"]["value"]
-        line["speedup_vs_plain_level"] = value / line["plain_fp64_level"]["value"]
-        # stated relative error of the mixed path against the plain FP64 GPU path
-        # (the FP64 path matches the CPU FP64 oracle to 1e-12 in the parity tests)
-        line["rel_err_vs_fp64"] = accuracy_vs_fp64(htgb, tree, n, ka, xa, kc, xc, wl, stream)
-
-    # ---- end to end through the public API with host buffers
-    A, C, X = main["A"], main["C"], main["X"]
-    blob32 = lambda b: np.ascontiguousarray(b, dtype=np.float32)
-    ha = torch.from_numpy(blob32(xa)).pin_memory()
-    hc = torch.from_numpy(blob32(xc)).pin_memory()
-    X.truncate(report=False, prec=htgb.HT_PREC_FP32, **wl["opts"])
-    out_sz = htgb.ht_tensor_blob_size(X.handle)
-    hout = torch.empty(4 * max(out_sz, 1), dtype=torch.float32).pin_memory()
-    opts = htgb.make_opts(prec=htgb.HT_PREC_FP32, **wl["opts"])
-    e2e_steps = max(3, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    d2h = 0
-    for _ in range(e2e_steps):
-        htgb.ht_tensor_upload(A.handle, ha.numpy())
-        htgb.ht_tensor_upload(C.handle, hc.numpy())
-        htgb.ht_add_into(A.handle, C.handle, X.handle)
-        htgb.ht_truncate(X.handle, opts)
-        sz = htgb.ht_tensor_blob_size(X.handle)
-        htgb.ht_tensor_download(X.handle, hout.numpy()[:sz])
-        d2h = sz * 4
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_val = e2e_steps / e2e_s
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = ws * e2e_steps / float(t.item())
-    line["e2e"] = {"value": e2e_val, "unit": "truncations/s", "h2d_bytes_per_step": int(ha.numel() * 4 + hc.numel() * 4),
-                   "d2h_bytes_per_step": int(d2h)}
-
-    # ---- CPU oracle baseline (rank 0, N = 1 only)
-    if ws == 1 and not args.no_cpu:
-        secs, cores = oracle_truncations(wl, 11, 2)
-        line["cpu_baseline"] = {"value": 2 / secs, "unit": "truncations/s", "cores": cores, "kind": "oracle",
-                                "sample": "2 add+truncate steps of the same workload, FP64, OpenMP over tree nodes"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
-    return 0
+    return {"sigma2_normwise": worst, "norm": abs(r32["norm"] - nrm) / nrm,
+            "truncated_tensor": diff_norm(x32, k32, x64, k64) / nrm,
+            "trunc_err_fp32": diff_norm(X64, None, x32, k32) / nrm,
+            "trunc_err_fp64": diff_norm(X64, None, x64, k64) / nrm,
+            "ranks_fp32_ge_fp64": bool(np.all(np.asarray(k32) >= np.asarray(k64)))}
 
 
 if __name__ == "__main__":

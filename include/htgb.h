@@ -76,7 +76,9 @@ typedef enum { HT_SCHED_LEVEL = 0, HT_SCHED_NODE = 1 } ht_schedule;
  *         HT_PREC_FP32): an eps below what the arithmetic resolves keeps rank.
  *         The two sons of the root have the same singular values and share
  *         one rank (decided on the first son).
- *  prec: HT_PREC_FP64 needs an F64 tensor, HT_PREC_FP32 an F32 tensor. */
+ *  prec: HT_PREC_FP64 needs an F64 tensor, HT_PREC_FP32 an F32 tensor.
+ *  tensor_caps: NULL, or (batch calls) one rank cap per tensor, host array of
+ *         count entries, used instead of rank_cap for that tensor. */
 typedef struct {
   int mode;
   double eps;
@@ -85,6 +87,7 @@ typedef struct {
   const int *ranks; /* host, one per node in pre-order, or NULL */
   int prec;
   int schedule;
+  const int *tensor_caps; /* host, one per tensor of a batch call, or NULL */
 } ht_trunc_opts;
 
 /* Optional report (pass NULL to skip; synchronises when given).

@@ -1288,7 +1288,8 @@ void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, in
   }
   // ranks
   P.begin(L_RANKS);
-  for (TState &S : TS) {
+  for (size_t i = 0; i < TS.size(); ++i) {
+    TState &S = TS[i];
     const ht_tree &T = S.x->tr;
     S.stats = P.palloc<double>(4);
     RankItem r;
@@ -1308,7 +1309,7 @@ void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, in
     r.d = T.d;
     r.mode = o.mode;
     r.eps_rel = o.eps_relative;
-    r.cap = o.rank_cap;
+    r.cap = o.tensor_caps ? o.tensor_caps[i] : o.rank_cap;
     r.eps = o.eps;
     // noise floor of a computed Gramian eigenvalue: 4 sqrt(2d-1) u lambda_max,
     // u the unit roundoff of the path (every node's rounding perturbs X independently)

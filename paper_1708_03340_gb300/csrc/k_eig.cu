@@ -100,16 +100,18 @@ __device__ __forceinline__ void givens(float f, float g, float &r, float &s, flo
 
 template <typename T>
 __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__restrict__ items, void *scratch,
-                                                             int64_t scratch_stride) {
+                                                             int64_t scratch_stride, int z_in_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EigItem it = items[blockIdx.x];
   const int k = it.k, tid = threadIdx.x, nt = blockDim.x;
-  // layout: [32 doubles][Z: k*k T, when it fits][6k + 32 T][k ints]; the FP64
-  // scratch comes first so that it stays 8-byte aligned for any k
+  // layout: [32 doubles][Z: k*k T, when the launch's largest k fits][6k + 32 T][k ints];
+  // the FP64 scratch comes first so that it stays 8-byte aligned for any k.
+  // z_in_smem is decided per launch (from its largest k), since the dynamic
+  // shared memory is sized for the launch, not for the item.
   double *redd = reinterpret_cast<double *>(smem_raw);
   T *Z;
   T *tail;
-  if (k <= kEigSmemK) {
+  if (z_in_smem) {
     Z = reinterpret_cast<T *>(redd + 32);
     tail = Z + (int64_t)k * k;
   } else {
@@ -360,14 +362,15 @@ __device__ void small_gemm(const double *A, const double *B, double *C, int k, b
 }
 
 __global__ void __launch_bounds__(EIG_THREADS) refine_kernel(const EigItem *__restrict__ items, double *scratch,
-                                                             int64_t scratch_stride) {
+                                                             int64_t scratch_stride, int buf_in_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EigItem it = items[blockIdx.x];
   const int k = it.k, tid = threadIdx.x, nt = blockDim.x;
   const int64_t kk = (int64_t)k * k;
-  double *buf = (k <= 64) ? reinterpret_cast<double *>(smem_raw) : scratch + (int64_t)blockIdx.x * scratch_stride;
+  // buf_in_smem: decided per launch from its largest k (the shared memory is sized for the launch)
+  double *buf = buf_in_smem ? reinterpret_cast<double *>(smem_raw) : scratch + (int64_t)blockIdx.x * scratch_stride;
   double *A = buf, *X = buf + kk, *W1 = buf + 2 * kk, *W2 = buf + 3 * kk;
-  double *small = (k <= 64) ? buf + 4 * kk : reinterpret_cast<double *>(smem_raw);
+  double *small = buf_in_smem ? buf + 4 * kk : reinterpret_cast<double *>(smem_raw);
   double *lam = small;          // k
   double *red = small + k;      // 32
   int *perm = reinterpret_cast<int *>(red + 32);
@@ -456,7 +459,8 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
     const size_t smem = ql_smem<double>(max_k);
     e = cudaFuncSetAttribute(eig_ql_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    eig_ql_kernel<double><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * max_k);
+    eig_ql_kernel<double><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * max_k,
+                                                             max_k <= kEigSmemK ? 1 : 0);
     count_launch();
     return cudaGetLastError();
   }
@@ -464,13 +468,14 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
   const size_t smem = ql_smem<float>(max_k);
   e = cudaFuncSetAttribute(eig_ql_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  eig_ql_kernel<float><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * max_k);
+  eig_ql_kernel<float><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * max_k,
+                                                            max_k <= kEigSmemK ? 1 : 0);
   count_launch();
   const size_t rsm = (max_k <= 64) ? (size_t)(4 * max_k * max_k + max_k + 32) * sizeof(double) + max_k * sizeof(int)
                                    : (size_t)(max_k + 32) * sizeof(double) + max_k * sizeof(int);
   e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
   if (e != cudaSuccess) return e;
-  refine_kernel<<<n_items, EIG_THREADS, rsm, s>>>(d_items, scratch, 4 * (int64_t)max_k * max_k);
+  refine_kernel<<<n_items, EIG_THREADS, rsm, s>>>(d_items, scratch, 4 * (int64_t)max_k * max_k, max_k <= 64 ? 1 : 0);
   count_launch();
   return cudaGetLastError();
 }

@@ -55,6 +55,7 @@ class TruncOpts(ctypes.Structure):
         ("ranks", ctypes.POINTER(ctypes.c_int)),
         ("prec", ctypes.c_int),
         ("schedule", ctypes.c_int),
+        ("tensor_caps", ctypes.POINTER(ctypes.c_int)),
     ]
 
 
@@ -230,7 +231,7 @@ def ht_gramians_noalloc(x, dev_ptr, prec=HT_PREC_FP64):
 
 
 def make_opts(mode="rank", eps=0.0, eps_relative=True, rank_cap=0, ranks=None, prec=HT_PREC_FP64,
-              schedule=HT_SCHED_LEVEL):
+              schedule=HT_SCHED_LEVEL, tensor_caps=None):
     o = TruncOpts()
     o.mode = HT_TRUNC_EPS if mode in ("eps", HT_TRUNC_EPS) else HT_TRUNC_RANK
     o.eps = float(eps)
@@ -242,7 +243,11 @@ def make_opts(mode="rank", eps=0.0, eps_relative=True, rank_cap=0, ranks=None, p
     if ranks is not None:
         keep = np.ascontiguousarray(ranks, dtype=np.int32)
         o.ranks = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-    o._keep = keep
+    keep_caps = None
+    if tensor_caps is not None:
+        keep_caps = np.ascontiguousarray(tensor_caps, dtype=np.int32)
+        o.tensor_caps = keep_caps.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    o._keep = (keep, keep_caps)
     return o
 
 

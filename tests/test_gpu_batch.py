@@ -37,27 +37,23 @@ def test_truncate_batch_uneven(dtype):
     specs = I.batched_specs(count=7, seed=5, d_range=(4, 9), n_range=(12, 90), k_range=(3, 16))
     built = [_sum4(sp, dtype) for sp in specs]
     xs = [b[2] for b in built]
-    k_target = specs[0][2]
-    # every tensor goes back to its own k: the batch call takes one option set, so
-    # truncate in groups of equal k
-    groups = {}
-    for i, sp in enumerate(specs):
-        groups.setdefault(sp[2], []).append(i)
+    # every tensor goes back to its own k (per-tensor rank caps), all in one call
+    caps = [sp[2] for sp in specs]
     prec = htgb.HT_PREC_FP64 if dtype == htgb.HT_F64 else htgb.HT_PREC_FP32
     tol = 1e-12 if dtype == htgb.HT_F64 else 1e-6
-    for k_target, idxs in groups.items():
-        opts = htgb.make_opts(mode="rank", rank_cap=k_target, prec=prec)
-        reps = htgb.ht_truncate_batch([xs[i].handle for i in idxs], opts, report=True)
-        for i, rep in zip(idxs, reps):
-            d, n, k, s = specs[i]
-            tree, nvec, X, kin, xin = built[i]
-            ref = O.truncate(d, nvec, kin, xin, mode="rank", rank_cap=k_target)
-            assert list(X.ranks()) == list(ref["k"])
-            assert abs(rep["norm"] - ref["norm"]) <= tol * ref["norm"]
-            idx = sample_idx(nvec, 150, i)
-            got = X.eval(idx)
-            want = O.eval_entries(d, nvec, ref["k"], ref["x"], idx)
-            assert np.abs(got - want).max() <= 10 * tol * ref["norm"], (i, specs[i])
+    opts = htgb.make_opts(mode="rank", rank_cap=1, prec=prec, tensor_caps=caps)
+    reps = htgb.ht_truncate_batch([x.handle for x in xs], opts, report=True)
+    for i, rep in enumerate(reps):
+        d, n, k, s = specs[i]
+        tree, nvec, X, kin, xin = built[i]
+        ref = O.truncate(d, nvec, kin, xin, mode="rank", rank_cap=k)
+        assert list(X.ranks()) == list(ref["k"])
+        assert max(X.ranks()[1:]) <= k
+        assert abs(rep["norm"] - ref["norm"]) <= tol * ref["norm"]
+        idx = sample_idx(nvec, 150, i)
+        got = X.eval(idx)
+        want = O.eval_entries(d, nvec, ref["k"], ref["x"], idx)
+        assert np.abs(got - want).max() <= 10 * tol * ref["norm"], (i, specs[i])
 
 
 def test_batch_equals_single_calls():
@@ -75,3 +71,36 @@ def test_batch_equals_single_calls():
         out.append([b[2].eval(sample_idx(b[1], 60, 2)) for b in built])
     for a, b in zip(*out):
         assert np.abs(a - b).max() <= 1e-13 * max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("dtype", [htgb.HT_F64, htgb.HT_F32])
+def test_batch_mixed_gramian_sizes(dtype):
+    """One batch whose eigen launch holds Gramians of 4..140 rows: the launch's
+    shared-memory layout is decided by its largest Gramian (above 128 rows the
+    eigenvectors live in global scratch for every item, above 64 the FP64
+    refinement does), and every item must follow it."""
+    big_n = [300, 200, 250, 180]
+    sig = lambda j: 0.9 ** j  # 10% gaps between neighbouring singular values: a well-posed cut
+    ht = lambda d, nn, k, s: I.random_ht(d, nn, k, s, "gauss", sig)
+    small_n, mid_n = [20, 9, 14, 11, 30], [40, 50, 60]
+    cases = [(4, big_n, ht(4, big_n, 70, 51), ht(4, big_n, 70, 52), 60),
+             (5, small_n, ht(5, small_n, 4, 53), ht(5, small_n, 4, 54), 3),
+             (3, mid_n, ht(3, mid_n, 30, 55), ht(3, mid_n, 30, 56), 20)]
+    xs, refs = [], []
+    for d, nn, a, c, cap in cases:
+        tree = htgb.HTTree(d)
+        A = htgb.HTTensor.from_blob(tree, a[0], a[1], a[2], dtype)
+        C = htgb.HTTensor.from_blob(tree, c[0], c[1], c[2], dtype)
+        xs.append(A.add(C))
+        k, x = O.add(d, a[0], a[1], as_stored(a[2], dtype), c[1], as_stored(c[2], dtype))
+        refs.append((d, a[0], O.truncate(d, a[0], k, x, mode="rank", rank_cap=cap)))
+    prec = htgb.HT_PREC_FP64 if dtype == htgb.HT_F64 else htgb.HT_PREC_FP32
+    opts = htgb.make_opts(mode="rank", rank_cap=1, prec=prec, tensor_caps=[cs[-1] for cs in cases])
+    htgb.ht_truncate_batch([x.handle for x in xs], opts)
+    tol = 1e-12 if dtype == htgb.HT_F64 else 1e-5
+    for i, (X, (d, nvec, ref)) in enumerate(zip(xs, refs)):
+        assert list(X.ranks()) == list(ref["k"])
+        idx = sample_idx(nvec, 200, i)
+        got = X.eval(idx)
+        want = O.eval_entries(d, nvec, ref["k"], ref["x"], idx)
+        assert np.abs(got - want).max() <= tol * ref["norm"], i
