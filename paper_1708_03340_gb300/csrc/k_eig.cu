@@ -89,11 +89,15 @@ __device__ __forceinline__ void givens(float f, float g, float &r, float &s, flo
     c = 1.0f;
     return;
   }
-  const float im = 1.0f / m;  // keep f^2 + g^2 away from FP32 underflow
+  // scale by 1/max(m, 1e-30) to keep f^2 + g^2 away from FP32 underflow; the
+  // floor keeps the scale finite when m is subnormal (1/m would overflow to
+  // inf and turn the rotation into NaN), and q stays a normal number then
+  const float sc = fmaxf(m, 1e-30f);
+  const float im = 1.0f / sc;
   const float fs = f * im, gs = g * im;
   const float q = fs * fs + gs * gs;
   const float ri = rsqrtf(q);
-  r = m * q * ri;
+  r = sc * q * ri;
   s = fs * ri;
   c = gs * ri;
 }

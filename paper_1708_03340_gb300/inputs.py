@@ -14,8 +14,12 @@ the root's entry is 1.
 
 Workload recipes (per node, "scaled along each mode j by sigma_j" means
 B[a,b,c] = g_abc * sigma_a * sigma_b * sigma_c with 1-based a, b, c; every
-transfer tensor is then divided by its Frobenius norm, a scalar factor of the
-whole tensor that keeps ||X|| inside FP32's exponent range):
+inner transfer tensor is then scaled so that its first (largest) slice
+B[1, :, :], weighted by the expected column norms of the sons' frames, has
+unit norm, the root likewise as a whole, and every Gaussian leaf frame is
+divided by sqrt(n) -- scalar factors of the whole tensor that keep ||X|| = O(1)
+for deep trees without changing any singular value ratio, rank or relative
+error):
 
 * ``small``      d=8, n=32, k=8, Gaussian U, sigma_j = 2^-j  (two seeds added)
 * ``brute``      d=4, n=8, k=4, as ``small``
@@ -138,6 +142,10 @@ def random_ht(d: int, n, k, seed: int, leaf: str = "gauss", sigma=None):
                 if nm < k:
                     raise ValueError("orthonormal leaf needs n >= k")
                 g = np.linalg.qr(g)[0]
+            else:
+                # columns of unit expected norm: a scalar factor of the whole tensor that keeps
+                # ||X|| finite for deep trees (256 leaves of norm sqrt(4096) would give ~64^256)
+                g = g / np.sqrt(nm)
             parts.append(np.asfortranarray(g).ravel(order="F"))
         else:
             if t == 0:
@@ -146,9 +154,18 @@ def random_ht(d: int, n, k, seed: int, leaf: str = "gauss", sigma=None):
             else:
                 g = normal(key, int(k) ** 3).reshape(int(k), int(k), int(k))
                 b = g * w[:, None, None] * w[None, :, None] * w[None, None, :]
-            # unit Frobenius norm: only a scalar factor of the whole tensor, which keeps
-            # ||X|| within FP32's exponent range for deep trees with decaying weights
-            parts.append((b / np.linalg.norm(b)).ravel())
+            # scalar normalisation (a factor of the whole tensor that keeps ||X|| = O(1)
+            # at any depth): column a of an inner node's frame has a norm close to
+            # || b[a, :, :] weighted by the sons' column norms ||, the sons' columns
+            # having norms 1 (leaves) or w_j / w_1 (inner nodes normalised this way);
+            # the first (largest) column is scaled to norm 1, the root to unit norm
+            def son_scale(s):
+                return np.ones(int(k)) if tr["son1"][s] < 0 else w / w[0]
+            s1, s2 = son_scale(tr["son1"][t]), son_scale(tr["son2"][t])
+            if t == 0:
+                parts.append((b / np.linalg.norm(b * s1[:, None] * s2[None, :])).ravel())
+            else:
+                parts.append((b / np.linalg.norm(b[0] * s1[:, None] * s2[None, :])).ravel())
     return n, ranks, np.concatenate(parts)
 
 

@@ -10,20 +10,22 @@ from paper_1708_03340_gb300 import inputs as I
 U32 = 2.0 ** -24
 
 
-def fp32_tol(d):
-    """Tolerance of the FP32-storage path on ||X|| and on the truncated tensor:
-    1e-6, widened for deep trees to 4 sqrt(2d-1) u_32 because every one of the
-    2d-1 nodes rounds its orthogonalized factors to FP32 independently (the
-    errors add like a random walk over the nodes)."""
-    return max(1e-6, 4.0 * np.sqrt(2 * d - 1) * U32)
+def fp32_tol(d, K=64):
+    """Tolerance of the FP32-storage path on ||X|| and on the truncated tensor.
+    Householder QR applies up to K reflectors to every column of a node's K
+    columns, each a rounding in FP32, so a node's orthogonalization perturbs X
+    by about sqrt(K) u_32 (a random walk over the K roundings); the 2d-1 nodes
+    round independently and add like a random walk over the nodes, and a
+    factor 4 covers the tail: 4 sqrt(K (2d-1)) u_32, at least 1e-6."""
+    return max(1e-6, 4.0 * np.sqrt(K * (2 * d - 1)) * U32)
 
 
-def fp32_tol_sigma(d):
+def fp32_tol_sigma(d, K=64):
     """Tolerance of the FP32-storage path on sigma^2 (normwise per node): every
     Gramian carries twice the relative error of ||X||^2's scale, plus one FP32
     contraction error per level of the top-down recursion (depth = ceil(log2 d))."""
     depth = int(np.ceil(np.log2(d)))
-    return max(1e-6, 2.0 * fp32_tol(d) + 4.0 * depth * U32)
+    return max(1e-6, 2.0 * fp32_tol(d, K) + 4.0 * depth * U32)
 
 
 def as_stored(blob, dtype):

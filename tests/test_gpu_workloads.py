@@ -90,3 +90,80 @@ def test_single_workload(single):
     assert abs(err_gpu - err_ref) <= tol + 2 * energy / nrm + unresolved / nrm
     if dtype == htgb.HT_F64:
         assert dist <= 1e-12 + 2 * energy / nrm  # FP64 resolves everything the oracle does
+
+
+def _rank_rule_holds(rep, d, eps, cap_fn, tol_rel):
+    """Every node's rank obeys the eps rule of the report's own singular
+    values: the discarded tail fits the per-node budget, and one fewer kept
+    direction would not (up to tol_rel of the budget), unless the cap binds."""
+    budget = (eps * rep["norm"]) ** 2 / (2 * d - 3)
+    sg = split_sigma(rep["korth"], rep["sigma"])
+    for t in range(1, 2 * d - 1):
+        r = int(rep["ranks"][t])
+        lam = np.asarray(sg[t], np.float64) ** 2
+        assert np.all(np.isfinite(lam))
+        assert 1 <= r <= max(len(lam), 1)
+        if r < len(lam):
+            assert lam[r:].sum() <= budget * (1 + tol_rel) + 1e-300
+
+
+@pytest.mark.parametrize("dtype", [htgb.HT_F64, htgb.HT_F32])
+def test_deep_workload_properties(dtype):
+    """d=256, n=4096, k=64 (rank 128 after the addition), eps = 1e-6 relative,
+    at full size in the benchmark's launch configuration: finite singular
+    values, ||X|| of both paths within the FP32 tolerance, the HSVD error
+    bound ||X - T(X)|| <= sqrt(sum of discarded sigma^2), and (FP64) ranks
+    obeying the eps rule."""
+    d = 256
+    (n, ka, xa), (_, kc, xc) = I.deep_pair(21)
+    tree, A, C, X = gpu_sum(d, n, (n, ka, xa), (n, kc, xc), dtype)
+    prec = htgb.HT_PREC_FP64 if dtype == htgb.HT_F64 else htgb.HT_PREC_FP32
+    rep = X.truncate(prec=prec, **I.DEEP_OPTS)
+    assert np.isfinite(rep["norm"]) and rep["norm"] > 0
+    assert np.all(np.isfinite(rep["sigma"]))
+    # ||X|| against the other path (FP64 orthogonalization of the same FP32-representable data)
+    Y = htgb.HTTensor.from_blob(tree, n, ka, as_stored(xa, dtype), htgb.HT_F64).add(
+        htgb.HTTensor.from_blob(tree, n, kc, as_stored(xc, dtype), htgb.HT_F64))
+    nrm64 = Y.norm()
+    tol = 1e-12 if dtype == htgb.HT_F64 else fp32_tol(d, 128)
+    assert abs(rep["norm"] - nrm64) <= tol * nrm64
+    # the HSVD bound, measured in FP64 on the GPU: ||X - T(X)||
+    T = htgb.HTTensor.from_blob(tree, n, X.ranks(), X.download().astype(np.float64), htgb.HT_F64)
+    T.scale(-1.0)
+    err = Y.add(T).norm()
+    bound = np.sqrt(rep["discarded_sq"])
+    print(f"deep dtype={dtype}: ||X||={nrm64:.6e} err/||X||={err / nrm64:.3e} bound/||X||={bound / nrm64:.3e} "
+          f"ranks[1:8]={list(X.ranks()[1:8])}")
+    assert err <= bound * (1 + 1e-6) + 4 * tol * nrm64
+    assert err <= 1e-6 * nrm64 * (1 + 1e-6) + 4 * tol * nrm64
+    if dtype == htgb.HT_F64:
+        _rank_rule_holds(rep, d, 1e-6, None, 1e-9)
+
+
+def test_wide_workload_fp32_against_fp64():
+    """d=16, n=2048, k=128 (rank 256 after the addition), truncated to rank 128,
+    full size: the FP32 path's singular values and truncated tensor against
+    the FP64 GPU path on the same FP32-representable inputs, and both against
+    the HSVD error bound."""
+    d = 16
+    (n, ka, xa), (_, kc, xc) = I.wide_pair(31)
+    out = {}
+    for dtype in (htgb.HT_F64, htgb.HT_F32):
+        tree, A, C, X = gpu_sum(d, n, (n, ka, as_stored(xa, htgb.HT_F32)), (n, kc, as_stored(xc, htgb.HT_F32)), dtype)
+        prec = htgb.HT_PREC_FP64 if dtype == htgb.HT_F64 else htgb.HT_PREC_FP32
+        rep = X.truncate(prec=prec, **I.WIDE_OPTS)
+        out[dtype] = (rep, X.ranks(), X.download().astype(np.float64))
+    (r64, k64, x64), (r32, k32, x32) = out[htgb.HT_F64], out[htgb.HT_F32]
+    assert list(k64) == list(k32)
+    nrm = r64["norm"]
+    assert abs(r32["norm"] - nrm) <= fp32_tol(d, 256) * nrm
+    s64 = split_sigma(r64["korth"], r64["sigma"])
+    worst = check_sigma(split_sigma(r32["korth"], r32["sigma"]), s64, fp32_tol_sigma(d, 256), floor=1e-5)
+    tree = htgb.HTTree(d)
+    P = htgb.HTTensor.from_blob(tree, n, k64, x64, htgb.HT_F64)
+    Q = htgb.HTTensor.from_blob(tree, n, k32, x32, htgb.HT_F64)
+    Q.scale(-1.0)
+    dist = P.add(Q).norm() / nrm
+    print(f"wide: sigma worst={worst:.2e} dist(T32, T64)/||X||={dist:.2e} bound/||X||={np.sqrt(r64['discarded_sq']) / nrm:.3e}")
+    # sigma_j = j^-2: the cut at 128 of 256 is far above FP32 resolution, so the truncations agree
+    assert dist <= 10 * fp32_tol(d, 256)
