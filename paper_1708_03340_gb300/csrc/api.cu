@@ -19,6 +19,7 @@
 
 #include "htgb.h"
 #include "internal.h"
+#include "gemm_tune.h"
 
 using namespace htgb;
 
@@ -249,6 +250,8 @@ struct Launch {
   double tc_flops = 0.0;  // flops of items whose shape suits 128-row tensor-core tiles
   const void *ranks = nullptr;  // tagged pointer to the rank array used by the launch
   void *scratch = nullptr;      // eig scratch (tagged)
+  int variant = 0;              // GEMM: SIMT tile shape (gemm_tile_shape)
+  bool comp = true;             // GEMM: compensated FP32 accumulation
 };
 
 template <typename P>
@@ -459,6 +462,37 @@ bool tc_enabled() {
   return v && v[0] == '1';
 }
 
+// SIMT tile shape of a GEMM launch, and the items' tile grid for it.  The
+// shape comes from the tuning table (gemm_tune.h, written by the autotuner):
+// the share of the launch's flops in items whose M is at least the table's
+// threshold decides between 64 x 64 and 128 x 64 tiles.
+void choose_gemm_variant(Plan &P, Launch &L) {
+  GemmItem *it = reinterpret_cast<GemmItem *>(P.items.data() + L.off);
+  double tall = 0.0, all = 0.0;
+  int64_t longest = 0;
+  for (int i = 0; i < L.n; ++i) {
+    const double fl = 2.0 * it[i].M * it[i].N * (double)it[i].K * it[i].Ko * it[i].batch;
+    all += fl;
+    if (it[i].M >= kTuneTallM && it[i].N >= kTuneTallMinN) tall += fl;
+    const int64_t per_cta = (int64_t)it[i].K * ((it[i].Ko + it[i].ksplit - 1) / it[i].ksplit);
+    longest = std::max(longest, per_cta);
+  }
+  // compensated accumulation where a CTA sums more than kTuneCompLen products;
+  // shorter sums carry at most sqrt(kTuneCompLen) u of rounding (typical)
+  L.comp = longest > kTuneCompLen;
+  L.variant = (all > 0.0 && tall >= kTuneTallShare * all) ? 1 : 0;
+  int bm = 64, bn = 64;
+  gemm_tile_shape(L.variant, &bm, &bn);
+  int tiles = 0;
+  for (int i = 0; i < L.n; ++i) {
+    it[i].tiles_m = (it[i].M + bm - 1) / bm;
+    it[i].tiles_n = (it[i].N + bn - 1) / bn;
+    it[i].tile0 = tiles;
+    tiles += it[i].tiles_m * it[i].tiles_n * it[i].batch * it[i].ksplit;
+  }
+  L.tiles = tiles;
+}
+
 // Workspace size of a plan: persistent | scratch | metadata | items.
 size_t plan_bytes(const Plan &P) {
   const size_t p_sz = (P.p_bytes + 255) & ~size_t(255);
@@ -477,6 +511,8 @@ ht_status prepare_plan(Plan &P, cudaStream_t s, char *base, char **ib_dev_out) {
   const size_t m_off = p_sz + s_sz;
   const size_t i_off = m_off + ((P.meta.size() + 255) & ~size_t(255));
   char *pb = base, *sb = base + p_sz, *mb = base + m_off;
+  for (Launch &L : P.launches)
+    if (L.kind == L_GEMM) choose_gemm_variant(P, L);
   for (Launch &L : P.launches) {
     uint8_t *ib = P.items.data() + L.off;
     switch (L.kind) {
@@ -520,8 +556,9 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
       case L_GEMM: {
         // FP32 launches whose flops sit mostly in tall items run on the tensor cores
         const bool tc = !f64 && tc_enabled() && L.tc_flops >= 0.5 * L.flops;
-        e = f64 ? launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s)
-                : launch_gemm<float>((const GemmItem *)items, L.n, L.tiles, rk, L.split, tc ? L.tc_tiles : 0, s);
+        e = f64 ? launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s, L.variant, false)
+                : launch_gemm<float>((const GemmItem *)items, L.n, L.tiles, rk, L.split, tc ? L.tc_tiles : 0, s,
+                                     L.variant, L.comp);
         break;
       }
       case L_QR:

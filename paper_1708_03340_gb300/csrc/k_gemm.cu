@@ -11,7 +11,7 @@ namespace htgb {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, THREADS = 256;
+constexpr int THREADS = 256;
 
 __device__ __forceinline__ int eff_dim(int lit, int ref, int mult, const int *ranks) {
   if (ref < 0) return lit;
@@ -28,11 +28,46 @@ __device__ __forceinline__ int find_item(const GemmItem *items, int n, int tile)
   return lo;
 }
 
-template <typename T>
+template <typename T, int TM>
+__device__ __forceinline__ void lds_vec(const T *p, T (&x)[TM]) {
+  if (sizeof(T) == 4 && TM % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < TM; i += 4) {
+      const float4 v = *reinterpret_cast<const float4 *>(p + i);
+      x[i] = (T)v.x; x[i + 1] = (T)v.y; x[i + 2] = (T)v.z; x[i + 3] = (T)v.w;
+    }
+  } else if (sizeof(T) == 8 && TM % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < TM; i += 2) {
+      const double2 v = *reinterpret_cast<const double2 *>(p + i);
+      x[i] = (T)v.x; x[i + 1] = (T)v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < TM; ++i) x[i] = p[i];
+  }
+}
+
+// One BM x BN tile of C per CTA, TM x TN outputs per thread, K walked in
+// BK-wide tiles through two shared-memory buffers: the global loads of tile
+// q+1 are issued into registers before tile q is multiplied, so their latency
+// hides behind the FMAs.  A thread's TM rows are groups of 4 consecutive rows,
+// 4 (BM / TM) apart, so that a warp's 16-byte shared-memory reads are
+// contiguous; rows of the shared tiles are padded by 4 elements, which keeps
+// those reads aligned and spreads the transposing stores of k-fast operands
+// over the banks.  kComp (FP32 only): every BK-wide tile is summed in
+// registers and added to the running sum with Kahan compensation
+// (compensated summation of the long Gramian reductions); chosen per launch
+// from the longest per-CTA reduction.
+template <typename T, int BM, int BN, int TM, int TN, int BK, bool kComp>
 __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restrict__ items, int n_items,
                                                         const int *__restrict__ ranks) {
-  __shared__ __align__(16) T As[BK][BM];
-  __shared__ __align__(16) T Bs[BK][BN];
+  static_assert((BM / TM) * (BN / TN) == THREADS, "one output block per thread");
+  static_assert(TM % 4 == 0 && TN % 4 == 0, "rows and columns in groups of 4");
+  constexpr int LA = (BM * BK) / THREADS, LB = (BN * BK) / THREADS;
+  constexpr int PAD = 4;
+  __shared__ __align__(16) T As[2][BK][BM + PAD];
+  __shared__ __align__(16) T Bs[2][BK][BN + PAD];
   const int tile = blockIdx.x;
   const GemmItem &it = items[find_item(items, n_items, tile)];
   int local = tile - it.tile0;
@@ -50,90 +85,134 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
   const int K = it.K;
   const int ko_begin = (int)((int64_t)chunk * it.Ko / it.ksplit);
   const int ko_end = (int)((int64_t)(chunk + 1) * it.Ko / it.ksplit);
+  const int kt = (K + BK - 1) / BK;                 // BK-tiles per outer chunk
+  const int nq = (ko_end - ko_begin) * kt;          // BK-tiles of this CTA
   const T *A = static_cast<const T *>(it.A) + (int64_t)b * it.sab;
   const T *B = static_cast<const T *>(it.B) + (int64_t)b * it.sbb;
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;  // thread owns rows 4tx..4tx+3, cols 4ty..4ty+3
+  const int tx = tid % (BM / TM), ty = tid / (BM / TM);
+  // row of output i: group i/4 of 4 rows, groups 4 (BM / TM) apart; columns likewise
+  auto row_of = [&](int i) { return (i >> 2) * (4 * (BM / TM)) + 4 * tx + (i & 3); };
+  auto col_of = [&](int j) { return (j >> 2) * (4 * (BN / TN)) + 4 * ty + (j & 3); };
   const bool a_mfast = (it.sam == 1);
   const bool b_nfast = (it.sbn == 1) && (it.sbk != 1);
-  // FP32: each 16-wide k-tile is summed in registers, then added to the
-  // running sum with Kahan compensation (compensated summation of the long
-  // Gramian reductions); FP64 sums directly.
-  constexpr bool kComp = sizeof(T) == 4;
-  T acc[4][4], sum[4][4], cmp[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = sum[i][j] = cmp[i][j] = T(0);
 
-  for (int ko = ko_begin; ko < ko_end; ++ko) {
+  T ra[LA], rb[LB];  // the next tile, in flight
+  auto load = [&](int q) {
+    const int ko = ko_begin + q / kt, k0 = (q % kt) * BK;
     const T *Ak = A + (int64_t)ko * it.sako;
     const T *Bk = B + (int64_t)ko * it.sbko;
-    for (int k0 = 0; k0 < K; k0 += BK) {
-      // A tile: BM x BK elements, 4 per thread
+    const int64_t kflat = (int64_t)ko * K;
 #pragma unroll
-      for (int r = 0; r < (BM * BK) / THREADS; ++r) {
-        int e = tid + r * THREADS;
-        int mm, kk;
-        if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
-        int gm = m0 + mm, gk = k0 + kk;
-        T v = T(0);
-        if (gm < M && gk < K && (it.k_total < 0 || (int64_t)ko * K + gk < it.k_total))
-          v = Ak[(int64_t)gm * it.sam + (int64_t)gk * it.sak];
-        As[kk][mm] = v;
-      }
-#pragma unroll
-      for (int r = 0; r < (BN * BK) / THREADS; ++r) {
-        int e = tid + r * THREADS;
-        int nn, kk;
-        if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
-        int gn = n0 + nn, gk = k0 + kk;
-        T v = T(0);
-        if (gn < N && gk < K && (it.k_total < 0 || (int64_t)ko * K + gk < it.k_total))
-          v = Bk[(int64_t)gk * it.sbk + (int64_t)gn * it.sbn];
-        Bs[kk][nn] = v;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < BK; ++kk) {
-        T a[4], bb[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[kk][4 * tx + i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][4 * ty + j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
-      }
-      if (kComp) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const T y = acc[i][j] - cmp[i][j];
-            const T t = sum[i][j] + y;
-            cmp[i][j] = (t - sum[i][j]) - y;
-            sum[i][j] = t;
-            acc[i][j] = T(0);
-          }
-      }
-      __syncthreads();
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * THREADS;
+      int mm, kk;
+      if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      T v = T(0);
+      if (gm < M && gk < K && (it.k_total < 0 || kflat + gk < it.k_total))
+        v = Ak[(int64_t)gm * it.sam + (int64_t)gk * it.sak];
+      ra[r] = v;
     }
+#pragma unroll
+    for (int r = 0; r < LB; ++r) {
+      const int e = tid + r * THREADS;
+      int nn, kk;
+      if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      T v = T(0);
+      if (gn < N && gk < K && (it.k_total < 0 || kflat + gk < it.k_total))
+        v = Bk[(int64_t)gk * it.sbk + (int64_t)gn * it.sbn];
+      rb[r] = v;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * THREADS;
+      int mm, kk;
+      if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+      As[buf][kk][mm] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < LB; ++r) {
+      const int e = tid + r * THREADS;
+      int nn, kk;
+      if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+      Bs[buf][kk][nn] = rb[r];
+    }
+  };
+
+  T acc[TM][TN], sum[kComp ? TM : 1][kComp ? TN : 1], cmp[kComp ? TM : 1][kComp ? TN : 1];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  if (kComp) {
+#pragma unroll
+    for (int i = 0; i < (kComp ? TM : 1); ++i)
+#pragma unroll
+      for (int j = 0; j < (kComp ? TN : 1); ++j) sum[i][j] = cmp[i][j] = T(0);
+  }
+  if (nq > 0) {
+    load(0);
+    store(0);
+  }
+  __syncthreads();
+  for (int q = 0; q < nq; ++q) {
+    const int buf = q & 1;
+    if (q + 1 < nq) load(q + 1);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], bb[TN];
+#pragma unroll
+      for (int g = 0; g < TM / 4; ++g) {
+        T x[4];
+        lds_vec<T, 4>(&As[buf][kk][g * 4 * (BM / TM) + 4 * tx], x);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[4 * g + u] = x[u];
+      }
+#pragma unroll
+      for (int g = 0; g < TN / 4; ++g) {
+        T x[4];
+        lds_vec<T, 4>(&Bs[buf][kk][g * 4 * (BN / TN) + 4 * ty], x);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) bb[4 * g + u] = x[u];
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    if (kComp) {
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          const T y = acc[i][j] - cmp[kComp ? i : 0][kComp ? j : 0];
+          const T t = sum[kComp ? i : 0][kComp ? j : 0] + y;
+          cmp[kComp ? i : 0][kComp ? j : 0] = (t - sum[kComp ? i : 0][kComp ? j : 0]) - y;
+          sum[kComp ? i : 0][kComp ? j : 0] = t;
+          acc[i][j] = T(0);
+        }
+    }
+    // the other buffer was last read before the previous barrier
+    if (q + 1 < nq) store(buf ^ 1);
+    __syncthreads();
   }
   if (kComp) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = sum[i][j];
+      for (int j = 0; j < TN; ++j) acc[i][j] = sum[kComp ? i : 0][kComp ? j : 0];
   }
   if (it.ksplit > 1) {
     T *P = static_cast<T *>(it.part) + ((int64_t)chunk * it.batch + b) * (int64_t)it.M * it.N;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        int gm = m0 + 4 * tx + i, gn = n0 + 4 * ty + j;
+      for (int j = 0; j < TN; ++j) {
+        const int gm = m0 + row_of(i), gn = n0 + col_of(j);
         if (gm < M && gn < N) P[(int64_t)gn * it.M + gm] = acc[i][j];
       }
     return;
@@ -141,10 +220,10 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
   T *C = static_cast<T *>(it.C) + (int64_t)b * it.scb;
   const T alpha = T(it.alpha), beta = T(it.beta);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int gm = m0 + 4 * tx + i, gn = n0 + 4 * ty + j;
+    for (int j = 0; j < TN; ++j) {
+      const int gm = m0 + row_of(i), gn = n0 + col_of(j);
       if (gm < M && gn < N) {
         T *c = C + (int64_t)gm * it.scm + (int64_t)gn * it.scn;
         T v = alpha * acc[i][j];
@@ -184,13 +263,21 @@ __global__ void gemm_reduce_kernel(const GemmItem *__restrict__ items, const int
 
 template <typename T>
 cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, bool any_split,
-                        int tc_tiles, cudaStream_t s) {
+                        int tc_tiles, cudaStream_t s, int variant, bool comp) {
   if (n_items <= 0 || total_tiles <= 0) return cudaSuccess;
   if (sizeof(T) == 4 && tc_tiles > 0) {
     cudaError_t e = launch_gemm_tc(d_items, n_items, tc_tiles, d_ranks, s);
     if (e != cudaSuccess) return e;
   } else {
-    gemm_kernel<T><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+    // Kahan compensation only for FP32 launches with long per-CTA reductions
+    const bool c = (sizeof(T) == 4) && comp;
+    if (variant == 1) {
+      if (c) gemm_kernel<T, 128, 64, 8, 4, 16, true><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+      else gemm_kernel<T, 128, 64, 8, 4, 16, false><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+    } else {
+      if (c) gemm_kernel<T, 64, 64, 4, 4, 16, true><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+      else gemm_kernel<T, 64, 64, 4, 4, 16, false><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+    }
     count_launch();
   }
   if (any_split) {
@@ -203,7 +290,12 @@ cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, c
   return cudaGetLastError();
 }
 
-template cudaError_t launch_gemm<double>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t);
-template cudaError_t launch_gemm<float>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t);
+template cudaError_t launch_gemm<double>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t, int, bool);
+template cudaError_t launch_gemm<float>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t, int, bool);
+
+void gemm_tile_shape(int variant, int *bm, int *bn) {
+  *bm = (variant == 1) ? 128 : 64;
+  *bn = 64;
+}
 
 }  // namespace htgb
