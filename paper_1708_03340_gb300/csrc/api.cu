@@ -462,25 +462,53 @@ bool tc_enabled() {
   return v && v[0] == '1';
 }
 
-// SIMT tile shape of a GEMM launch, and the items' tile grid for it.  The
-// shape comes from the tuning table (gemm_tune.h, written by the autotuner):
-// the share of the launch's flops in items whose M is at least the table's
-// threshold decides between 64 x 64 and 128 x 64 tiles.
+// Tuning table (gemm_tune.h, written by tune_gemm.py); the autotuner sweeps
+// it through HTGB_TUNE="tall_m,tall_share,square_share" without rebuilding.
+struct GemmTune {
+  int tall_m = kTuneTallM;
+  double tall_share = kTuneTallShare;
+  double square_share = kTuneSquareShare;
+};
+const GemmTune &gemm_tune() {
+  static GemmTune t = [] {
+    GemmTune v;
+    if (const char *e = getenv("HTGB_TUNE")) {
+      int m = 0;
+      double a = 0.0, b = 0.0;
+      if (sscanf(e, "%d,%lf,%lf", &m, &a, &b) == 3) {
+        v.tall_m = m;
+        v.tall_share = a;
+        v.square_share = b;
+      }
+    }
+    return v;
+  }();
+  return t;
+}
+
+// SIMT tile shape of a GEMM launch, and the items' tile grid for it.  Items
+// with M >= tall_m are "tall", those also with N >= tall_m "square"; the
+// shares of the launch's flops in them pick 128 x 128 (uncompensated
+// launches), 128 x 64 or 64 x 64 tiles.
 void choose_gemm_variant(Plan &P, Launch &L) {
+  const GemmTune &tu = gemm_tune();
   GemmItem *it = reinterpret_cast<GemmItem *>(P.items.data() + L.off);
-  double tall = 0.0, all = 0.0;
+  double tall = 0.0, square = 0.0, all = 0.0;
   int64_t longest = 0;
   for (int i = 0; i < L.n; ++i) {
     const double fl = 2.0 * it[i].M * it[i].N * (double)it[i].K * it[i].Ko * it[i].batch;
     all += fl;
-    if (it[i].M >= kTuneTallM && it[i].N >= kTuneTallMinN) tall += fl;
+    if (it[i].M >= tu.tall_m) tall += fl;
+    if (it[i].M >= tu.tall_m && it[i].N >= tu.tall_m) square += fl;
     const int64_t per_cta = (int64_t)it[i].K * ((it[i].Ko + it[i].ksplit - 1) / it[i].ksplit);
     longest = std::max(longest, per_cta);
   }
   // compensated accumulation where a CTA sums more than kTuneCompLen products;
   // shorter sums carry at most sqrt(kTuneCompLen) u of rounding (typical)
   L.comp = longest > kTuneCompLen;
-  L.variant = (all > 0.0 && tall >= kTuneTallShare * all) ? 1 : 0;
+  L.variant = 0;
+  if (all > 0.0 && !L.comp && square >= tu.square_share * all) L.variant = 2;
+  else if (all > 0.0 && tall >= tu.tall_share * all) L.variant = 1;
   int bm = 64, bn = 64;
   gemm_tile_shape(L.variant, &bm, &bn);
   int tiles = 0;

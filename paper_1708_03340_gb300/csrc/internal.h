@@ -105,9 +105,10 @@ struct RankItem {
 // launchers (stream-ordered; return cudaGetLastError())
 // ---------------------------------------------------------------------------
 // tc_tiles > 0: run the FP32 items on the tcgen05 kernel (k_tc.cu) with that many tiles
-// variant: SIMT tile shape (0: 64 x 64, 1: 128 x 64); items' tiles_m / tiles_n /
-// tile0 must be laid out for that shape (gemm_tile_shape).  comp: Kahan-
-// compensated FP32 accumulation across the BK-wide tiles of a CTA.
+// variant: SIMT tile shape (0: 64 x 64, 1: 128 x 64, 2: 128 x 128, the last
+// without compensation only); items' tiles_m / tiles_n / tile0 must be laid
+// out for that shape (gemm_tile_shape).  comp: Kahan-compensated FP32
+// accumulation across the BK-wide tiles of a CTA.
 template <typename T>
 cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks,
                         bool any_split, int tc_tiles, cudaStream_t s, int variant, bool comp);

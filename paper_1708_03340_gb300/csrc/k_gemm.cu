@@ -271,7 +271,9 @@ cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, c
   } else {
     // Kahan compensation only for FP32 launches with long per-CTA reductions
     const bool c = (sizeof(T) == 4) && comp;
-    if (variant == 1) {
+    if (variant == 2 && !c) {
+      gemm_kernel<T, 128, 128, 8, 8, 16, false><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+    } else if (variant >= 1) {
       if (c) gemm_kernel<T, 128, 64, 8, 4, 16, true><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
       else gemm_kernel<T, 128, 64, 8, 4, 16, false><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
     } else {
@@ -294,8 +296,8 @@ template cudaError_t launch_gemm<double>(const GemmItem *, int, int, const int *
 template cudaError_t launch_gemm<float>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t, int, bool);
 
 void gemm_tile_shape(int variant, int *bm, int *bn) {
-  *bm = (variant == 1) ? 128 : 64;
-  *bn = 64;
+  *bm = (variant >= 1) ? 128 : 64;
+  *bn = (variant == 2) ? 128 : 64;
 }
 
 }  // namespace htgb
