@@ -48,13 +48,30 @@ __device__ __forceinline__ void lds_vec(const T *p, T (&x)[TM]) {
   }
 }
 
+// Asynchronous element copy global -> shared (cp.async, 4 or 8 bytes); with
+// valid == false nothing is read (src-size 0) and the destination is
+// zero-filled.  src is always an aligned address inside the operand.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst_smem, const T *src, bool valid) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem));
+  const int n = valid ? (int)sizeof(T) : 0;
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // One BM x BN tile of C per CTA, TM x TN outputs per thread, K walked in
-// BK-wide tiles through two shared-memory buffers: the global loads of tile
-// q+1 are issued into registers before tile q is multiplied, so their latency
-// hides behind the FMAs.  A thread's TM rows are groups of 4 consecutive rows,
+// BK-wide tiles through NS shared-memory stages filled by cp.async: the
+// copies of tile q + NS - 1 are in flight while tile q is multiplied, and
+// every element lands directly at its (possibly transposed) place, zero
+// outside the matrix.  A thread's TM rows are groups of 4 consecutive rows,
 // 4 (BM / TM) apart, so that a warp's 16-byte shared-memory reads are
 // contiguous; rows of the shared tiles are padded by 4 elements, which keeps
-// those reads aligned and spreads the transposing stores of k-fast operands
+// those reads aligned and spreads the transposing writes of k-fast operands
 // over the banks.  kComp (FP32 only): every BK-wide tile is summed in
 // registers and added to the running sum with Kahan compensation
 // (compensated summation of the long Gramian reductions); chosen per launch
@@ -65,9 +82,9 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
   static_assert((BM / TM) * (BN / TN) == THREADS, "one output block per thread");
   static_assert(TM % 4 == 0 && TN % 4 == 0, "rows and columns in groups of 4");
   constexpr int LA = (BM * BK) / THREADS, LB = (BN * BK) / THREADS;
-  constexpr int PAD = 4;
-  __shared__ __align__(16) T As[2][BK][BM + PAD];
-  __shared__ __align__(16) T Bs[2][BK][BN + PAD];
+  constexpr int PAD = 4, NS = 3;
+  __shared__ __align__(16) T As[NS][BK][BM + PAD];
+  __shared__ __align__(16) T Bs[NS][BK][BN + PAD];
   const int tile = blockIdx.x;
   const GemmItem &it = items[find_item(items, n_items, tile)];
   int local = tile - it.tile0;
@@ -97,50 +114,33 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
   const bool a_mfast = (it.sam == 1);
   const bool b_nfast = (it.sbn == 1) && (it.sbk != 1);
 
-  T ra[LA], rb[LB];  // the next tile, in flight
-  auto load = [&](int q) {
-    const int ko = ko_begin + q / kt, k0 = (q % kt) * BK;
-    const T *Ak = A + (int64_t)ko * it.sako;
-    const T *Bk = B + (int64_t)ko * it.sbko;
-    const int64_t kflat = (int64_t)ko * K;
+  // issue the copies of BK-tile q into stage st (one commit group per call)
+  auto issue = [&](int q, int st) {
+    if (q < nq) {
+      const int ko = ko_begin + q / kt, k0 = (q % kt) * BK;
+      const T *Ak = A + (int64_t)ko * it.sako;
+      const T *Bk = B + (int64_t)ko * it.sbko;
+      const int64_t kflat = (int64_t)ko * K;
 #pragma unroll
-    for (int r = 0; r < LA; ++r) {
-      const int e = tid + r * THREADS;
-      int mm, kk;
-      if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
-      const int gm = m0 + mm, gk = k0 + kk;
-      T v = T(0);
-      if (gm < M && gk < K && (it.k_total < 0 || kflat + gk < it.k_total))
-        v = Ak[(int64_t)gm * it.sam + (int64_t)gk * it.sak];
-      ra[r] = v;
-    }
+      for (int r = 0; r < LA; ++r) {
+        const int e = tid + r * THREADS;
+        int mm, kk;
+        if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+        const int gm = m0 + mm, gk = k0 + kk;
+        const bool v = gm < M && gk < K && (it.k_total < 0 || kflat + gk < it.k_total);
+        cp_async_elem<T>(&As[st][kk][mm], Ak + (v ? (int64_t)gm * it.sam + (int64_t)gk * it.sak : 0), v);
+      }
 #pragma unroll
-    for (int r = 0; r < LB; ++r) {
-      const int e = tid + r * THREADS;
-      int nn, kk;
-      if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
-      const int gn = n0 + nn, gk = k0 + kk;
-      T v = T(0);
-      if (gn < N && gk < K && (it.k_total < 0 || kflat + gk < it.k_total))
-        v = Bk[(int64_t)gk * it.sbk + (int64_t)gn * it.sbn];
-      rb[r] = v;
+      for (int r = 0; r < LB; ++r) {
+        const int e = tid + r * THREADS;
+        int nn, kk;
+        if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+        const int gn = n0 + nn, gk = k0 + kk;
+        const bool v = gn < N && gk < K && (it.k_total < 0 || kflat + gk < it.k_total);
+        cp_async_elem<T>(&Bs[st][kk][nn], Bk + (v ? (int64_t)gk * it.sbk + (int64_t)gn * it.sbn : 0), v);
+      }
     }
-  };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int r = 0; r < LA; ++r) {
-      const int e = tid + r * THREADS;
-      int mm, kk;
-      if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
-      As[buf][kk][mm] = ra[r];
-    }
-#pragma unroll
-    for (int r = 0; r < LB; ++r) {
-      const int e = tid + r * THREADS;
-      int nn, kk;
-      if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
-      Bs[buf][kk][nn] = rb[r];
-    }
+    cp_async_commit();
   };
 
   T acc[TM][TN], sum[kComp ? TM : 1][kComp ? TN : 1], cmp[kComp ? TM : 1][kComp ? TN : 1];
@@ -154,14 +154,13 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
 #pragma unroll
       for (int j = 0; j < (kComp ? TN : 1); ++j) sum[i][j] = cmp[i][j] = T(0);
   }
-  if (nq > 0) {
-    load(0);
-    store(0);
-  }
-  __syncthreads();
+#pragma unroll
+  for (int st = 0; st < NS - 1; ++st) issue(st, st);
   for (int q = 0; q < nq; ++q) {
-    const int buf = q & 1;
-    if (q + 1 < nq) load(q + 1);
+    const int buf = q % NS;
+    cp_async_wait<NS - 2>();  // this thread's copies of tile q have landed
+    __syncthreads();          // everybody's have; and stage (q - 1) % NS is no longer read
+    issue(q + NS - 1, (q + NS - 1) % NS);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       T a[TM], bb[TN];
@@ -196,10 +195,8 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
           acc[i][j] = T(0);
         }
     }
-    // the other buffer was last read before the previous barrier
-    if (q + 1 < nq) store(buf ^ 1);
-    __syncthreads();
   }
+  cp_async_wait<0>();  // no copy may be left in flight when the CTA exits
   if (kComp) {
 #pragma unroll
     for (int i = 0; i < TM; ++i)
