@@ -259,6 +259,14 @@ inline P *tagp(uint64_t tag, size_t off) {
   return reinterpret_cast<P *>(tag | (uint64_t)off);
 }
 
+// The tensor-core contraction kernel (k_tc.cu) runs the FP32 contractions
+// when HTGB_TC=1 (opt-in; see the kernel's header for its precision).
+bool tc_enabled() {
+  const char *v = getenv("HTGB_TC");
+  return v && v[0] == '1';
+}
+constexpr int kTcMaxK = 512;  // products one tensor-core CTA accumulates in TMEM
+
 struct Plan {
   std::vector<uint8_t> items;
   std::vector<uint8_t> meta;
@@ -337,6 +345,13 @@ struct Plan {
       g.sbn = am; g.sbk = ak; g.sbko = ako; g.sbb = ab;
       std::swap(g.scm, g.scn);
       std::swap(g.M, g.N);
+    }
+    if (dtype == HT_F32 && tc_enabled()) {
+      // the tensor-core kernel accumulates a CTA's whole reduction in TMEM (FP32):
+      // keep it at most kTcMaxK products by splitting the outer range across CTAs
+      const int64_t red = (int64_t)g.K * g.Ko;
+      if (g.K <= kTcMaxK && red > (int64_t)kTcMaxK * g.ksplit)
+        g.ksplit = (int)std::min<int64_t>(g.Ko, (red + kTcMaxK - 1) / kTcMaxK);
     }
     g.tiles_m = (g.M + 63) / 64;
     g.tiles_n = (g.N + 63) / 64;
@@ -453,14 +468,7 @@ void reloc_items<RankItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
 // order after the last launch.  `keep` receives the relocated persistent base
 // (so that callers can read results) and the caller must free it with
 // cudaFreeAsync; if keep is null, everything is freed here.
-// The tensor-core contraction kernel (k_tc.cu) runs the FP32 contractions when
-// HTGB_TC=1.  It is off by default: on deep trees its FP32 accumulation inside
-// the MMA (not compensated) costs about 6x the error of the compensated SIMT
-// kernel (||X|| to 6e-6 instead of 1e-6 at d = 64) and it is not faster there.
-bool tc_enabled() {
-  const char *v = getenv("HTGB_TC");
-  return v && v[0] == '1';
-}
+
 
 // Tuning table (gemm_tune.h, written by tune_gemm.py); the autotuner sweeps
 // it through HTGB_TUNE="tall_m,tall_share,square_share" without rebuilding.

@@ -10,16 +10,27 @@
 // six products l*h, h*l, m*m, m*h, h*m, h*h (smallest first) carry the
 // product to FP32 accuracy (dropped terms are below 2^-33 relative).
 //
-// Per CTA: one 128 x 64 tile of C.  K is walked in stages of 32: the 128
-// threads load a stage into registers, split it and store it in shared memory
-// in the canonical no-swizzle K-major layout (8-row x 16-byte core matrices);
-// one thread issues the 24 MMAs (6 piece products x 4 k-steps of 8) into two
-// tensor-memory accumulators that restart at every stage (the h*h products
-// and the five corrections, so no accumulator takes more than 20 additions)
-// and commits them to an mbarrier; everybody waits (bounded), reads its row of
-// both accumulators with tcgen05.ld (warp w owns lanes 32w..32w+31) and adds
-// the stage to a running FP32 sum in registers.  Long reductions are split
-// across CTAs and their partial sums added in FP64 (k_gemm.cu).
+// Per CTA: one 128 x 64 tile of C, 128 threads.  K is walked in stages of 32
+// through two shared-memory stage buffers (each holding the three pieces of
+// A and of B in the canonical no-swizzle K-major layout, 8-row x 16-byte core
+// matrices).  Per stage the threads split the FP32 values (loaded into
+// registers one stage ahead) into their buffer, and one thread issues the 24
+// MMAs (6 piece products x 4 k-steps of 8) into two tensor-memory
+// accumulators -- the h*h products and the five corrections -- and commits
+// them to that buffer's mbarrier.  The MMAs of a stage run while the threads
+// split the next one; a buffer is refilled only after its mbarrier reports the
+// MMAs that read it complete (bounded waits, error flag).  The accumulators
+// cover the CTA's whole reduction, at most kTcMaxK products (the plan splits
+// longer reductions across CTAs, whose partial sums are added in FP64 by
+// k_gemm.cu), and are read once at the end with tcgen05.ld (warp w owns TMEM
+// lanes 32w..32w+31).
+//
+// Measured on GB300 (opt-in, HTGB_TC=1): 5.5 - 7.5 TFLOP/s on the benchmark
+// workloads, below the SIMT kernel (12 - 25), because the per-element split
+// and scattered 4-byte shared stores of 128 threads cannot feed the MMAs; and
+// the tensor core's FP32 accumulation is biased (errors grow with the number
+// of accumulated products instead of like a random walk), which puts ||X|| of
+// the d = 256 workload at 7e-5 relative, above the FP32 path's tolerance.
 #include <stdint.h>
 
 #include "internal.h"
@@ -105,7 +116,7 @@ template <int NT>  // NT: columns of the tile (multiple of 16, <= TCN, 2 NT <= T
 __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmItem *__restrict__ items, int n_items,
                                                              const int *__restrict__ ranks) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -127,11 +138,12 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmItem *__r
   const int K = it.K;
   const int ko_begin = (int)((int64_t)chunk * it.Ko / it.ksplit);
   const int ko_end = (int)((int64_t)(chunk + 1) * it.Ko / it.ksplit);
+  const int kt = (K + TCK - 1) / TCK;
+  const int ns = (ko_end - ko_begin) * kt;  // stages of this CTA
   const float *A = static_cast<const float *>(it.A) + (int64_t)b * it.sab;
   const float *B = static_cast<const float *>(it.B) + (int64_t)b * it.sbb;
-  unsigned char *As = sm;                // 3 pieces
-  unsigned char *Bs = sm + 3 * PIECE_A;  // 3 pieces
-  const uint32_t bar = smem_addr(&mbar);
+  constexpr uint32_t STAGE = 3 * PIECE_A + 3 * PIECE_B;  // bytes of one stage buffer
+  const uint32_t bar0 = smem_addr(&mbar[0]), bar1 = smem_addr(&mbar[1]);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
@@ -140,7 +152,9 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmItem *__r
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_flag = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -151,106 +165,126 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmItem *__r
   const uint32_t idesc = idesc_tf32(TCM, NT);
   const bool a_mfast = (it.sam == 1);
   const bool b_nfast = (it.sbn == 1) && (it.sbk != 1);
-  uint32_t parity = 0;
-  float acc[NT];  // row m0 + 32 warp + lane of the tile, summed over stages in registers
-#pragma unroll
-  for (int j = 0; j < NT; ++j) acc[j] = 0.0f;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-
-  for (int ko = ko_begin; ko < ko_end; ++ko) {
+  constexpr int PA = TCM * TCK / TC_THREADS;  // 32 elements of A per thread and stage
+  constexpr int PB = NT * TCK / TC_THREADS;   // 16 elements of B
+  float xa[PA], xb[PB];
+  auto load = [&](int s) {
+    const int ko = ko_begin + s / kt, k0 = (s % kt) * TCK;
     const float *Ak = A + (int64_t)ko * it.sako;
     const float *Bk = B + (int64_t)ko * it.sbko;
-    for (int k0 = 0; k0 < K; k0 += TCK) {
-      // ---- stage: batched loads into registers, then split into 3 TF32 pieces
-      {
-        constexpr int PER = TCM * TCK / TC_THREADS;  // 32 elements of A per thread
-        float x[PER];
+    const int64_t kflat = (int64_t)ko * K;
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-          const int e = tid + q * TC_THREADS;
-          int r, k;
-          if (a_mfast) { r = e % TCM; k = e / TCM; } else { k = e % TCK; r = e / TCK; }
-          const int gm = m0 + r, gk = k0 + k;
-          const bool kin = gk < K && (it.k_total < 0 || (int64_t)ko * K + gk < it.k_total);
-          x[q] = (gm < M && kin) ? Ak[(int64_t)gm * it.sam + (int64_t)gk * it.sak] : 0.0f;
-        }
+    for (int q = 0; q < PA; ++q) {
+      const int e = tid + q * TC_THREADS;
+      int r, k;
+      if (a_mfast) { r = e % TCM; k = e / TCM; } else { k = e % TCK; r = e / TCK; }
+      const int gm = m0 + r, gk = k0 + k;
+      const bool kin = gk < K && (it.k_total < 0 || kflat + gk < it.k_total);
+      xa[q] = (gm < M && kin) ? Ak[(int64_t)gm * it.sam + (int64_t)gk * it.sak] : 0.0f;
+    }
 #pragma unroll
-        for (int q = 0; q < PER; ++q) {
-          const int e = tid + q * TC_THREADS;
-          int r, k;
-          if (a_mfast) { r = e % TCM; k = e / TCM; } else { k = e % TCK; r = e / TCK; }
-          float h, md, l;
-          split3(x[q], h, md, l);
-          const uint32_t o = core_off(r, k);
-          *reinterpret_cast<float *>(As + o) = h;
-          *reinterpret_cast<float *>(As + PIECE_A + o) = md;
-          *reinterpret_cast<float *>(As + 2 * PIECE_A + o) = l;
-        }
-      }
-      {
-        constexpr int PERB = NT * TCK / TC_THREADS;
-        float x[PERB];
+    for (int q = 0; q < PB; ++q) {
+      const int e = tid + q * TC_THREADS;
+      int nn, k;
+      if (b_nfast) { nn = e % NT; k = e / NT; } else { k = e % TCK; nn = e / TCK; }
+      const int gn = n0 + nn, gk = k0 + k;
+      const bool kin = gk < K && (it.k_total < 0 || kflat + gk < it.k_total);
+      xb[q] = (gn < N && kin) ? Bk[(int64_t)gk * it.sbk + (int64_t)gn * it.sbn] : 0.0f;
+    }
+  };
+  auto split_store = [&](unsigned char *buf) {
+    unsigned char *As = buf, *Bs = buf + 3 * PIECE_A;
 #pragma unroll
-        for (int q = 0; q < PERB; ++q) {
-          const int e = tid + q * TC_THREADS;
-          int nn, k;
-          if (b_nfast) { nn = e % NT; k = e / NT; } else { k = e % TCK; nn = e / TCK; }
-          const int gn = n0 + nn, gk = k0 + k;
-          const bool kin = gk < K && (it.k_total < 0 || (int64_t)ko * K + gk < it.k_total);
-          x[q] = (gn < N && kin) ? Bk[(int64_t)gk * it.sbk + (int64_t)gn * it.sbn] : 0.0f;
-        }
+    for (int q = 0; q < PA; ++q) {
+      const int e = tid + q * TC_THREADS;
+      int r, k;
+      if (a_mfast) { r = e % TCM; k = e / TCM; } else { k = e % TCK; r = e / TCK; }
+      float h, md, l;
+      split3(xa[q], h, md, l);
+      const uint32_t o = core_off(r, k);
+      *reinterpret_cast<float *>(As + o) = h;
+      *reinterpret_cast<float *>(As + PIECE_A + o) = md;
+      *reinterpret_cast<float *>(As + 2 * PIECE_A + o) = l;
+    }
 #pragma unroll
-        for (int q = 0; q < PERB; ++q) {
-          const int e = tid + q * TC_THREADS;
-          int nn, k;
-          if (b_nfast) { nn = e % NT; k = e / NT; } else { k = e % TCK; nn = e / TCK; }
-          float h, md, l;
-          split3(x[q], h, md, l);
-          const uint32_t o = core_off(nn, k);
-          *reinterpret_cast<float *>(Bs + o) = h;
-          *reinterpret_cast<float *>(Bs + PIECE_B + o) = md;
-          *reinterpret_cast<float *>(Bs + 2 * PIECE_B + o) = l;
-        }
-      }
-      // generic-proxy stores must be visible to the tensor core's async proxy
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
-        // correction products (smallest first) into columns [NT, 2NT), hi*hi into [0, NT);
-        // both accumulators restart at every stage (at most 4 x 5 + 4 accumulations)
-        const int pa[6] = {2, 0, 1, 1, 0, 0};
-        const int pb[6] = {0, 2, 1, 0, 1, 0};
-#pragma unroll
-        for (int p = 0; p < 6; ++p) {
-          const uint32_t dcol = (p == 5) ? 0u : (uint32_t)NT;
-#pragma unroll
-          for (int st = 0; st < TCK / 8; ++st) {
-            const uint64_t da = smem_desc(a0 + pa[p] * PIECE_A + st * 256);
-            const uint64_t db = smem_desc(b0 + pb[p] * PIECE_B + st * 256);
-            const uint32_t accf = ((p == 0 || p == 5) && st == 0) ? 0u : 1u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "setp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + dcol),
-                "l"(da), "l"(db), "r"(idesc), "r"(accf)
-                : "memory");
-          }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                     : "memory");
-      }
-      if (!mbar_wait(bar, parity)) {
+    for (int q = 0; q < PB; ++q) {
+      const int e = tid + q * TC_THREADS;
+      int nn, k;
+      if (b_nfast) { nn = e % NT; k = e / NT; } else { k = e % TCK; nn = e / TCK; }
+      float h, md, l;
+      split3(xb[q], h, md, l);
+      const uint32_t o = core_off(nn, k);
+      *reinterpret_cast<float *>(Bs + o) = h;
+      *reinterpret_cast<float *>(Bs + PIECE_B + o) = md;
+      *reinterpret_cast<float *>(Bs + 2 * PIECE_B + o) = l;
+    }
+  };
+
+  if (ns > 0) load(0);
+  for (int s = 0; s < ns; ++s) {
+    const int bi = s & 1;
+    unsigned char *buf = sm + bi * STAGE;
+    // the MMAs of stage s - 2 read this buffer: wait for them (use number s/2 - 1 of its barrier)
+    if (s >= 2) {
+      if (!mbar_wait(bi ? bar1 : bar0, (uint32_t)((s / 2 - 1) & 1))) {
         atomicExch(&g_tc_wait_error, 1);
         abort_flag = 1;
       }
-      parity ^= 1u;
+    }
+    split_store(buf);
+    if (s + 1 < ns) load(s + 1);  // next stage's values in flight during the sync and the MMAs
+    // generic-proxy stores must be visible to the tensor core's async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (abort_flag) break;  // uniform: set before the barrier by some thread, read by all after it
+    if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // stage sums: hi*hi + corrections, added to the running row in registers
+      const uint32_t a0 = smem_addr(buf), b0 = smem_addr(buf + 3 * PIECE_A);
+      // correction products (smallest first) into columns [NT, 2NT), hi*hi into [0, NT);
+      // the first MMA of the CTA into each accumulator overwrites it
+      const int pa[6] = {2, 0, 1, 1, 0, 0};
+      const int pb[6] = {0, 2, 1, 0, 1, 0};
 #pragma unroll
-      for (int c0 = 0; c0 < NT; c0 += 16) {
-        uint32_t vh[16], vc[16];
+      for (int p = 0; p < 6; ++p) {
+        const uint32_t dcol = (p == 5) ? 0u : (uint32_t)NT;
+#pragma unroll
+        for (int st = 0; st < TCK / 8; ++st) {
+          const uint64_t da = smem_desc(a0 + pa[p] * PIECE_A + st * 256);
+          const uint64_t db = smem_desc(b0 + pb[p] * PIECE_B + st * 256);
+          const uint32_t accf = (s == 0 && (p == 0 || p == 5) && st == 0) ? 0u : 1u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "setp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + dcol),
+              "l"(da), "l"(db), "r"(idesc), "r"(accf)
+              : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bi ? bar1 : bar0)
+                   : "memory");
+    }
+  }
+  // the last commit tracks every MMA issued before it
+  const int last = ns - 1;
+  bool ok = !abort_flag && ns > 0;
+  if (ns > 0) {
+    if (!mbar_wait((last & 1) ? bar1 : bar0, (uint32_t)((last / 2) & 1))) {
+      atomicExch(&g_tc_wait_error, 1);
+      ok = false;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  const int row = m0 + warp * 32 + lane;
+  float *Cp = static_cast<float *>(it.C) + (int64_t)b * it.scb;
+  float *Pp = it.ksplit > 1 ? static_cast<float *>(it.part) + ((int64_t)chunk * it.batch + b) * (int64_t)it.M * it.N
+                            : nullptr;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  if (ok || ns == 0) {
+#pragma unroll
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+      uint32_t vh[16], vc[16];
+      if (ns > 0) {
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
             "%14, %15}, [%16];"
@@ -266,40 +300,31 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmItem *__r
               "=r"(vc[15])
             : "r"(trow + (uint32_t)(NT + c0)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(vh[j]) + __uint_as_float(vc[j]);
+        for (int j = 0; j < 16; ++j) vh[j] = vc[j] = 0u;
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();  // shared stage and TMEM accumulators may be overwritten now
-      if (abort_flag) break;
-    }
-    if (abort_flag) break;
-  }
-
-  // ---- epilogue: registers -> global
-  if (!abort_flag) {
-    const int row = m0 + warp * 32 + lane;
-    if (row < M) {
-      float *Cp = static_cast<float *>(it.C) + (int64_t)b * it.scb;
-      float *Pp = it.ksplit > 1
-                      ? static_cast<float *>(it.part) + ((int64_t)chunk * it.batch + b) * (int64_t)it.M * it.N
-                      : nullptr;
+      if (row < M) {
 #pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        const int col = n0 + j;
-        if (j >= n_here) continue;
-        if (Pp) {
-          Pp[(int64_t)col * it.M + row] = acc[j];
-        } else {
-          float *c = Cp + (int64_t)row * it.scm + (int64_t)col * it.scn;
-          float out = (float)it.alpha * acc[j];
-          if (it.beta != 0.0) out += (float)it.beta * *c;
-          *c = out;
+        for (int j = 0; j < 16; ++j) {
+          if (c0 + j >= n_here) continue;
+          const int col = n0 + c0 + j;
+          const float v = __uint_as_float(vh[j]) + __uint_as_float(vc[j]);
+          if (Pp) {
+            Pp[(int64_t)col * it.M + row] = v;
+          } else {
+            float *c = Cp + (int64_t)row * it.scm + (int64_t)col * it.scn;
+            float out = (float)it.alpha * v;
+            if (it.beta != 0.0) out += (float)it.beta * *c;
+            *c = out;
+          }
         }
       }
     }
-  } else {
-    mbar_wait(bar, parity ^ 1u);  // let an abandoned stage's MMAs finish before TMEM is released
+  } else if (ns > 0) {
+    // abandoned: let every issued MMA finish (bounded) before the TMEM is released
+    mbar_wait(bar0, 0u);
+    mbar_wait(bar1, 0u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -310,7 +335,7 @@ __global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const GemmItem *__r
 
 }  // namespace
 
-size_t gemm_tc_smem_bytes() { return 3 * (size_t)PIECE_A + 3 * (size_t)PIECE_B + 1024; }
+size_t gemm_tc_smem_bytes() { return 2 * (3 * (size_t)PIECE_A + 3 * (size_t)PIECE_B) + 1024; }
 
 cudaError_t launch_gemm_tc(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, cudaStream_t s) {
   if (n_items <= 0 || total_tiles <= 0) return cudaSuccess;
