@@ -401,8 +401,9 @@ def main():
     psteps = max(2, min(args.steps, 5))
     prof = profiled_arm(htgb.HT_F32, htgb.HT_PREC_FP32, psteps)
     roofline = None
-    if prof["prof"]:
-        name, rec = max(prof["prof"].items(), key=lambda kv: kv[1]["ms"])
+    arith = {k: v for k, v in prof["prof"].items() if v["flops"] > 0}  # families with an arithmetic roofline
+    if arith:
+        name, rec = max(arith.items(), key=lambda kv: kv[1]["ms"])
         per_launch_ms = rec["ms"] / rec["launches"]
         per_launch_flops = rec["flops"] / rec["launches"]
         ach = per_launch_flops / (per_launch_ms / 1e3)

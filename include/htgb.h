@@ -217,6 +217,15 @@ ht_status ht_graph_free(ht_graph *graph);
 
 /* ||X||: orthogonalizes a copy, returns ||B_D||_F (Sec. 3.4).  Synchronises. */
 ht_status ht_norm(const ht_tensor *x, double *out);
+/* Inner product <X, Y> (Sec. 3.2, Lemma "phi"): Phi_t = U_t^T V_t computed
+ * bottom-up from the leaves (Phi = U^T V) through the transfer tensors,
+ * Phi_t = M_1(B_t) (Phi_s1 (x) Phi_s2) M_1(B'_t)^T, one batched launch per
+ * contraction and tree level; the root's 1 x 1 Phi is <X, Y>.  X and Y: same
+ * d, mode sizes and dtype, any ranks; neither needs to be orthogonal.  The
+ * sum runs in the tensors' dtype (F32: FP32 contractions, long reductions
+ * split with FP64 partial sums).  Synchronises.  Errors: HT_EINVAL. */
+ht_status ht_inner(const ht_tensor *x, const ht_tensor *y, double *out);
+
 /* Entries X[idx[e*d + 0], ..., idx[e*d + d-1]] for e < m (Sec. 3.1, eq.
  * "transfermult").  idx and out are host arrays.  Synchronises. */
 ht_status ht_eval_entries(const ht_tensor *x, const int64_t *idx, int64_t m, double *out);

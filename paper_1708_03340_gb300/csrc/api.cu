@@ -1581,6 +1581,143 @@ void plan_project(Plan &P, std::vector<TState> &TS, const int *rank_array) {
   }
 }
 
+// ---- inner product <X, Y> (Sec. 3.2, Definition "phi", Lemma "phi") -------
+// Phi_t = U_t^T V_t bottom-up: leaves Phi = U^T V; inner nodes
+// Phi_t[i, i'] = sum B_t[i, j, l] Phi_s1[j, j'] Phi_s2[l, l'] B'_t[i', j', l'],
+// as three contractions per node: T1 = Phi_s1 B'_t (mode 2), T2 = Phi_s2 T1
+// (mode 3), Phi_t = M_1(B_t) M_1(T2)^T; the root's 1 x 1 Phi is <X, Y>.
+void *plan_inner(Plan &P, const ht_tensor *x, const ht_tensor *y) {
+  const ht_tree &T = x->tr;
+  const size_t esz = P.esz;
+  std::vector<void *> phi(T.nn);
+  for (int t = 0; t < T.nn; ++t) {
+    const int kx = (t == 0) ? 1 : x->k[t], ky = (t == 0) ? 1 : y->k[t];
+    phi[t] = P.palloc_bytes((size_t)kx * ky * esz);
+  }
+  constexpr int kChunk = 256;
+  auto split_for = [&](int ko, int tiles_total) {
+    return std::max(1, std::min(ko, (2 * kSmCount + tiles_total - 1) / std::max(tiles_total, 1)));
+  };
+  for (int h = 0; h <= T.max_height; ++h) {
+    P.sreset();
+    if (h == 0) {
+      int tiles = 0;
+      for (int t = 0; t < T.nn; ++t)
+        if (is_leaf(T, t)) tiles += ((x->k[t] + 63) / 64) * ((y->k[t] + 63) / 64);
+      P.begin(L_GEMM);
+      for (int t = 0; t < T.nn; ++t) {
+        if (!is_leaf(T, t)) continue;
+        const int64_t n = x->n[T.lo[t]];
+        GemmItem g = gemm0();
+        g.A = node_ptr(x, t);  // U^T: element (m, k) = U[k, m]
+        g.sam = n;
+        g.sak = 1;
+        g.sako = kChunk;
+        g.B = node_ptr(y, t);
+        g.sbk = 1;
+        g.sbn = n;
+        g.sbko = kChunk;
+        g.C = phi[t];
+        g.scm = 1;
+        g.scn = x->k[t];
+        g.M = x->k[t];
+        g.N = y->k[t];
+        g.K = (int)std::min<int64_t>(n, kChunk);
+        g.Ko = (int)((n + kChunk - 1) / kChunk);
+        g.k_total = n;
+        g.ksplit = split_for(g.Ko, tiles);
+        P.gemm(g, t);
+      }
+      continue;
+    }
+    struct Job {
+      int t, K0, K0y, k1, k2, k1y, k2y;
+      void *T1, *T2;
+    };
+    std::vector<Job> jobs;
+    for (int t = 0; t < T.nn; ++t) {
+      if (is_leaf(T, t) || T.height[t] != h) continue;
+      Job J;
+      J.t = t;
+      J.K0 = (t == 0) ? 1 : x->k[t];
+      J.K0y = (t == 0) ? 1 : y->k[t];
+      J.k1 = x->k[T.s1[t]];
+      J.k2 = x->k[T.s2[t]];
+      J.k1y = y->k[T.s1[t]];
+      J.k2y = y->k[T.s2[t]];
+      J.T1 = P.salloc_bytes((size_t)J.K0y * J.k1 * J.k2y * esz);
+      J.T2 = P.salloc_bytes((size_t)J.K0y * J.k1 * J.k2 * esz);
+      jobs.push_back(J);
+    }
+    // T1[i'][j][l'] = sum_j' Phi_s1[j, j'] B'[i', j', l']
+    P.begin(L_GEMM);
+    for (Job &J : jobs) {
+      GemmItem g = gemm0();
+      g.A = phi[T.s1[J.t]];
+      g.sam = 1;
+      g.sak = J.k1;
+      g.B = node_ptr(y, J.t);
+      g.sbk = J.k2y;
+      g.sbn = 1;
+      g.sbb = (int64_t)J.k1y * J.k2y;
+      g.C = J.T1;
+      g.scm = J.k2y;
+      g.scn = 1;
+      g.scb = (int64_t)J.k1 * J.k2y;
+      g.M = J.k1;
+      g.N = J.k2y;
+      g.K = J.k1y;
+      g.batch = J.K0y;
+      P.gemm(g, J.t);
+    }
+    // T2[i'][j][l] = sum_l' Phi_s2[l, l'] T1[i'][j][l']
+    P.begin(L_GEMM);
+    for (Job &J : jobs) {
+      GemmItem g = gemm0();
+      g.A = phi[T.s2[J.t]];
+      g.sam = 1;
+      g.sak = J.k2;
+      g.B = J.T1;
+      g.sbk = 1;
+      g.sbn = J.k2y;
+      g.C = J.T2;
+      g.scm = 1;
+      g.scn = J.k2;
+      g.M = J.k2;
+      g.N = J.K0y * J.k1;
+      g.K = J.k2y;
+      P.gemm(g, J.t);
+    }
+    // Phi_t[i, i'] = sum_{j,l} B[i][j][l] T2[i'][j][l]
+    int tiles = 0;
+    for (Job &J : jobs) tiles += ((J.K0 + 63) / 64) * ((J.K0y + 63) / 64);
+    P.begin(L_GEMM);
+    for (Job &J : jobs) {
+      const int64_t red = (int64_t)J.k1 * J.k2;
+      GemmItem g = gemm0();
+      g.A = node_ptr(x, J.t);
+      g.sam = red;
+      g.sak = 1;
+      g.sako = kChunk;
+      g.B = J.T2;
+      g.sbk = 1;
+      g.sbn = red;
+      g.sbko = kChunk;
+      g.C = phi[J.t];
+      g.scm = 1;
+      g.scn = J.K0;
+      g.M = J.K0;
+      g.N = J.K0y;
+      g.K = (int)std::min<int64_t>(red, kChunk);
+      g.Ko = (int)((red + kChunk - 1) / kChunk);
+      g.k_total = red;
+      g.ksplit = split_for(g.Ko, tiles);
+      P.gemm(g, J.t);
+    }
+  }
+  return phi[0];
+}
+
 ht_status check_prec(const ht_tensor *x, int prec) {
   if (prec == HT_PREC_FP64 && x->dtype != HT_F64)
     return fail(HT_EUNSUPPORTED, "HT_PREC_FP64 needs an HT_F64 tensor");
@@ -2254,6 +2391,31 @@ ht_status ht_norm(const ht_tensor *xc, double *out) {
   }
   ht_tensor_free(y);
   return st;
+}
+
+ht_status ht_inner(const ht_tensor *xc, const ht_tensor *yc, double *out) {
+  if (!xc || !yc || !out) return fail(HT_EINVAL, "null argument");
+  HT_TRY(add_check(xc, yc));
+  ht_tensor *x = const_cast<ht_tensor *>(xc), *y = const_cast<ht_tensor *>(yc);
+  HT_TRY(sync_ranks(x));
+  HT_TRY(sync_ranks(y));
+  if (x->stream != y->stream) HT_CU(cudaStreamSynchronize(y->stream));
+  Plan P;
+  P.dtype = x->dtype;
+  P.esz = x->esz;
+  void *root = plan_inner(P, x, y);
+  char *pb = nullptr;
+  HT_TRY(run_plan(P, x->stream, &pb));
+  const void *d_root = reloc(root, pb, nullptr, nullptr);
+  double v = 0.0;
+  float vf = 0.0f;
+  cudaError_t e = (x->dtype == HT_F64) ? cudaMemcpyAsync(&v, d_root, sizeof(double), cudaMemcpyDeviceToHost, x->stream)
+                                       : cudaMemcpyAsync(&vf, d_root, sizeof(float), cudaMemcpyDeviceToHost, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  cudaFreeAsync(pb, x->stream);
+  if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  *out = (x->dtype == HT_F64) ? v : (double)vf;
+  return HT_OK;
 }
 
 ht_status ht_eval_entries(const ht_tensor *xc, const int64_t *idx, int64_t m, double *out) {

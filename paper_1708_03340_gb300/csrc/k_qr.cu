@@ -121,13 +121,11 @@ __global__ void __launch_bounds__(QR_THREADS) qr_block_kernel(const QrItem *__re
 //
 // Column j's reflector H_j = I - tau_j v_j v_j^T, v_j = [0; 1; scl_j w_j],
 // where w_j is the part of column j below the diagonal (after H_0..H_{j-1}).
-// The group owning column j publishes w_j (rows <= j zero) and alpha_j (the
-// diagonal entry) in shared memory; after one barrier every warp forms
-// ||w_j||, beta_j, tau_j and scl_j itself (the same sums in the same order,
-// so the same bits everywhere) and applies H_j to its columns right of j.
-// The owner of column j+1 then publishes w_{j+1}.  The critical path per
-// column is one shared-memory round trip, one reduction, a square root and
-// a division; no warp waits for another to build the reflector.
+// The group owning column j forms ||w_j||, beta_j, tau_j and scl_j from its
+// registers and publishes them with w_j in shared memory; after one barrier
+// every warp holding a column right of j applies H_j (one dot product per
+// column, 3 shuffles), and the owner of column j+1 publishes the next
+// reflector.  One barrier per column.
 //
 // The w_j stay in shared memory, so Q = H_0 ... H_{n-1} [I; 0] is then
 // accumulated backwards on the columns in registers without barriers.
@@ -180,12 +178,14 @@ __device__ __forceinline__ void row_sub(T (&a)[NI][4], int j, int s, T d) {
       if (32 * i + 4 * s + e == j) a[i][e] -= d;
 }
 
-// Publish w_j of column j (rows <= j zero) into wj and alpha_j; only the
-// lanes with me set (the owner group) write.  Called by the whole warp.
+// Publish column j's reflector: w_j (the part below the diagonal, rows <= j
+// zero) into wj, and tau_j, scl_j, beta_j (R(j, j)) formed from ||w_j|| and
+// alpha_j = the diagonal entry; only the lanes with me set (the owner group)
+// write.  Called by the whole warp (the reductions span it).
 template <typename T, int NI>
-__device__ __forceinline__ void publish(const T (&a)[NI][4], T *wj, T *alpha_j, int j, int s, bool me) {
-  const T al = group_sum(row_of<T, NI>(a, j, s));
-  if (!me) return;
+__device__ __forceinline__ void publish(const T (&a)[NI][4], T *wj, T *tau_j, T *scl_j, T *beta_j, int j, int s,
+                                        bool me) {
+  T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     T x[4];
@@ -194,9 +194,25 @@ __device__ __forceinline__ void publish(const T (&a)[NI][4], T *wj, T *alpha_j, 
       const int r = 32 * i + 4 * s + e;
       x[e] = (i >= 2 || r > j) ? a[i][e] : T(0);  // j < 64: rows of chunks i >= 2 lie below j
     }
-    st4(wj + 32 * i + 4 * s, x);
+    q0 += x[0] * x[0];
+    q1 += x[1] * x[1];
+    q2 += x[2] * x[2];
+    q3 += x[3] * x[3];
+    if (me) st4(wj + 32 * i + 4 * s, x);
   }
-  if (s == 0) *alpha_j = al;
+  const T s2 = group_sum((q0 + q1) + (q2 + q3));
+  const T alpha = group_sum(row_of<T, NI>(a, j, s));
+  if (!me || s != 0) return;
+  T tj = T(0), beta = alpha, sc = T(0);
+  if (s2 != T(0)) {
+    const T nrm = sqrt(alpha * alpha + s2);
+    beta = (alpha <= T(0)) ? nrm : -nrm;
+    tj = (beta - alpha) / beta;
+    sc = T(1) / (alpha - beta);
+  }
+  *tau_j = tj;
+  *scl_j = sc;
+  *beta_j = beta;
 }
 
 // a <- H_j a for the lane's column: d = a_j + scl (w^T a), a -= tau d v.
@@ -247,7 +263,7 @@ __global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restric
   T *W = reinterpret_cast<T *>(smem_raw);  // REG_MR x n: w_j in column j
   T *tau = W + (int64_t)REG_MR * n;        // n
   T *scl = tau + n;                        // n
-  T *alp = scl + n;                        // n
+  T *bet = scl + n;                        // n: R(j, j)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 3, s = lane & 7;
   const int c = 4 * warp + g;  // this lane's column
@@ -260,74 +276,25 @@ __global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restric
       const int r = 32 * i + 4 * s + e;
       a[i][e] = (c < n && r < m) ? A[r] : T(0);
     }
-  if (warp == 0) publish<T, NI>(a, W, alp, 0, s, g == 0);
+  if (warp == 0) publish<T, NI>(a, W, tau, scl, bet, 0, s, g == 0);
   for (int j = 0; j < n; ++j) {
     __syncthreads();
     if (4 * warp + 3 < j) continue;  // every column of this warp is finished
     const T *wj = W + (int64_t)j * REG_MR;
-    // one pass over w_j: ||w_j||^2 and w_j^T a
-    T v[KEEP ? NI : 1][4];
-    T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
-    T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
-#pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      T x[4];
-      ld4(wj + 32 * i + 4 * s, x);
-      q0 += x[0] * x[0];
-      q1 += x[1] * x[1];
-      q2 += x[2] * x[2];
-      q3 += x[3] * x[3];
-      d0 += x[0] * a[i][0];
-      d1 += x[1] * a[i][1];
-      d2 += x[2] * a[i][2];
-      d3 += x[3] * a[i][3];
-      if (KEEP) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) v[KEEP ? i : 0][e] = x[e];
-      }
-    }
-    const T s2 = group_sum((q0 + q1) + (q2 + q3));
-    const T sw = group_sum((d0 + d1) + (d2 + d3));
-    const T aj = group_sum(row_of<T, NI>(a, j, s));
-    // the reflector of column j, formed by every warp from the same sums
-    const T alpha = alp[j];
-    T tj = T(0), beta = alpha, sc = T(0);
-    if (s2 != T(0)) {
-      const T nrm = sqrt(alpha * alpha + s2);
-      beta = (alpha <= T(0)) ? nrm : -nrm;
-      tj = (beta - alpha) / beta;
-      sc = T(1) / (alpha - beta);
-    }
+    const T tj = tau[j], sc = scl[j];
     if (c == j) {  // the owner: R(j, j) = beta; rows below j are not read again
+      const T beta = bet[j];
 #pragma unroll
       for (int i = 0; i < 2 && i < NI; ++i)
 #pragma unroll
         for (int e = 0; e < 4; ++e)
           if (32 * i + 4 * s + e == j) a[i][e] = beta;
-      if (s == 0) {
-        tau[j] = tj;
-        scl[j] = sc;
-      }
     }
-    if (c > j && tj != T(0)) {  // H_j on the columns right of j: a -= tau (a_j + scl w^T a) [e_j + scl w]
-      const T d = tj * (aj + sc * sw);
-      const T ds = d * sc;
-      row_sub<T, NI>(a, j, s, d);
-#pragma unroll
-      for (int i = 0; i < NI; ++i) {
-        T x[4];
-        if (KEEP) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) x[e] = v[KEEP ? i : 0][e];
-        } else {
-          ld4(wj + 32 * i + 4 * s, x);
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) a[i][e] -= ds * x[e];
-      }
-    }
-    if (j + 1 < n && warp == ((j + 1) >> 2))  // the owner warp of column j+1 publishes w_{j+1}
-      publish<T, NI>(a, W + (int64_t)(j + 1) * REG_MR, alp + j + 1, j + 1, s, g == ((j + 1) & 3));
+    if (4 * warp + 3 > j && tj != T(0))  // H_j on the columns right of j
+      reg_apply<T, NI, KEEP>(a, wj, j, tj, sc, c > j, s);
+    if (j + 1 < n && warp == ((j + 1) >> 2))  // the owner warp of column j+1 publishes its reflector
+      publish<T, NI>(a, W + (int64_t)(j + 1) * REG_MR, tau + j + 1, scl + j + 1, bet + j + 1, j + 1, s,
+                     g == ((j + 1) & 3));
   }
   __syncthreads();
   // R (n x n upper triangular) from the registers

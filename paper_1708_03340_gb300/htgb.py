@@ -33,7 +33,7 @@ EXPORTS = [
     "ht_add", "ht_add_into", "ht_orthogonalize", "ht_gramians", "ht_truncate",
     "ht_truncate_batch", "ht_norm", "ht_eval_entries", "ht_last_error",
     "ht_profile_set", "ht_profile_read", "ht_launch_count", "ht_gramians_noalloc",
-    "ht_graph_add_truncate", "ht_graph_launch", "ht_graph_kernels", "ht_graph_free",
+    "ht_graph_add_truncate", "ht_graph_launch", "ht_graph_kernels", "ht_graph_free", "ht_inner",
 ]
 HT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 HT_K_GEMM, HT_K_QR, HT_K_EIG, HT_K_COPY, HT_K_COMPACT, HT_K_RANKS, HT_K_ADD, HT_K_EVAL, HT_K_MISC = range(9)
@@ -120,6 +120,7 @@ def load(build_if_missing: bool = True):
             "ht_graph_launch": ([vp], ctypes.c_int),
             "ht_graph_kernels": ([vp, i32p], ctypes.c_int),
             "ht_graph_free": ([vp], ctypes.c_int),
+            "ht_inner": ([vp, vp, f64p], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -302,6 +303,12 @@ def ht_graph_free(g):
     _check(load().ht_graph_free(g))
 
 
+def ht_inner(x, y) -> float:
+    v = ctypes.c_double()
+    _check(load().ht_inner(x, y, ctypes.byref(v)))
+    return v.value
+
+
 def ht_norm(x) -> float:
     v = ctypes.c_double()
     _check(load().ht_norm(x, ctypes.byref(v)))
@@ -409,6 +416,9 @@ class HTTensor:
 
     def norm(self) -> float:
         return ht_norm(self.handle)
+
+    def inner(self, other: "HTTensor") -> float:
+        return ht_inner(self.handle, other.handle)
 
     def eval(self, idx) -> np.ndarray:
         return ht_eval_entries(self.handle, idx)
