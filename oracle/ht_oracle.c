@@ -803,5 +803,64 @@ double ho_inner(int d, const int64_t *n, const int *ka, const double *xa, const 
 }
 
 /* Direct access to the dense building blocks, for their own pins. */
+/* Application of an H-operator to an H-tensor, Lemma "operator" (Sec. 3.6):
+ * C = L A with L stored as an HT tensor over the index pairs (j_mu, i_mu)
+ * (eq. "operatorastensor"), pair (j, i) flattened as j + i m_mu, i.e. the
+ * leaf columns of L are column-major m_mu x n_mu matrices W_r.  Ranks of C
+ * are kbar_t k_t, the pair index (p, i) of (operator rank, tensor rank)
+ * flattened as p k_t + i.  Leaves: V[:, r k + l] = W_r U[:, l]
+ * (eq. "operatorleafframes"); inner nodes: F_t = H_t (x) B_t,
+ * F[(p,i),(q,j),(r,l)] = H[p,q,r] B[i,j,l].
+ *   d, n (tensor mode sizes), m (output mode sizes), kop/xop (operator, mode
+ *   sizes m n), kx/xx (tensor), kout/xout (result). */
+int ho_apply(int d, const int64_t *n, const int64_t *m, const int *kop, const double *xop, const int *kx,
+             const double *xx, int *kout, double *xout) {
+  otree T;
+  if (d < 2 || tree_init(&T, d)) return -1;
+  int64_t *mn = (int64_t *)malloc(sizeof(int64_t) * (size_t)d);
+  for (int mu = 0; mu < d; ++mu) mn[mu] = m[mu] * n[mu];
+  for (int t = 0; t < T.nn; ++t) kout[t] = (t == 0) ? 1 : kop[t] * kx[t];
+  int64_t *oo = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)(T.nn + 1));
+  int64_t *ox = oo + T.nn + 1, *oc = ox + T.nn + 1;
+  node_offsets(&T, mn, kop, oo);
+  node_offsets(&T, n, kx, ox);
+  node_offsets(&T, m, kout, oc);
+  for (int t = 0; t < T.nn; ++t) {
+    const double *H = xop + oo[t], *B = xx + ox[t];
+    double *F = xout + oc[t];
+    if (is_leaf(&T, t)) {
+      const int mu = T.lo[t];
+      const int64_t mm = m[mu], nm = n[mu];
+      const int kb = kop[t], k = kx[t];
+      for (int r = 0; r < kb; ++r)
+        for (int l = 0; l < k; ++l)
+          for (int64_t j = 0; j < mm; ++j) {
+            double acc = 0.0;
+            for (int64_t i = 0; i < nm; ++i) acc += H[(int64_t)r * mm * nm + j + i * mm] * B[(int64_t)l * nm + i];
+            F[((int64_t)r * k + l) * mm + j] = acc;
+          }
+    } else {
+      const int s1 = T.s1[t], s2 = T.s2[t];
+      const int pt = (t == 0) ? 1 : kop[t], p1 = kop[s1], p2 = kop[s2];
+      const int it = (t == 0) ? 1 : kx[t], i1 = kx[s1], i2 = kx[s2];
+      const int o1 = p1 * i1, o2 = p2 * i2;
+      for (int p = 0; p < pt; ++p)
+        for (int i = 0; i < it; ++i)
+          for (int q = 0; q < p1; ++q)
+            for (int j = 0; j < i1; ++j)
+              for (int r = 0; r < p2; ++r)
+                for (int l = 0; l < i2; ++l) {
+                  const int64_t I = (int64_t)p * it + i, J = (int64_t)q * i1 + j, L = (int64_t)r * i2 + l;
+                  F[(I * o1 + J) * o2 + L] =
+                      H[((int64_t)p * p1 + q) * p2 + r] * B[((int64_t)i * i1 + j) * i2 + l];
+                }
+    }
+  }
+  free(oo);
+  free(mn);
+  tree_free(&T);
+  return 0;
+}
+
 void ho_qr(int64_t m, int n, const double *A, double *Q, double *R) { hh_qr(m, n, A, m, Q, R); }
 void ho_eig_sym(int n, const double *A, double *w, double *V) { jacobi_eig(n, A, w, V); }

@@ -56,6 +56,7 @@ def _load():
             lib.ho_eval.argtypes = [ctypes.c_int, i64p, i32p, f64p, ctypes.c_int64, i64p, f64p]
             lib.ho_inner.argtypes = [ctypes.c_int, i64p, i32p, f64p, i32p, f64p]
             lib.ho_inner.restype = ctypes.c_double
+            lib.ho_apply.argtypes = [ctypes.c_int, i64p, i64p, i32p, f64p, i32p, f64p, i32p, f64p]
             lib.ho_qr.argtypes = [ctypes.c_int64, ctypes.c_int, f64p, f64p, f64p]
             lib.ho_eig_sym.argtypes = [ctypes.c_int, f64p, f64p, f64p]
             _lib = lib
@@ -210,6 +211,25 @@ def inner(d, n, ka, xa, kc, xc) -> float:
     n, ka, kc, xa, xc = _i64(n), _i32(ka), _i32(kc), _f64(xa), _f64(xc)
     return float(_load().ho_inner(d, _p(n, ctypes.c_int64), _p(ka, ctypes.c_int), _p(xa, ctypes.c_double),
                                   _p(kc, ctypes.c_int), _p(xc, ctypes.c_double)))
+
+
+def apply(d, n, m, kop, xop, kx, xx):
+    """C = L X (Lemma "operator", Sec. 3.6): L an HT tensor over the index pairs
+    (j_mu, i_mu), mode sizes m_mu n_mu, pair (j, i) flattened as j + i m_mu.
+    Returns (kout, xout) with kout_t = kop_t kx_t, pair (p, i) as p kx_t + i."""
+    n, m = _i64(n), _i64(m)
+    if n.size == 1:
+        n = np.full(d, int(n[0]), np.int64)
+    if m.size == 1:
+        m = np.full(d, int(m[0]), np.int64)
+    kop, kx, xop, xx = _i32(kop), _i32(kx), _f64(xop), _f64(xx)
+    kout = np.array([1] + [int(kop[t]) * int(kx[t]) for t in range(1, 2 * d - 1)], np.int32)
+    xout = np.zeros(size(d, m, kout), np.float64)
+    rc = _load().ho_apply(d, _p(n, ctypes.c_int64), _p(m, ctypes.c_int64), _p(kop, ctypes.c_int), _p(xop, ctypes.c_double),
+                          _p(kx, ctypes.c_int), _p(xx, ctypes.c_double), _p(kout, ctypes.c_int), _p(xout, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError("ho_apply failed")
+    return kout, xout
 
 
 def qr(a):

@@ -104,3 +104,44 @@ def test_batch_mixed_gramian_sizes(dtype):
         got = X.eval(idx)
         want = O.eval_entries(d, nvec, ref["k"], ref["x"], idx)
         assert np.abs(got - want).max() <= tol * ref["norm"], i
+
+
+def test_batched_wave_in_benchmark_configuration():
+    """The batched workload as the benchmark runs it: a CUDA graph over a wave
+    of uneven tensors (sums of 4, ranks 4k up to 192, per-tensor caps), FP32
+    path.  The three cheapest tensors of the wave are recomputed by the oracle
+    (on the FP32-rounded addends) and compared entrywise; every tensor's ranks
+    obey its cap."""
+    specs = I.batched_specs(count=4096, seed=41)[:16]
+    dtype = htgb.HT_F32
+    A, C, X, trees = [], [], [], []
+    for (d, n, k, s) in specs:
+        tr = htgb.HTTree(d)
+        trees.append(tr)
+        T = [htgb.HTTensor.from_blob(tr, nv, kv, xv, dtype) for (nv, kv, xv) in I.batched_terms((d, n, k, s))]
+        a, c = T[0].add(T[1]), T[2].add(T[3])
+        kk = a.ranks() + c.ranks()
+        kk[0] = 1
+        A.append(a), C.append(c), X.append(htgb.HTTensor.create(tr, a.n, kk, dtype))
+    opts = htgb.make_opts(mode="rank", prec=htgb.HT_PREC_FP32, tensor_caps=[sp[2] for sp in specs])
+    g = htgb.ht_graph_add_truncate([a.handle for a in A], [c.handle for c in C], [x.handle for x in X], opts)
+    try:
+        htgb.ht_graph_launch(g)
+        for x, sp in zip(X, specs):
+            assert max(x.ranks()[1:]) <= sp[2]
+        cost = [(sp[0] - 2) * (4 * sp[2]) ** 4 + sp[0] * sp[1] * (4 * sp[2]) ** 2 for sp in specs]
+        for i in np.argsort(cost)[:3]:
+            d, n, k, s = specs[i]
+            terms = I.batched_terms((d, n, k, s))
+            nv = terms[0][0]
+            kk, xx = terms[0][1], as_stored(terms[0][2], dtype)
+            for (_, kv, xv) in terms[1:]:
+                kk, xx = O.add(d, nv, kk, xx, kv, as_stored(xv, dtype))
+            ref = O.truncate(d, nv, kk, xx, mode="rank", rank_cap=k)
+            assert list(X[i].ranks()) == list(ref["k"])
+            idx = sample_idx(nv, 200, int(i))
+            got = X[i].eval(idx)
+            want = O.eval_entries(d, nv, ref["k"], ref["x"], idx)
+            assert np.abs(got - want).max() <= 1e-5 * ref["norm"], (i, specs[i])
+    finally:
+        htgb.ht_graph_free(g)

@@ -287,3 +287,45 @@ def test_golden_diagonal_tensor():
     assert abs(err - g["trunc_err"]) < 1e-13
     res = O.truncate(d, n, k, x, mode="eps", eps=g["eps_abs"], eps_relative=False)
     assert list(res["k"][1:]) == [g["eps_rank"]] * 6
+
+
+def _full(d, n, k, x):
+    """All entries of an HT tensor by the oracle's evaluation (pinned above), C order."""
+    n = np.broadcast_to(np.asarray(n, np.int64), (d,))
+    idx = np.stack(np.meshgrid(*[np.arange(v) for v in n], indexing="ij"), axis=-1).reshape(-1, d)
+    return O.eval_entries(d, n, k, x, idx).reshape(tuple(int(v) for v in n))
+
+
+def test_operator_application_equals_full_matrix_vector():
+    """Lemma "operator" (Sec. 3.6): the HT representation of C = L X equals the
+    product of the full operator (built entry by entry from its own HT
+    representation over the index pairs (j, i) = j + i m) with the full tensor."""
+    d, m, n = 4, 3, 4
+    op = I.random_ht(d, m * n, 2, 31)
+    x = I.random_ht(d, n, 3, 32)
+    kc, xc = O.apply(d, n, m, op[1], op[2], x[1], x[2])
+    assert list(kc[1:]) == [2 * 3] * (2 * d - 2)
+    L = _full(d, m * n, op[1], op[2])          # L[(j1,i1), ..., (j4,i4)]
+    L = L.reshape(n, m, n, m, n, m, n, m)        # axis pair (i, j) from e = j + i m
+    X = _full(d, n, x[1], x[2])
+    C = np.einsum("aebfcgdh,abcd->efgh", L, X)   # axes (i1, j1, ..., i4, j4); C[j] = sum_i L[(j,i)] X[i]
+    got = _full(d, m, kc, xc)
+    assert np.abs(got - C).max() <= 1e-12 * np.abs(C).max()
+
+
+def test_identity_operator_returns_the_tensor():
+    d, n = 5, [4, 6, 3, 5, 2]
+    x = I.random_ht(d, n, 3, 33)
+    tr = I.tree(d)
+    nodes = []
+    for t in range(2 * d - 1):
+        if tr["son1"][t] < 0:
+            nm = n[tr["lo"][t]]
+            nodes.append(np.eye(nm).reshape(-1, 1, order="F"))
+        else:
+            nodes.append(np.ones((1, 1)) if t == 0 else np.ones((1, 1, 1)))
+    kop = np.ones(2 * d - 1, np.int32)
+    xop = I.nodes_blob(d, nodes)
+    kc, xc = O.apply(d, n, n, kop, xop, x[1], x[2])
+    assert list(kc) == list(x[1])
+    assert np.array_equal(xc, np.asarray(x[2], np.float64))
