@@ -151,6 +151,19 @@ ht_status ht_add(const ht_tensor *a, const ht_tensor *c, ht_tensor **out);
 /* Same, into an existing tensor whose ranks already equal k + kbar (no allocation). */
 ht_status ht_add_into(const ht_tensor *a, const ht_tensor *c, ht_tensor *out);
 
+/* Application of an H-operator to an H-tensor, Lemma "operator" (Sec. 3.6):
+ * out = L X.  The operator L is an HT tensor over the index pairs
+ * (j_mu, i_mu) (eq. "operatorastensor"), i.e. an ht_tensor with mode sizes
+ * m_mu n_mu whose leaf columns are column-major m_mu x n_mu matrices W_r
+ * (pair (j, i) at j + i m_mu); X has mode sizes n_mu; out must be created with
+ * mode sizes m_mu and capacities kbar_t k_t (kbar: ranks of L, k: of X).
+ * Leaves: V[:, r k + l] = W_r U[:, l] (eq. "operatorleafframes", batched
+ * products); inner nodes: F_t = H_t (x) B_t, the pair (p, i) of (operator
+ * rank, tensor rank) at p k_t + i.  The ranks of out become kbar_t k_t;
+ * truncate it with ht_truncate.  Same tree and dtype for all three.  Errors:
+ * HT_EINVAL (shapes, capacities), HT_ENOMEM, HT_ECUDA. */
+ht_status ht_apply(const ht_tensor *op, const ht_tensor *x, ht_tensor *out);
+
 /* Orthogonalization, Sec. 3.4 (leaves -> root): QR of every leaf frame and of
  * M_{2,3}(B_t) of every inner node after B_t <- (I, R_s1, R_s2) o B_t; the root
  * becomes R_t1 B_D R_t2^T.  In place; ranks become min(n, k) at leaves and

@@ -2018,6 +2018,87 @@ ht_status ht_add_into(const ht_tensor *a, const ht_tensor *c, ht_tensor *out) {
   return add_pack(a, c, out);
 }
 
+ht_status ht_apply(const ht_tensor *op, const ht_tensor *x, ht_tensor *out) {
+  if (!op || !x || !out) return fail(HT_EINVAL, "null argument");
+  if (op->tr.d != x->tr.d || out->tr.d != x->tr.d) return fail(HT_EINVAL, "tensors have different d");
+  if (op->dtype != x->dtype || out->dtype != x->dtype) return fail(HT_EINVAL, "tensors have different dtype");
+  const ht_tree &T = x->tr;
+  for (int mu = 0; mu < T.d; ++mu)
+    if (op->n[mu] != out->n[mu] * x->n[mu])
+      return fail(HT_EINVAL, "operator mode size must be (output mode size) x (tensor mode size)");
+  HT_TRY(sync_ranks(const_cast<ht_tensor *>(op)));
+  HT_TRY(sync_ranks(const_cast<ht_tensor *>(x)));
+  for (int t = 1; t < T.nn; ++t)
+    if (out->cap[t] != op->k[t] * x->k[t]) return fail(HT_EINVAL, "output capacity must equal kbar_t k_t");
+  cudaStream_t s = out->stream;
+  if (op->stream != s) HT_CU(cudaStreamSynchronize(op->stream));
+  if (x->stream != s) HT_CU(cudaStreamSynchronize(x->stream));
+  out->k = out->cap;
+  out->k[0] = 1;
+  out->orthogonal = false;
+  HT_TRY(upload_ranks(out));
+  // leaves: V[:, r k + l] = W_r U[:, l], W_r the m x n column-major matrix in column r of the operator's leaf
+  Plan P;
+  P.dtype = x->dtype;
+  P.esz = x->esz;
+  P.begin(L_GEMM);
+  for (int t = 0; t < T.nn; ++t) {
+    if (!is_leaf(T, t)) continue;
+    const int mu = T.lo[t];
+    const int64_t m = out->n[mu], n = x->n[mu];
+    const int kb = op->k[t], k = x->k[t];
+    GemmItem g = gemm0();
+    g.A = node_ptr(op, t);
+    g.sam = 1;
+    g.sak = m;
+    g.sab = m * n;
+    g.B = node_ptr(x, t);
+    g.sbk = 1;
+    g.sbn = n;
+    g.sbb = 0;
+    g.C = node_ptr(out, t);
+    g.scm = 1;
+    g.scn = m;
+    g.scb = m * k;
+    g.M = (int)m;
+    g.N = k;
+    g.K = (int)n;
+    g.batch = kb;
+    P.gemm(g, t);
+  }
+  HT_TRY(run_plan(P, s, nullptr));
+  // inner nodes: F_t = H_t (x) B_t
+  std::vector<int64_t> desc;
+  int64_t max_e = 0;
+  int cnt = 0;
+  for (int t = 0; t < T.nn; ++t) {
+    if (is_leaf(T, t)) continue;
+    const int64_t pt = (t == 0) ? 1 : op->k[t], p1 = op->k[T.s1[t]], p2 = op->k[T.s2[t]];
+    const int64_t it = (t == 0) ? 1 : x->k[t], i1 = x->k[T.s1[t]], i2 = x->k[T.s2[t]];
+    const int64_t count = pt * it * p1 * i1 * p2 * i2;
+    desc.push_back(op->slot[t]);
+    desc.push_back(x->slot[t]);
+    desc.push_back(out->slot[t]);
+    desc.push_back(pt | (p1 << 20) | (p2 << 40));
+    desc.push_back(it | (i1 << 20) | (i2 << 40));
+    desc.push_back(count);
+    max_e = std::max(max_e, count);
+    ++cnt;
+  }
+  int64_t *d_desc = nullptr;
+  HT_CU(cudaMallocAsync((void **)&d_desc, desc.size() * sizeof(int64_t), s));
+  HT_CU(cudaMemcpyAsync(d_desc, desc.data(), desc.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  prof_begin(HT_K_MISC, s);
+  cudaError_t e = (x->dtype == HT_F64) ? launch_kron<double>(op->arena, x->arena, out->arena, d_desc, cnt, max_e, s)
+                                       : launch_kron<float>(op->arena, x->arena, out->arena, d_desc, cnt, max_e, s);
+  prof_end(HT_K_MISC, s, 0.0);
+  if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  HT_CU(cudaFreeAsync(d_desc, s));
+  // the host copy of desc must outlive the staged copy
+  HT_CU(cudaStreamSynchronize(s));
+  return HT_OK;
+}
+
 ht_status ht_orthogonalize(ht_tensor *x, int prec) {
   if (!x) return fail(HT_EINVAL, "null tensor");
   HT_TRY(check_prec(x, prec));

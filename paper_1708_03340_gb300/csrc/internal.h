@@ -126,6 +126,10 @@ cudaError_t launch_ranks(const RankItem *d_items, int n_items, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pack_add(const void *a, const void *c, void *out, const int64_t *d_desc, int n_nodes,
                             int64_t max_elems, cudaStream_t s);
+// Kronecker transfer tensors of an operator application (6 int64 per node descriptor)
+template <typename T>
+cudaError_t launch_kron(const void *h, const void *b, void *f, const int64_t *d_desc, int n_nodes, int64_t max_elems,
+                        cudaStream_t s);
 template <typename T>
 cudaError_t launch_eval_level(const void *x, const int64_t *node_off, const int *ranks, const int *tree,
                               const int64_t *n, const int64_t *idx, const int64_t *row_off, int64_t rows_per,

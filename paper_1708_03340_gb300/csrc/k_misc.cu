@@ -190,6 +190,33 @@ __global__ void pack_add_kernel(const T *__restrict__ a, const T *__restrict__ c
   }
 }
 
+// ---- Kronecker transfer tensors of an operator application -------------------
+// Lemma "operator" (Sec. 3.6): F_t = H_t (x) B_t, F[(p,i),(q,j),(r,l)] =
+// H[p,q,r] B[i,j,l], pair (p, i) flattened as p * k_t + i (operator index
+// slow).  desc per node (8 int64): H offset, B offset, F offset,
+// pt, p1, p2 (operator ranks), it, i1, i2 (tensor ranks) packed as
+// [offH, offB, offF, pt | p1 << 20 | p2 << 40, it | i1 << 20 | i2 << 40, count].
+template <typename T>
+__global__ void kron_kernel(const T *__restrict__ h, const T *__restrict__ b, T *__restrict__ f,
+                            const int64_t *__restrict__ desc) {
+  const int64_t *ds = desc + 6 * (int64_t)blockIdx.y;
+  const T *H = h + ds[0];
+  const T *B = b + ds[1];
+  T *F = f + ds[2];
+  const int64_t pt = ds[3] & 0xFFFFF, p1 = (ds[3] >> 20) & 0xFFFFF, p2 = (ds[3] >> 40) & 0xFFFFF;
+  const int64_t it = ds[4] & 0xFFFFF, i1 = (ds[4] >> 20) & 0xFFFFF, i2 = (ds[4] >> 40) & 0xFFFFF;
+  (void)pt;
+  const int64_t count = ds[5];
+  const int64_t o1 = p1 * i1, o2 = p2 * i2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += stride) {
+    const int64_t L = e % o2, IJ = e / o2;
+    const int64_t J = IJ % o1, I = IJ / o1;
+    const int64_t p = I / it, i = I - p * it, q = J / i1, j = J - q * i1, r = L / i2, l = L - r * i2;
+    F[e] = H[(p * p1 + q) * p2 + r] * B[(i * i1 + j) * i2 + l];
+  }
+}
+
 // ---- entry evaluation ---------------------------------------------------------
 // d_tree: per node [is_leaf, mode, son1, son2, height]; rows buffer holds u_t
 // for every (index, node) at offset e * rows_per + row_off[t].
@@ -297,6 +324,23 @@ cudaError_t launch_pack_add(const void *a, const void *c, void *out, const int64
 }
 template cudaError_t launch_pack_add<double>(const void *, const void *, void *, const int64_t *, int, int64_t, cudaStream_t);
 template cudaError_t launch_pack_add<float>(const void *, const void *, void *, const int64_t *, int, int64_t, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_kron(const void *h, const void *b, void *f, const int64_t *d_desc, int n_nodes, int64_t max_elems,
+                        cudaStream_t s) {
+  int gx = (int)((max_elems + 255) / 256);
+  if (gx > 256) gx = 256;
+  if (gx < 1) gx = 1;
+  for (int base = 0; base < n_nodes; base += 65535) {
+    const int cnt = n_nodes - base < 65535 ? n_nodes - base : 65535;
+    kron_kernel<T><<<dim3(gx, cnt), 256, 0, s>>>(static_cast<const T *>(h), static_cast<const T *>(b),
+                                                  static_cast<T *>(f), d_desc + 6 * (int64_t)base);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_kron<double>(const void *, const void *, void *, const int64_t *, int, int64_t, cudaStream_t);
+template cudaError_t launch_kron<float>(const void *, const void *, void *, const int64_t *, int, int64_t, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_eval_level(const void *x, const int64_t *node_off, const int *ranks, const int *tree, const int64_t *n,

@@ -33,7 +33,7 @@ EXPORTS = [
     "ht_add", "ht_add_into", "ht_orthogonalize", "ht_gramians", "ht_truncate",
     "ht_truncate_batch", "ht_norm", "ht_eval_entries", "ht_last_error",
     "ht_profile_set", "ht_profile_read", "ht_launch_count", "ht_gramians_noalloc",
-    "ht_graph_add_truncate", "ht_graph_launch", "ht_graph_kernels", "ht_graph_free", "ht_inner",
+    "ht_graph_add_truncate", "ht_graph_launch", "ht_graph_kernels", "ht_graph_free", "ht_inner", "ht_apply",
 ]
 HT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 HT_K_GEMM, HT_K_QR, HT_K_EIG, HT_K_COPY, HT_K_COMPACT, HT_K_RANKS, HT_K_ADD, HT_K_EVAL, HT_K_MISC = range(9)
@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True):
             "ht_graph_kernels": ([vp, i32p], ctypes.c_int),
             "ht_graph_free": ([vp], ctypes.c_int),
             "ht_inner": ([vp, vp, f64p], ctypes.c_int),
+            "ht_apply": ([vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -301,6 +302,10 @@ def ht_graph_kernels(g) -> int:
 
 def ht_graph_free(g):
     _check(load().ht_graph_free(g))
+
+
+def ht_apply(op, x, out):
+    _check(load().ht_apply(op, x, out))
 
 
 def ht_inner(x, y) -> float:
