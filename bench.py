@@ -101,10 +101,10 @@ WORKLOADS = {
                       "truncated to rank 128"),
 }
 
-# DRAM bytes per launch of the dominant kernel family on the default workload,
-# from the committed ncu launch list (profiles/); None when not captured for
-# the current kernels.
-TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes (read + write) per launch of the dominant kernel family, averaged
+# over one step's launches of that family, from one ncu capture of the current
+# kernels (profiles/gemm_kernel_single_d64_fp32.md); None where not captured.
+TRAFFIC_PER_LAUNCH = {("single", "gemm"): 15.536e6}
 
 
 def model_flops(d, n, K, r):
