@@ -450,6 +450,11 @@ def main():
         line["speedup_vs_plain_per_node"] = value / line["plain_fp64_per_node"]["value"]
         line["speedup_vs_plain_level"] = value / line["plain_fp64_level"]["value"]
         line["rel_err_vs_fp64"] = accuracy_vs_fp64(htgb, stream)
+        # the square-root Gramian mode of the FP32 path (HT_PREC_FP32_SQRT): accuracy arm
+        sq = graph_arm(htgb.HT_F32, htgb.HT_PREC_FP32_SQRT, ps, 3)
+        line["fp32_sqrt_gramians"] = {"value": sq["value"], "unit": "truncations/s", "ms_per_step": sq["ms"] / ps,
+                                      "rel_err_vs_fp64": accuracy_vs_fp64(htgb, stream, htgb.HT_PREC_FP32_SQRT)}
+        htgb.ht_graph_free(sq["g"])
 
     # ---- end to end through the public API: pinned host blobs in, truncated blobs out, every step
     A, C, X, g = main_arm["A"], main_arm["C"], main_arm["X"], main_arm["g"]
@@ -501,7 +506,7 @@ def main():
     return 0
 
 
-def accuracy_vs_fp64(htgb, stream):
+def accuracy_vs_fp64(htgb, stream, prec32=None):
     """Errors of the FP32-storage path relative to the FP64 GPU path on the same
     (FP32-representable) inputs of the default workload, all computed by the
     library on the GPU: sigma^2 normwise per node, ||X||, ||T32(X) - T64(X)|| / ||X||
@@ -517,7 +522,8 @@ def accuracy_vs_fp64(htgb, stream):
         A = htgb.HTTensor.from_blob(tree, n, ka, xa32, dt, stream)
         C = htgb.HTTensor.from_blob(tree, n, kc, xc32, dt, stream)
         X = A.add(C)
-        rep = X.truncate(prec=htgb.HT_PREC_FP32 if dt == htgb.HT_F32 else htgb.HT_PREC_FP64, **opts)
+        p32 = htgb.HT_PREC_FP32 if prec32 is None else prec32
+        rep = X.truncate(prec=p32 if dt == htgb.HT_F32 else htgb.HT_PREC_FP64, **opts)
         res[name] = (rep, X.ranks(), X.download().astype(np.float64))
     X64 = htgb.HTTensor.from_blob(tree, n, ka, xa32, htgb.HT_F64, stream).add(
         htgb.HTTensor.from_blob(tree, n, kc, xc32, htgb.HT_F64, stream))

@@ -56,8 +56,16 @@ typedef enum { HT_F64 = 0, HT_F32 = 1 } ht_dtype;
 
 /* Arithmetic of the truncation.  HT_PREC_FP64: every step in FP64 (F64
  * tensors).  HT_PREC_FP32: storage and dense contractions in FP32, the small
- * k x k Gramian eigendecompositions in FP64 (F32 tensors). */
-typedef enum { HT_PREC_FP64 = 0, HT_PREC_FP32 = 1 } ht_prec;
+ * k x k Gramian eigendecompositions in FP64 (F32 tensors).
+ * HT_PREC_FP32_SQRT: as HT_PREC_FP32, but the reduced Gramians of Sec. 3.3
+ * are carried as square-root factors Ghat_t = S_t S_t^T (top-down: the sons'
+ * Gramians are Gram products of B_t contracted with S_t, accumulated exactly
+ * in double-float with FP64 results; S_s is their semidefinite Cholesky
+ * factor), so FP32 rounding perturbs the singular values by O(u_32 sigma_max)
+ * instead of O(sqrt(u_32) sigma_max); the eps rule's noise floor becomes
+ * (4 sqrt(2d-1) u_32)^2 sigma_{t,1}^2.  F32 tensors.  This is the direction
+ * the paper's conclusion names for avoiding B^T B products. */
+typedef enum { HT_PREC_FP64 = 0, HT_PREC_FP32 = 1, HT_PREC_FP32_SQRT = 2 } ht_prec;
 
 typedef enum { HT_TRUNC_RANK = 0, HT_TRUNC_EPS = 1 } ht_trunc_mode;
 

@@ -235,7 +235,7 @@ constexpr uint64_t TAG_S = 1ull << 61;  // per-phase scratch workspace
 constexpr uint64_t TAG_M = 1ull << 60;  // metadata appended to the item upload
 constexpr uint64_t TAG_MASK = (1ull << 60) - 1;
 
-enum LKind { L_GEMM, L_QR, L_EIG, L_COPY, L_COMPACT, L_RANKS };
+enum LKind { L_GEMM, L_QR, L_EIG, L_COPY, L_COMPACT, L_RANKS, L_CHOL };
 
 struct Launch {
   LKind kind;
@@ -252,6 +252,7 @@ struct Launch {
   void *scratch = nullptr;      // eig scratch (tagged)
   int variant = 0;              // GEMM: SIMT tile shape (gemm_tile_shape)
   bool comp = true;             // GEMM: compensated FP32 accumulation
+  bool df = false;              // GEMM: double-float accumulation, FP64 output (square-root Gramians)
 };
 
 template <typename P>
@@ -273,6 +274,7 @@ struct Plan {
   std::vector<Launch> launches;
   size_t p_bytes = 0, s_bytes = 0, s_peak = 0;
   bool node_sched = false;
+  bool sqrt_gram = false;  // Gramians from square-root factors (HT_PREC_FP32_SQRT)
   int dtype = HT_F64;
   size_t esz = 8;
   std::string err;  // set by a planning step that cannot handle its input
@@ -321,7 +323,9 @@ struct Plan {
     if (node_sched && L.n > 0 && L.node != node) {
       LKind k = L.kind;
       const void *r = L.ranks;
+      const bool df = L.df;
       begin(k, r);
+      cur().df = df;
     }
     Launch &M = cur();
     M.node = node;
@@ -360,7 +364,9 @@ struct Plan {
     if (node_sched && cur().n > 0 && cur().node != node) {
       LKind k = cur().kind;
       const void *r = cur().ranks;
+      const bool df = cur().df;
       begin(k, r);
+      cur().df = df;
     }
     Launch &L = cur();
     g.tile0 = L.tiles;
@@ -372,7 +378,7 @@ struct Plan {
     if (g.M >= 128) L.tc_flops += fl;
     if (g.ksplit > 1) {
       L.split = true;
-      g.part = salloc_bytes((size_t)g.ksplit * g.batch * g.M * g.N * esz);
+      g.part = salloc_bytes((size_t)g.ksplit * g.batch * g.M * g.N * (L.df ? sizeof(double) : esz));
     }
     push_item(g, node);
   }
@@ -392,6 +398,7 @@ struct Plan {
   void copy(const CopyItem &c, int node) { push_item(c, node); }
   void compact(const CompactItem &c, int node) { push_item(c, node); }
   void rank(const RankItem &r, int node) { push_item(r, node); }
+  void chol(const CholItem &c, int node) { push_item(c, node); }
 };
 
 inline void *reloc(const void *p, char *pb, char *sb, char *mb) {
@@ -447,6 +454,15 @@ void reloc_items<CompactItem>(uint8_t *base, int n, char *pb, char *sb, char *mb
   for (int i = 0; i < n; ++i) {
     it[i].src = reloc(it[i].src, pb, sb, mb);
     it[i].dst = reloc(it[i].dst, pb, sb, mb);
+  }
+}
+template <>
+void reloc_items<CholItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
+  CholItem *it = reinterpret_cast<CholItem *>(base);
+  for (int i = 0; i < n; ++i) {
+    it[i].G = (const double *)reloc(it[i].G, pb, sb, mb);
+    it[i].W = (double *)reloc(it[i].W, pb, sb, mb);
+    it[i].S = (float *)reloc(it[i].S, pb, sb, mb);
   }
 }
 template <>
@@ -513,9 +529,10 @@ void choose_gemm_variant(Plan &P, Launch &L) {
   }
   // compensated accumulation where a CTA sums more than kTuneCompLen products;
   // shorter sums carry at most sqrt(kTuneCompLen) u of rounding (typical)
-  L.comp = longest > kTuneCompLen;
+  L.comp = longest > kTuneCompLen && !L.df;
   L.variant = 0;
-  if (all > 0.0 && !L.comp && square >= tu.square_share * all) L.variant = 2;
+  if (L.df) L.variant = 0;  // the double-float kernel exists in the 64 x 64 shape only
+  else if (all > 0.0 && !L.comp && square >= tu.square_share * all) L.variant = 2;
   else if (all > 0.0 && tall >= tu.tall_share * all) L.variant = 1;
   int bm = 64, bn = 64;
   gemm_tile_shape(L.variant, &bm, &bn);
@@ -558,6 +575,7 @@ ht_status prepare_plan(Plan &P, cudaStream_t s, char *base, char **ib_dev_out) {
       case L_COPY: reloc_items<CopyItem>(ib, L.n, pb, sb, mb); break;
       case L_COMPACT: reloc_items<CompactItem>(ib, L.n, pb, sb, mb); break;
       case L_RANKS: reloc_items<RankItem>(ib, L.n, pb, sb, mb); break;
+      case L_CHOL: reloc_items<CholItem>(ib, L.n, pb, sb, mb); break;
     }
     L.ranks = reloc(L.ranks, pb, sb, mb);
     L.scratch = reloc(L.scratch, pb, sb, mb);
@@ -592,22 +610,28 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
       case L_GEMM: {
         // FP32 launches whose flops sit mostly in tall items run on the tensor cores
         const bool tc = !f64 && tc_enabled() && L.tc_flops >= 0.5 * L.flops;
-        e = f64 ? launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s, L.variant, false)
-                : launch_gemm<float>((const GemmItem *)items, L.n, L.tiles, rk, L.split, tc ? L.tc_tiles : 0, s,
-                                     L.variant, L.comp);
+        e = f64 ? launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s, L.variant, false,
+                                      false)
+                : launch_gemm<float>((const GemmItem *)items, L.n, L.tiles, rk, L.split,
+                                     (tc && !L.df) ? L.tc_tiles : 0, s, L.variant, L.comp, L.df);
         break;
       }
       case L_QR:
         e = f64 ? launch_qr<double>((const QrItem *)items, L.n, L.max_m, L.max_n, s)
                 : launch_qr<float>((const QrItem *)items, L.n, L.max_m, L.max_n, s);
         break;
-      case L_EIG: e = launch_eig((const EigItem *)items, L.n, L.max_n, (double *)L.scratch, s, f64 ? 0 : 1); break;
+      case L_EIG:
+        // square-root Gramians carry eigenvalues far below the FP32 solve's resolution,
+        // which one refinement step cannot separate (it treats them as one cluster): FP64 QL
+        e = launch_eig((const EigItem *)items, L.n, L.max_n, (double *)L.scratch, s, (f64 || P.sqrt_gram) ? 0 : 1);
+        break;
       case L_COPY: e = launch_copy((const CopyItem *)items, L.n, rk, 0, s); break;
       case L_COMPACT:
         e = f64 ? launch_compact<double>((const CompactItem *)items, L.n, rk, s)
                 : launch_compact<float>((const CompactItem *)items, L.n, rk, s);
         break;
       case L_RANKS: e = launch_ranks((const RankItem *)items, L.n, s); break;
+      case L_CHOL: e = launch_chol((const CholItem *)items, L.n, s); break;
     }
     prof_end((int)L.kind, s, L.flops);
     kernels += (int)(g_launches - before);
@@ -662,6 +686,7 @@ struct TState {
   std::vector<int> kin, ko;       // input ranks, ranks after orthogonalization
   std::vector<void *> R;          // R factors (T), ko[t] x kin[t], column-major, ld = ko[t]
   std::vector<void *> G;          // Gramians (T), ko x ko
+  std::vector<void *> Sf;         // square-root Gramian factors (FP32), ko x ko, inner nodes
   std::vector<double *> G64;      // Gramians (FP64)
   std::vector<double *> V64;      // eigenvectors (FP64)
   std::vector<void *> V;          // eigenvectors (T)
@@ -1174,7 +1199,167 @@ void plan_orthogonalize(Plan &P, std::vector<TState> &TS) {
 
 // ---- reduced Gramians (Sec. 3.3) -----------------------------------------
 // dev_out: optional per-tensor FP64 output blocks (ht_gramians); else P-alloc.
+// ---- square-root Gramians (HT_PREC_FP32_SQRT) -------------------------------
+// The paper's Gramian recursion squares the singular values; with FP32 data
+// that resolves sigma only down to about sqrt(u_32) sigma_max.  Here every
+// Gramian is carried as a factor, Ghat_t = S_t S_t^T, top-down:
+//   Y[a, p, l] = sum_i S_t[i, a] B_t[i, p, l]            (FP32 contraction)
+//   Ghat_s1[p, q] = sum_{a,l} Y[a,p,l] Y[a,q,l],  Ghat_s2[l, l'] = sum_{a,j} Y[a,j,l] Y[a,j,l']
+// (eqs. "acctransferSon1/2" with Ghat_t = S_t S_t^T inserted), the Gram
+// products accumulated exactly in double-float with FP64 output, and S_s the
+// semidefinite Cholesky factor of Ghat_s (FP64, stored FP32) for the next
+// level.  Rounding then perturbs the factors, i.e. the singular values
+// themselves, by O(u_32) sigma_max.  S_root = 1.
+void plan_gramians_sqrt(Plan &P, std::vector<TState> &TS, const std::vector<double *> *dev_out) {
+  const size_t esz = P.esz;
+  int max_d = 0;
+  for (size_t si = 0; si < TS.size(); ++si) {
+    TState &S = TS[si];
+    const ht_tree &T = S.x->tr;
+    S.G.assign(T.nn, nullptr);
+    S.G64.assign(T.nn, nullptr);
+    S.Sf.assign(T.nn, nullptr);
+    int64_t off = 0;
+    for (int t = 0; t < T.nn; ++t) {
+      const int kt = (t == 0) ? 1 : S.ko[t];
+      if (dev_out) {
+        S.G64[t] = (*dev_out)[si] + off;
+        off += (int64_t)kt * kt;
+      } else {
+        S.G64[t] = P.palloc<double>((size_t)kt * kt);
+      }
+      if (!is_leaf(T, t)) S.Sf[t] = P.palloc_bytes((size_t)kt * kt * sizeof(float));
+    }
+    max_d = std::max(max_d, T.max_depth);
+  }
+  // S_root = 1, Ghat_root = 1
+  P.begin(L_COPY);
+  for (TState &S : TS) {
+    CopyItem c = copy0();
+    c.dst = S.Sf[0];
+    c.rows = c.cols = 1;
+    c.dr = c.dc = 1;
+    c.dst_f64 = 0;
+    P.copy(c, S.node_base);
+    CopyItem c2 = c;
+    c2.dst = S.G64[0];
+    c2.dst_f64 = 1;
+    P.copy(c2, S.node_base);
+  }
+  for (int L = 0; L <= max_d; ++L) {
+    P.sreset();
+    struct Job {
+      TState *S;
+      int t, K0, k1, k2;
+      void *Y;
+    };
+    std::vector<Job> jobs;
+    int tiles = 0;
+    for (TState &S : TS) {
+      const ht_tree &T = S.x->tr;
+      for (int t = 0; t < T.nn; ++t) {
+        if (is_leaf(T, t) || T.depth[t] != L) continue;
+        Job J;
+        J.S = &S;
+        J.t = t;
+        J.K0 = (t == 0) ? 1 : S.ko[t];
+        J.k1 = S.ko[T.s1[t]];
+        J.k2 = S.ko[T.s2[t]];
+        J.Y = P.salloc_bytes((size_t)J.K0 * J.k1 * J.k2 * esz);
+        jobs.push_back(J);
+        tiles += ((J.k1 + 63) / 64) * ((J.k1 + 63) / 64) + ((J.k2 + 63) / 64) * ((J.k2 + 63) / 64);
+      }
+    }
+    if (jobs.empty()) continue;
+    // Y_mat (k1k2 x K0) = B_mat (k1k2 x K0) * S_t (K0 x K0)
+    P.begin(L_GEMM);
+    for (Job &J : jobs) {
+      GemmItem g = gemm0();
+      g.A = node_ptr(J.S->x, J.t);
+      g.sam = 1;
+      g.sak = (int64_t)J.k1 * J.k2;
+      g.B = J.S->Sf[J.t];
+      g.sbk = 1;
+      g.sbn = J.K0;
+      g.C = J.Y;
+      g.scm = 1;
+      g.scn = (int64_t)J.k1 * J.k2;
+      g.M = J.k1 * J.k2;
+      g.N = J.K0;
+      g.K = J.K0;
+      P.gemm(g, J.S->node_base + J.t);
+    }
+    // Ghat_s1 = sum_{a,l} Y[a,p,l] Y[a,q,l], Ghat_s2 = sum_{a,j} Y[a,j,l] Y[a,j,l'] (double-float, FP64 out)
+    const int ksplit = std::max(1, (2 * kSmCount + tiles - 1) / std::max(tiles, 1));
+    P.begin(L_GEMM);
+    P.cur().df = true;
+    for (Job &J : jobs) {
+      const ht_tree &T = J.S->x->tr;
+      const int s1 = T.s1[J.t], s2 = T.s2[J.t];
+      const int64_t kk = (int64_t)J.k1 * J.k2;
+      GemmItem g = gemm0();
+      g.A = J.Y;
+      g.sam = J.k2;
+      g.sak = 1;
+      g.sako = kk;
+      g.B = J.Y;
+      g.sbk = 1;
+      g.sbko = kk;
+      g.sbn = J.k2;
+      g.C = J.S->G64[s1];
+      g.scm = 1;
+      g.scn = J.k1;
+      g.M = J.k1;
+      g.N = J.k1;
+      g.K = J.k2;
+      g.Ko = J.K0;
+      g.ksplit = std::min(ksplit, J.K0);
+      P.gemm(g, J.S->node_base + J.t);
+      GemmItem h = gemm0();
+      h.A = J.Y;
+      h.sam = 1;
+      h.sak = J.k2;
+      h.sako = kk;
+      h.B = J.Y;
+      h.sbk = J.k2;
+      h.sbko = kk;
+      h.sbn = 1;
+      h.C = J.S->G64[s2];
+      h.scm = 1;
+      h.scn = J.k2;
+      h.M = J.k2;
+      h.N = J.k2;
+      h.K = J.k1;
+      h.Ko = J.K0;
+      h.ksplit = std::min(ksplit, J.K0);
+      P.gemm(h, J.S->node_base + J.t);
+    }
+    // factors of the inner sons for the next level
+    P.begin(L_CHOL);
+    bool any = false;
+    for (Job &J : jobs) {
+      const ht_tree &T = J.S->x->tr;
+      for (int s : {T.s1[J.t], T.s2[J.t]}) {
+        if (is_leaf(T, s)) continue;
+        const int ks = J.S->ko[s];
+        CholItem c;
+        c.G = J.S->G64[s];
+        c.W = static_cast<double *>(P.salloc_bytes((size_t)ks * ks * sizeof(double)));
+        c.S = static_cast<float *>(J.S->Sf[s]);
+        c.k = ks;
+        P.chol(c, J.S->node_base + s);
+        any = true;
+      }
+    }
+    (void)any;
+  }
+}
+
 void plan_gramians(Plan &P, std::vector<TState> &TS, const std::vector<double *> *dev_out) {
+  if (P.sqrt_gram) {
+    plan_gramians_sqrt(P, TS, dev_out);
+    return;
+  }
   const size_t esz = P.esz;
   const bool f64 = (P.dtype == HT_F64);
   int max_d = 0;
@@ -1351,7 +1536,7 @@ void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, in
       n_eig++;
     }
   }
-  if (eig_scratch_needed(max_k, P.dtype == HT_F64 ? 0 : 1)) {
+  if (eig_scratch_needed(max_k, (P.dtype == HT_F64 || P.sqrt_gram) ? 0 : 1)) {
     // one scratch slab per item of a launch (node schedule: one item per launch)
     size_t per = 4 * (size_t)max_k * max_k;
     size_t cnt = P.node_sched ? 1 : n_eig;
@@ -1387,6 +1572,8 @@ void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, in
     // noise floor of a computed Gramian eigenvalue: 4 sqrt(2d-1) u lambda_max,
     // u the unit roundoff of the path (every node's rounding perturbs X independently)
     r.noise = 4.0 * std::sqrt(2.0 * T.d - 1.0) * (P.dtype == HT_F64 ? 0x1p-53 : 0x1p-24);
+    // square-root Gramians: rounding perturbs the singular values, not their squares
+    if (P.sqrt_gram) r.noise = r.noise * r.noise;
     P.rank(r, S.node_base);
   }
 }
@@ -1721,9 +1908,10 @@ void *plan_inner(Plan &P, const ht_tensor *x, const ht_tensor *y) {
 ht_status check_prec(const ht_tensor *x, int prec) {
   if (prec == HT_PREC_FP64 && x->dtype != HT_F64)
     return fail(HT_EUNSUPPORTED, "HT_PREC_FP64 needs an HT_F64 tensor");
-  if (prec == HT_PREC_FP32 && x->dtype != HT_F32)
-    return fail(HT_EUNSUPPORTED, "HT_PREC_FP32 needs an HT_F32 tensor");
-  if (prec != HT_PREC_FP64 && prec != HT_PREC_FP32) return fail(HT_EINVAL, "unknown precision");
+  if ((prec == HT_PREC_FP32 || prec == HT_PREC_FP32_SQRT) && x->dtype != HT_F32)
+    return fail(HT_EUNSUPPORTED, "HT_PREC_FP32 and HT_PREC_FP32_SQRT need an HT_F32 tensor");
+  if (prec != HT_PREC_FP64 && prec != HT_PREC_FP32 && prec != HT_PREC_FP32_SQRT)
+    return fail(HT_EINVAL, "unknown precision");
   return HT_OK;
 }
 
@@ -2120,6 +2308,7 @@ ht_status ht_gramians(ht_tensor *x, double *dev_out, int prec) {
   HT_TRY(check_prec(x, prec));
   HT_TRY(sync_ranks(x));
   Plan P;
+  P.sqrt_gram = (prec == HT_PREC_FP32_SQRT);
   P.dtype = x->dtype;
   P.esz = x->esz;
   std::vector<TState> TS(1);
@@ -2166,6 +2355,7 @@ ht_status ht_gramians_noalloc(ht_tensor *x, double *dev_out, int prec) {
   HT_TRY(noalloc_scratch(&scratch));
   HT_TRY(sync_ranks(x));
   Plan P;
+  P.sqrt_gram = (prec == HT_PREC_FP32_SQRT);
   P.dtype = x->dtype;
   P.esz = x->esz;
   std::vector<TState> TS(1);
@@ -2193,6 +2383,7 @@ static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_o
   P.dtype = dtype;
   P.esz = (dtype == HT_F64) ? 8 : 4;
   P.node_sched = (o->schedule == HT_SCHED_NODE);
+  P.sqrt_gram = (o->prec == HT_PREC_FP32_SQRT);
   std::vector<TState> TS(count);
   int total_nodes = 0;
   for (int i = 0; i < count; ++i) {
@@ -2320,6 +2511,7 @@ ht_status ht_graph_add_truncate(const ht_tensor *const *a, const ht_tensor *cons
   P.dtype = out[0]->dtype;
   P.esz = (P.dtype == HT_F64) ? 8 : 4;
   P.node_sched = (o->schedule == HT_SCHED_NODE);
+  P.sqrt_gram = (o->prec == HT_PREC_FP32_SQRT);
   std::vector<TState> TS(count);
   int total_nodes = 0;
   for (int i = 0; i < count; ++i) {

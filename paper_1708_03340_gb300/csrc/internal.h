@@ -59,6 +59,17 @@ struct EigItem {
   int k;
 };
 
+// Semidefinite Cholesky factor of one k x k FP64 Gramian: G = S S^T, S lower
+// triangular (FP32 output, zeros above the diagonal); W is a k x k FP64
+// working array.  Pivots at or below tau = 4 k u_64 max_i G_ii give a zero
+// column (the Gramian is singular there to working accuracy).
+struct CholItem {
+  const double *G;
+  double *W;
+  float *S;
+  int k;
+};
+
 // 2-D strided copy with optional cast, identity or zero fill, scaling.
 //   dst[r*dr + c*dc] = (src ? alpha*src[r*sr + c*sc] : (zero ? 0 : (r == c ? 1 : 0))) + beta*dst[...]
 // rows/cols may be rank references like GemmItem dims (-1: literal).
@@ -108,10 +119,11 @@ struct RankItem {
 // variant: SIMT tile shape (0: 64 x 64, 1: 128 x 64, 2: 128 x 128, the last
 // without compensation only); items' tiles_m / tiles_n / tile0 must be laid
 // out for that shape (gemm_tile_shape).  comp: Kahan-compensated FP32
-// accumulation across the BK-wide tiles of a CTA.
+// accumulation across the BK-wide tiles of a CTA.  df (FP32 only): double-float
+// accumulation of exact products, FP64 output and split-K partials.
 template <typename T>
 cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks,
-                        bool any_split, int tc_tiles, cudaStream_t s, int variant, bool comp);
+                        bool any_split, int tc_tiles, cudaStream_t s, int variant, bool comp, bool df);
 void gemm_tile_shape(int variant, int *bm, int *bn);
 cudaError_t launch_gemm_tc(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, cudaStream_t s);
 template <typename T>
@@ -120,6 +132,7 @@ cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, 
 // scratch: 4 * max_k^2 doubles per item when max_k exceeds the shared-memory sizes (eig_scratch_needed).
 cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s, int mode);
 cudaError_t launch_copy(const CopyItem *d_items, int n_items, const int *d_ranks, int f64_any, cudaStream_t s);
+cudaError_t launch_chol(const CholItem *d_items, int n_items, cudaStream_t s);
 template <typename T>
 cudaError_t launch_compact(const CompactItem *d_items, int n_items, const int *d_ranks, cudaStream_t s);
 cudaError_t launch_ranks(const RankItem *d_items, int n_items, cudaStream_t s);

@@ -454,7 +454,59 @@ size_t ql_smem(int max_k) {
   return (max_k <= kEigSmemK) ? (size_t)max_k * max_k * sizeof(T) + tail : tail;
 }
 
+// ---- semidefinite Cholesky (square-root Gramian factors) --------------------
+// Right-looking, one column per step: pivot d = A_jj; d <= tau gives a zero
+// column, otherwise L_jj = sqrt(d), L_ij = A_ij / L_jj and the trailing lower
+// triangle takes A_ip -= L_ij L_pj.  tau = 4 k u_64 max_i G_ii.
+__global__ void __launch_bounds__(EIG_THREADS) chol_kernel(const CholItem *__restrict__ items) {
+  const CholItem it = items[blockIdx.x];
+  const int k = it.k, tid = threadIdx.x, nt = blockDim.x;
+  double *A = it.W;
+  __shared__ double red[32];
+  __shared__ double piv, pinv;
+  double mx = 0.0;
+  for (int e = tid; e < k * k; e += nt) {
+    const int c = e / k, r = e - c * k;
+    const double v = 0.5 * (it.G[(int64_t)c * k + r] + it.G[(int64_t)r * k + c]);
+    A[e] = v;
+    if (r == c) mx = fmax(mx, v);
+  }
+  mx = block_max_d(mx, red);
+  const double tau = 4.0 * k * 1.1102230246251565e-16 * mx;
+  for (int j = 0; j < k; ++j) {
+    __syncthreads();  // the previous update is complete
+    if (tid == 0) {
+      const double d = A[(int64_t)j * k + j];
+      piv = (d > tau) ? sqrt(d) : 0.0;
+      pinv = (d > tau) ? 1.0 / piv : 0.0;
+      A[(int64_t)j * k + j] = piv;
+    }
+    __syncthreads();
+    const double pi = pinv;
+    for (int i = j + 1 + tid; i < k; i += nt) A[(int64_t)j * k + i] *= pi;
+    __syncthreads();
+    if (pi == 0.0) continue;
+    const int m = k - j - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int p = j + 1 + e / m, i = j + 1 + e % m;
+      if (i >= p) A[(int64_t)p * k + i] -= A[(int64_t)j * k + i] * A[(int64_t)j * k + p];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < k * k; e += nt) {
+    const int c = e / k, r = e - c * k;
+    it.S[e] = (r >= c) ? (float)A[e] : 0.0f;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_chol(const CholItem *d_items, int n_items, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  chol_kernel<<<n_items, EIG_THREADS, 0, s>>>(d_items);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s, int mode) {
   if (n_items <= 0) return cudaSuccess;

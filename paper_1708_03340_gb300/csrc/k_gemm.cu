@@ -5,6 +5,8 @@
 // "transfer tensor transformation" (R-apply and projection), the reduced
 // Gramian contractions of eqs. "acctransferSon1/2", the leaf products U Q|_r
 // and the TSQR recombination.  One launch walks all items of a tree level.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace htgb {
@@ -75,10 +77,17 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // over the banks.  kComp (FP32 only): every BK-wide tile is summed in
 // registers and added to the running sum with Kahan compensation
 // (compensated summation of the long Gramian reductions); chosen per launch
-// from the longest per-CTA reduction.
-template <typename T, int BM, int BN, int TM, int TN, int BK, bool kComp>
+// from the longest per-CTA reduction.  kAcc = 2 (FP32 inputs only): every
+// product is carried exactly as a pair (p, e) with p = a b rounded and
+// e = fma(a, b, -p), and summed into a double-float (hi, lo) with a two-sum
+// (Dekker / Knuth error-free transformations), so the sum is FP64-accurate;
+// the output (and any split-K partials) are FP64.
+template <typename T, int BM, int BN, int TM, int TN, int BK, int kAcc>
 __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restrict__ items, int n_items,
                                                         const int *__restrict__ ranks) {
+  constexpr bool kComp = (kAcc == 1);
+  constexpr bool kDF = (kAcc == 2) && sizeof(T) == 4;  // double-float accumulation, FP64 output
+  using OutT = typename std::conditional<kDF, double, T>::type;
   static_assert((BM / TM) * (BN / TN) == THREADS, "one output block per thread");
   static_assert(TM % 4 == 0 && TN % 4 == 0, "rows and columns in groups of 4");
   constexpr int LA = (BM * BK) / THREADS, LB = (BN * BK) / THREADS;
@@ -143,16 +152,16 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
     cp_async_commit();
   };
 
-  T acc[TM][TN], sum[kComp ? TM : 1][kComp ? TN : 1], cmp[kComp ? TM : 1][kComp ? TN : 1];
+  T acc[TM][TN], sum[(kComp || kDF) ? TM : 1][(kComp || kDF) ? TN : 1], cmp[(kComp || kDF) ? TM : 1][(kComp || kDF) ? TN : 1];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
-  if (kComp) {
+  if (kComp || kDF) {
 #pragma unroll
-    for (int i = 0; i < (kComp ? TM : 1); ++i)
+    for (int i = 0; i < ((kComp || kDF) ? TM : 1); ++i)
 #pragma unroll
-      for (int j = 0; j < (kComp ? TN : 1); ++j) sum[i][j] = cmp[i][j] = T(0);
+      for (int j = 0; j < ((kComp || kDF) ? TN : 1); ++j) sum[i][j] = cmp[i][j] = T(0);
   }
 #pragma unroll
   for (int st = 0; st < NS - 1; ++st) issue(st, st);
@@ -178,10 +187,28 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
 #pragma unroll
         for (int u = 0; u < 4; ++u) bb[4 * g + u] = x[u];
       }
+      if (kDF) {
 #pragma unroll
-      for (int i = 0; i < TM; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+          for (int j = 0; j < TN; ++j) {
+            const int ii = kDF ? i : 0, jj = kDF ? j : 0;
+            // the _rn intrinsics keep every rounding in place (no contraction into FMAs)
+            const float pr = __fmul_rn((float)a[i], (float)bb[j]);
+            const float er = __fmaf_rn((float)a[i], (float)bb[j], -pr);  // a b = pr + er exactly
+            const float hi = (float)sum[ii][jj];
+            const float t = __fadd_rn(hi, pr);
+            const float bp = __fsub_rn(t, hi);
+            const float e2 = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(pr, bp));  // hi + pr = t + e2
+            sum[ii][jj] = (T)t;
+            cmp[ii][jj] = (T)__fadd_rn((float)cmp[ii][jj], __fadd_rn(e2, er));
+          }
+      } else {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+      }
     }
     if (kComp) {
 #pragma unroll
@@ -203,28 +230,35 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
 #pragma unroll
       for (int j = 0; j < TN; ++j) acc[i][j] = sum[kComp ? i : 0][kComp ? j : 0];
   }
+  auto result = [&](int i, int j) -> OutT {
+    if (kDF) {
+      const int ii = kDF ? i : 0, jj = kDF ? j : 0;
+      return (OutT)((double)sum[ii][jj] + (double)cmp[ii][jj]);
+    }
+    return (OutT)acc[i][j];
+  };
   if (it.ksplit > 1) {
-    T *P = static_cast<T *>(it.part) + ((int64_t)chunk * it.batch + b) * (int64_t)it.M * it.N;
+    OutT *P = static_cast<OutT *>(it.part) + ((int64_t)chunk * it.batch + b) * (int64_t)it.M * it.N;
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
         const int gm = m0 + row_of(i), gn = n0 + col_of(j);
-        if (gm < M && gn < N) P[(int64_t)gn * it.M + gm] = acc[i][j];
+        if (gm < M && gn < N) P[(int64_t)gn * it.M + gm] = result(i, j);
       }
     return;
   }
-  T *C = static_cast<T *>(it.C) + (int64_t)b * it.scb;
-  const T alpha = T(it.alpha), beta = T(it.beta);
+  OutT *C = static_cast<OutT *>(it.C) + (int64_t)b * it.scb;
+  const OutT alpha = OutT(it.alpha), beta = OutT(it.beta);
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int gm = m0 + row_of(i), gn = n0 + col_of(j);
       if (gm < M && gn < N) {
-        T *c = C + (int64_t)gm * it.scm + (int64_t)gn * it.scn;
-        T v = alpha * acc[i][j];
-        if (beta != T(0)) v += beta * *c;
+        OutT *c = C + (int64_t)gm * it.scm + (int64_t)gn * it.scn;
+        OutT v = alpha * result(i, j);
+        if (beta != OutT(0)) v += beta * *c;
         *c = v;
       }
     }
@@ -260,37 +294,45 @@ __global__ void gemm_reduce_kernel(const GemmItem *__restrict__ items, const int
 
 template <typename T>
 cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, bool any_split,
-                        int tc_tiles, cudaStream_t s, int variant, bool comp) {
+                        int tc_tiles, cudaStream_t s, int variant, bool comp, bool df) {
   if (n_items <= 0 || total_tiles <= 0) return cudaSuccess;
   if (sizeof(T) == 4 && tc_tiles > 0) {
     cudaError_t e = launch_gemm_tc(d_items, n_items, tc_tiles, d_ranks, s);
     if (e != cudaSuccess) return e;
   } else {
-    // Kahan compensation only for FP32 launches with long per-CTA reductions
+    // Kahan compensation only for FP32 launches with long per-CTA reductions;
+    // double-float accumulation (FP64 output) when asked for
     const bool c = (sizeof(T) == 4) && comp;
-    if (variant == 2 && !c) {
-      gemm_kernel<T, 128, 128, 8, 8, 16, false><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+    if (sizeof(T) == 4 && df) {
+      gemm_kernel<T, 64, 64, 4, 4, 16, 2><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+    } else if (variant == 2 && !c) {
+      gemm_kernel<T, 128, 128, 8, 8, 16, 0><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
     } else if (variant >= 1) {
-      if (c) gemm_kernel<T, 128, 64, 8, 4, 16, true><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
-      else gemm_kernel<T, 128, 64, 8, 4, 16, false><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+      if (c) gemm_kernel<T, 128, 64, 8, 4, 16, 1><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+      else gemm_kernel<T, 128, 64, 8, 4, 16, 0><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
     } else {
-      if (c) gemm_kernel<T, 64, 64, 4, 4, 16, true><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
-      else gemm_kernel<T, 64, 64, 4, 4, 16, false><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+      if (c) gemm_kernel<T, 64, 64, 4, 4, 16, 1><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+      else gemm_kernel<T, 64, 64, 4, 4, 16, 0><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
     }
     count_launch();
   }
   if (any_split) {
     for (int base = 0; base < n_items; base += 65535) {
       const int cnt = n_items - base < 65535 ? n_items - base : 65535;
-      gemm_reduce_kernel<T><<<dim3(64, cnt), 256, 0, s>>>(d_items + base, d_ranks);
+      if (sizeof(T) == 4 && df)
+        gemm_reduce_kernel<double><<<dim3(64, cnt), 256, 0, s>>>(d_items + base, d_ranks);
+      else
+        gemm_reduce_kernel<T><<<dim3(64, cnt), 256, 0, s>>>(d_items + base, d_ranks);
       count_launch();
     }
   }
   return cudaGetLastError();
 }
 
-template cudaError_t launch_gemm<double>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t, int, bool);
-template cudaError_t launch_gemm<float>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t, int, bool);
+template cudaError_t launch_gemm<double>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t, int, bool,
+                                         bool);
+template cudaError_t launch_gemm<float>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t, int, bool,
+                                        bool);
 
 void gemm_tile_shape(int variant, int *bm, int *bn) {
   *bm = (variant >= 1) ? 128 : 64;
