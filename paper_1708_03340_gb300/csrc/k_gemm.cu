@@ -83,7 +83,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // (Dekker / Knuth error-free transformations), so the sum is FP64-accurate;
 // the output (and any split-K partials) are FP64.
 template <typename T, int BM, int BN, int TM, int TN, int BK, int kAcc>
-__global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(THREADS, sizeof(T) != 4 ? 1
+                                           : (BM * BN <= 64 * 64 ? (kAcc == 0 ? 3 : 2) : (BM * BN <= 128 * 64 && kAcc == 0 ? 2 : 1)))
+    gemm_kernel(const GemmItem *__restrict__ items, int n_items,
                                                         const int *__restrict__ ranks) {
   constexpr bool kComp = (kAcc == 1);
   constexpr bool kDF = (kAcc == 2) && sizeof(T) == 4;  // double-float accumulation, FP64 output
@@ -123,30 +125,55 @@ __global__ void __launch_bounds__(THREADS) gemm_kernel(const GemmItem *__restric
   const bool a_mfast = (it.sam == 1);
   const bool b_nfast = (it.sbn == 1) && (it.sbk != 1);
 
+  // Per copied element of this thread: its place in the tile and its global
+  // offset without the k tile (fixed for the CTA); a tile adds k0 and ko.
+  int offa[LA], offb[LB];  // 32-bit: the plan keeps every tile offset below 2^31 elements
+  unsigned vmask = 0;  // bit r: row of A element r inside M; bit LA + r: column of B element r inside N
+#pragma unroll
+  for (int r = 0; r < LA; ++r) {
+    const int e = tid + r * THREADS;
+    int mm, kk;
+    if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+    const int gm = m0 + mm;
+    offa[r] = (gm < M) ? (int)((int64_t)gm * it.sam + (int64_t)kk * it.sak) : 0;
+    if (gm < M) vmask |= 1u << r;
+  }
+#pragma unroll
+  for (int r = 0; r < LB; ++r) {
+    const int e = tid + r * THREADS;
+    int nn, kk;
+    if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+    const int gn = n0 + nn;
+    offb[r] = (gn < N) ? (int)((int64_t)kk * it.sbk + (int64_t)gn * it.sbn) : 0;
+    if (gn < N) vmask |= 1u << (LA + r);
+  }
   // issue the copies of BK-tile q into stage st (one commit group per call)
   auto issue = [&](int q, int st) {
     if (q < nq) {
       const int ko = ko_begin + q / kt, k0 = (q % kt) * BK;
-      const T *Ak = A + (int64_t)ko * it.sako;
-      const T *Bk = B + (int64_t)ko * it.sbko;
-      const int64_t kflat = (int64_t)ko * K;
+      const T *Ak = A + (int64_t)ko * it.sako + (int64_t)k0 * it.sak;
+      const T *Bk = B + (int64_t)ko * it.sbko + (int64_t)k0 * it.sbk;
+      // k limit of this tile: K, or the flat cut of a ragged last chunk
+      int klim = K - k0;
+      if (it.k_total >= 0) {
+        const int64_t rest = it.k_total - ((int64_t)ko * K + k0);
+        if (rest < klim) klim = (int)(rest > 0 ? rest : 0);
+      }
 #pragma unroll
       for (int r = 0; r < LA; ++r) {
         const int e = tid + r * THREADS;
         int mm, kk;
         if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
-        const int gm = m0 + mm, gk = k0 + kk;
-        const bool v = gm < M && gk < K && (it.k_total < 0 || kflat + gk < it.k_total);
-        cp_async_elem<T>(&As[st][kk][mm], Ak + (v ? (int64_t)gm * it.sam + (int64_t)gk * it.sak : 0), v);
+        const bool v = ((vmask >> r) & 1u) && kk < klim;
+        cp_async_elem<T>(&As[st][kk][mm], Ak + (v ? offa[r] : 0), v);
       }
 #pragma unroll
       for (int r = 0; r < LB; ++r) {
         const int e = tid + r * THREADS;
         int nn, kk;
         if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
-        const int gn = n0 + nn, gk = k0 + kk;
-        const bool v = gn < N && gk < K && (it.k_total < 0 || kflat + gk < it.k_total);
-        cp_async_elem<T>(&Bs[st][kk][nn], Bk + (v ? (int64_t)gk * it.sbk + (int64_t)gn * it.sbn : 0), v);
+        const bool v = ((vmask >> (LA + r)) & 1u) && kk < klim;
+        cp_async_elem<T>(&Bs[st][kk][nn], Bk + (v ? offb[r] : 0), v);
       }
     }
     cp_async_commit();
