@@ -8,6 +8,7 @@
 // is allocated; items and small metadata arrays are uploaded with a single
 // copy.  All work is stream-ordered on the tensor's stream.
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #include <mutex>
 #include <cmath>
@@ -341,6 +342,14 @@ struct Plan {
     if (g.n_mult < 1) g.n_mult = 1;
     if (g.b_mult < 1) g.b_mult = 1;
     if (g.M <= 0 || g.N <= 0) return;
+    {
+      // the SIMT kernel keeps a thread's in-tile element offsets in 32 bits
+      const int64_t kk = 63;  // largest in-tile k index of any tile shape, with margin
+      const int64_t oa = (int64_t)(g.M - 1) * std::llabs(g.sam) + kk * std::llabs(g.sak);
+      const int64_t ob = (int64_t)(g.N - 1) * std::llabs(g.sbn) + kk * std::llabs(g.sbk);
+      if (oa >= (int64_t)INT32_MAX || ob >= (int64_t)INT32_MAX)
+        err = "contraction operand spans 2^31 elements or more within one tile row/column";
+    }
     if (dtype == HT_F32 && g.M < 128 && g.N >= 128 && g.m_ref < 0 && g.n_ref < 0) {
       // C^T = B^T A^T puts the long dimension on the 128-row MMA tiles
       std::swap(g.A, g.B);
