@@ -104,7 +104,7 @@ WORKLOADS = {
 # DRAM bytes (read + write) per launch of the dominant kernel family, averaged
 # over one step's launches of that family, from one ncu capture of the current
 # kernels (profiles/gemm_kernel_single_d64_fp32.md); None where not captured.
-TRAFFIC_PER_LAUNCH = {("single", "gemm"): 15.536e6}
+TRAFFIC_PER_LAUNCH = {("single", "gemm"): 15.52e6}
 
 
 def model_flops(d, n, K, r):

@@ -279,6 +279,15 @@ ht_status ht_profile_read(int kind, int64_t *launches, double *total_ms, double 
 /* Number of kernels this library has launched since it was loaded (all kinds). */
 ht_status ht_launch_count(int64_t *total);
 
+/* Synchronises the device, then reports the device-side error word of the
+ * kernels whose threads wait on one another inside a CTA (the opt-in tcgen05
+ * contraction's mbarrier waits).  Every such wait is bounded; one that gave
+ * up (never expected: the waiting and the signalling threads belong to one
+ * resident CTA) marks its results invalid and sets the word.  Returns HT_ETIMEOUT if a
+ * word was set since the last call (and clears it), HT_ECUDA if the device
+ * reports an error, else HT_OK. */
+ht_status ht_device_status(void);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *ht_last_error(void);
 

@@ -564,6 +564,28 @@ size_t plan_bytes(const Plan &P) {
   return i_off + P.items.size();
 }
 
+// HTGB_PLAN_DUMP=1: one line per launch of every prepared plan on stderr
+// (kind, items, tiles, flops, tile shape; for contractions the items' dims).
+void dump_plan(const Plan &P) {
+  static const char *names[] = {"gemm", "qr", "eig", "copy", "compact", "ranks", "chol"};
+  fprintf(stderr, "plan: %zu launches, dtype %s\n", P.launches.size(), P.dtype == HT_F64 ? "f64" : "f32");
+  for (const Launch &L : P.launches) {
+    fprintf(stderr, "  %-7s items %4d tiles %5d max_m %5d max_n %4d mflop %9.3f", names[L.kind], L.n, L.tiles, L.max_m,
+            L.max_n, L.flops * 1e-6);
+    if (L.kind == L_GEMM) {
+      fprintf(stderr, " variant %d comp %d df %d split %d |", L.variant, (int)L.comp, (int)L.df, (int)L.split);
+      const GemmItem *it = reinterpret_cast<const GemmItem *>(P.items.data() + L.off);
+      for (int i = 0; i < L.n && i < 3; ++i)
+        fprintf(stderr, " %dx%dx(%dx%d)b%d/s%d[a %lld,%lld,%lld b %lld,%lld,%lld c %lld,%lld]", it[i].M, it[i].N, it[i].K,
+                it[i].Ko, it[i].batch, it[i].ksplit, (long long)it[i].sam, (long long)it[i].sak, (long long)it[i].sako,
+                (long long)it[i].sbk, (long long)it[i].sbko, (long long)it[i].sbn, (long long)it[i].scm,
+                (long long)it[i].scn);
+      if (L.n > 3) fprintf(stderr, " ...");
+    }
+    fprintf(stderr, "\n");
+  }
+}
+
 // Relocate the plan's tagged pointers into the workspace at base and upload
 // the metadata and the work items (stream-ordered copies from host memory
 // that stays alive in P).
@@ -575,6 +597,7 @@ ht_status prepare_plan(Plan &P, cudaStream_t s, char *base, char **ib_dev_out) {
   char *pb = base, *sb = base + p_sz, *mb = base + m_off;
   for (Launch &L : P.launches)
     if (L.kind == L_GEMM) choose_gemm_variant(P, L);
+  if (getenv("HTGB_PLAN_DUMP")) dump_plan(P);
   for (Launch &L : P.launches) {
     uint8_t *ib = P.items.data() + L.off;
     switch (L.kind) {
@@ -1966,6 +1989,15 @@ ht_status ht_profile_read(int kind, int64_t *launches, double *total_ms, double 
     }
     g_prof_done.swap(keep);
   }
+  return HT_OK;
+}
+
+ht_status ht_device_status(void) {
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
+  const int t = tc_take_wait_error();
+  if (t < 0) return fail(HT_ECUDA, "reading the device error word failed");
+  if (t) return fail(HT_ETIMEOUT, "a tcgen05 contraction's bounded wait gave up");
   return HT_OK;
 }
 

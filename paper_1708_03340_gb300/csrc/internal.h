@@ -153,6 +153,11 @@ cudaError_t launch_sumsq(const void *x, int64_t count, double *out, cudaStream_t
 template <typename T>
 cudaError_t launch_scale(void *x, int64_t count, double alpha, cudaStream_t s);
 
+// Device error word of the kernel with bounded waits (tcgen05 contraction):
+// read and clear; 1 if a wait gave up since the last call, 0 if not, -1 if
+// the read failed.  Synchronises the device (symbol copies).
+int tc_take_wait_error();
+
 // launch accounting / tracing (api.cu)
 void count_launch(int n = 1);
 void prof_begin(int kind, cudaStream_t s);

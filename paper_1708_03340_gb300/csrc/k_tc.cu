@@ -347,4 +347,14 @@ cudaError_t launch_gemm_tc(const GemmItem *d_items, int n_items, int total_tiles
   return cudaGetLastError();
 }
 
+int tc_take_wait_error() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_tc_wait_error, sizeof(int)) != cudaSuccess) return -1;
+  if (v) {
+    const int z = 0;
+    if (cudaMemcpyToSymbol(g_tc_wait_error, &z, sizeof(int)) != cudaSuccess) return -1;
+  }
+  return v;
+}
+
 }  // namespace htgb

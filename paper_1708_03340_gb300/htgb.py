@@ -34,6 +34,7 @@ EXPORTS = [
     "ht_truncate_batch", "ht_norm", "ht_eval_entries", "ht_last_error",
     "ht_profile_set", "ht_profile_read", "ht_launch_count", "ht_gramians_noalloc",
     "ht_graph_add_truncate", "ht_graph_launch", "ht_graph_kernels", "ht_graph_free", "ht_inner", "ht_apply",
+    "ht_device_status",
 ]
 HT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 HT_K_GEMM, HT_K_QR, HT_K_EIG, HT_K_COPY, HT_K_COMPACT, HT_K_RANKS, HT_K_ADD, HT_K_EVAL, HT_K_MISC = range(9)
@@ -114,6 +115,7 @@ def load(build_if_missing: bool = True):
             "ht_profile_set": ([ctypes.c_uint], ctypes.c_int),
             "ht_profile_read": ([ctypes.c_int, i64p, f64p, f64p, ctypes.c_int], ctypes.c_int),
             "ht_launch_count": ([i64p], ctypes.c_int),
+            "ht_device_status": ([], ctypes.c_int),
             "ht_gramians_noalloc": ([vp, vp, ctypes.c_int], ctypes.c_int),
             "ht_graph_add_truncate": ([ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
                                        ctypes.POINTER(TruncOpts), ctypes.POINTER(vp)], ctypes.c_int),
@@ -343,6 +345,11 @@ def ht_launch_count() -> int:
     n = ctypes.c_int64()
     _check(load().ht_launch_count(ctypes.byref(n)))
     return n.value
+
+
+def ht_device_status() -> None:
+    """Synchronises; raises HTError(HT_ETIMEOUT) if a kernel's bounded wait gave up since the last call."""
+    _check(load().ht_device_status())
 
 
 # ---------------------------------------------------------------------------

@@ -25,3 +25,13 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _device_status_after_gpu_tests(request):
+    """Every GPU test ends with the library's device check: no CUDA error and
+    no bounded in-kernel wait that gave up."""
+    yield
+    if "gpu" in request.keywords:
+        from paper_1708_03340_gb300 import htgb
+        htgb.ht_device_status()
