@@ -20,16 +20,19 @@ constexpr int kRegRows = 256;  // rows of a register-resident block (32 x NI)
 // products reduce over the 8 lanes of its group (3 shuffles) and shared
 // vectors are read four rows at a time.
 //
-// Column j's reflector H_j = I - tau_j v_j v_j^T, v_j = [0; 1; scl_j w_j],
-// where w_j is the part of column j below the diagonal (after H_0..H_{j-1}).
-// The group owning column j forms ||w_j||, beta_j, tau_j and scl_j from its
-// registers and publishes them with w_j in shared memory; after one barrier
-// every warp holding a column right of j applies H_j (one dot product per
-// column, 3 shuffles), and the owner of column j+1 publishes the next
-// reflector.  One barrier per column.
+// Column j's reflector is kept in the scaled form H_j = I - tau_j v_j v_j^T
+// with v_j(j) = 1, v_j zero above row j and scl_j times the column below it
+// (|v_j| <= 1 entrywise, tau_j in [1, 2]).  The warp owning column j forms
+// ||.||^2 below the diagonal, beta_j = R(j, j), tau_j and scl_j from its
+// registers and stores v_j and tau_j in shared memory; after one barrier
+// every warp holding a column right of j applies H_j with one dot product
+// (one 8-lane sum) and one axpy: a -= tau_j (v_j^T a) v_j.  Row j needs no
+// special case, since v_j(j) = 1.  The owner of column j+1 forms the next
+// reflector right after its own update.  One barrier per column.
 //
-// The w_j stay in shared memory, so Q = H_0 ... H_{n-1} [I; 0] is then
-// accumulated backwards on the columns in registers without barriers.
+// The v_j stay in shared memory, so Q = H_0 ... H_{n-1} [I; 0] is then
+// accumulated backwards on the columns in registers without barriers, the
+// reflector of the next step loaded while the current one is applied.
 // ---------------------------------------------------------------------------
 constexpr int REG_MR = kRegRows;  // leading dimension of the reflector array (rows)
 
@@ -58,75 +61,74 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
-// Row j (< 64) of the lane's column, or 0 if the lane does not hold it.
+// Row j (< 64) of column c of the lane's warp, broadcast to the group that
+// holds column c (one select tree and one shuffle).
 template <typename T, int NI>
-__device__ __forceinline__ T row_of(const T (&a)[NI][4], int j, int s) {
-  T x = T(0);
-#pragma unroll
-  for (int i = 0; i < 2 && i < NI; ++i)
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if (32 * i + 4 * s + e == j) x = a[i][e];
-  return x;
+__device__ __forceinline__ T row_value(const T (&a)[NI][4], int j, int lane) {
+  const int e = j & 3;
+  const T y0 = (e & 1) ? a[0][1] : a[0][0], y1 = (e & 1) ? a[0][3] : a[0][2];
+  const T z0 = (e & 1) ? a[1][1] : a[1][0], z1 = (e & 1) ? a[1][3] : a[1][2];
+  const T y = (e & 2) ? y1 : y0, z = (e & 2) ? z1 : z0;
+  return __shfl_sync(0xffffffffu, (j >> 5) ? z : y, (lane & ~7) | ((j >> 2) & 7));
 }
 
+// Form column j's reflector from the lane's registers (called by the whole
+// warp that owns column j, after H_0..H_{j-1} reached it): the owner group
+// stores v_j into vj and tau_j, and its lanes set R(j, j) = beta_j in their
+// registers (rows below j become free: they are held in vj).
 template <typename T, int NI>
-__device__ __forceinline__ void row_sub(T (&a)[NI][4], int j, int s, T d) {
-#pragma unroll
-  for (int i = 0; i < 2 && i < NI; ++i)
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if (32 * i + 4 * s + e == j) a[i][e] -= d;
-}
-
-// Publish column j's reflector: w_j (the part below the diagonal, rows <= j
-// zero) into wj, and tau_j, scl_j, beta_j (R(j, j)) formed from ||w_j|| and
-// alpha_j = the diagonal entry; only the lanes with me set (the owner group)
-// write.  Called by the whole warp (the reductions span it).
-template <typename T, int NI>
-__device__ __forceinline__ void publish(const T (&a)[NI][4], T *wj, T *tau_j, T *scl_j, T *beta_j, int j, int s,
-                                        bool me) {
+__device__ __forceinline__ void form_reflector(T (&a)[NI][4], T *vj, T *tau_j, int j, int lane, bool me) {
+  const int s = lane & 7;
   T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
-    T x[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int r = 32 * i + 4 * s + e;
-      x[e] = (i >= 2 || r > j) ? a[i][e] : T(0);  // j < 64: rows of chunks i >= 2 lie below j
+      const T x = (i >= 2 || r > j) ? a[i][e] : T(0);  // j < 64: rows of chunks i >= 2 lie below j
+      if (e == 0) q0 += x * x;
+      if (e == 1) q1 += x * x;
+      if (e == 2) q2 += x * x;
+      if (e == 3) q3 += x * x;
     }
-    q0 += x[0] * x[0];
-    q1 += x[1] * x[1];
-    q2 += x[2] * x[2];
-    q3 += x[3] * x[3];
-    if (me) st4(wj + 32 * i + 4 * s, x);
   }
   const T s2 = group_sum((q0 + q1) + (q2 + q3));
-  const T alpha = group_sum(row_of<T, NI>(a, j, s));
-  if (!me || s != 0) return;
-  T tj = T(0), beta = alpha, sc = T(0);
+  const T alpha = row_value<T, NI>(a, j, lane);
+  // beta = R(j, j) = -sign(alpha) sqrt(alpha^2 + s2), tau = (beta - alpha) / beta,
+  // scl = 1 / (alpha - beta); the identity (tau = 0, v = e_j) when s2 = 0
+  T tj = T(0), sc = T(0), beta = alpha;
   if (s2 != T(0)) {
     const T nrm = sqrt(alpha * alpha + s2);
     beta = (alpha <= T(0)) ? nrm : -nrm;
     tj = (beta - alpha) / beta;
     sc = T(1) / (alpha - beta);
   }
-  *tau_j = tj;
-  *scl_j = sc;
-  *beta_j = beta;
+  if (!me) return;
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    T x[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = 32 * i + 4 * s + e;
+      x[e] = (i >= 2 || r > j) ? sc * a[i][e] : (r == j ? T(1) : T(0));
+      if (i < 2 && r == j) a[i][e] = beta;
+    }
+    st4(vj + 32 * i + 4 * s, x);
+  }
+  if (s == 0) *tau_j = tj;
 }
 
-// a <- H_j a for the lane's column: d = a_j + scl (w^T a), a -= tau d v.
-// Every lane takes part in the reductions; upd says whether this lane's
-// column takes the update.  kKeep keeps w in registers between the passes.
+// a <- a - tau (v^T a) v for the lane's column (v in shared memory; x holds
+// it on return when kKeep).  upd = false leaves a unchanged (the reduction
+// spans the warp, so every lane takes part).
 template <typename T, int NI, bool kKeep>
-__device__ __forceinline__ void reg_apply(T (&a)[NI][4], const T *wj, int j, T tj, T scl, bool upd, int s) {
+__device__ __forceinline__ void apply_reflector(T (&a)[NI][4], const T *vj, T tj, bool upd, int s) {
   T v[kKeep ? NI : 1][4];
   T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     T x[4];
-    ld4(wj + 32 * i + 4 * s, x);
+    ld4(vj + 32 * i + 4 * s, x);
     d0 += x[0] * a[i][0];
     d1 += x[1] * a[i][1];
     d2 += x[2] * a[i][2];
@@ -136,12 +138,8 @@ __device__ __forceinline__ void reg_apply(T (&a)[NI][4], const T *wj, int j, T t
       for (int e = 0; e < 4; ++e) v[kKeep ? i : 0][e] = x[e];
     }
   }
-  const T aj = group_sum(row_of<T, NI>(a, j, s));
-  const T sw = group_sum((d0 + d1) + (d2 + d3));
-  if (!upd) return;
-  const T d = tj * (aj + scl * sw);  // tau (v^T a)
-  const T ds = d * scl;
-  row_sub<T, NI>(a, j, s, d);
+  const T sum = group_sum((d0 + d1) + (d2 + d3));
+  const T d = upd ? tj * sum : T(0);
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     T x[4];
@@ -149,10 +147,10 @@ __device__ __forceinline__ void reg_apply(T (&a)[NI][4], const T *wj, int j, T t
 #pragma unroll
       for (int e = 0; e < 4; ++e) x[e] = v[kKeep ? i : 0][e];
     } else {
-      ld4(wj + 32 * i + 4 * s, x);
+      ld4(vj + 32 * i + 4 * s, x);
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) a[i][e] -= ds * x[e];
+    for (int e = 0; e < 4; ++e) a[i][e] -= d * x[e];
   }
 }
 
@@ -161,10 +159,8 @@ __global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restric
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const QrItem it = items[blockIdx.x];
   const int m = it.m, n = it.n;
-  T *W = reinterpret_cast<T *>(smem_raw);  // REG_MR x n: w_j in column j
-  T *tau = W + (int64_t)REG_MR * n;        // n
-  T *scl = tau + n;                        // n
-  T *bet = scl + n;                        // n: R(j, j)
+  T *V = reinterpret_cast<T *>(smem_raw);  // REG_MR x n: v_j in column j
+  T *tau = V + (int64_t)REG_MR * n;        // n
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 3, s = lane & 7;
   const int c = 4 * warp + g;  // this lane's column
@@ -177,25 +173,14 @@ __global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restric
       const int r = 32 * i + 4 * s + e;
       a[i][e] = (c < n && r < m) ? A[r] : T(0);
     }
-  if (warp == 0) publish<T, NI>(a, W, tau, scl, bet, 0, s, g == 0);
-  for (int j = 0; j < n; ++j) {
-    __syncthreads();
-    if (4 * warp + 3 < j) continue;  // every column of this warp is finished
-    const T *wj = W + (int64_t)j * REG_MR;
-    const T tj = tau[j], sc = scl[j];
-    if (c == j) {  // the owner: R(j, j) = beta; rows below j are not read again
-      const T beta = bet[j];
-#pragma unroll
-      for (int i = 0; i < 2 && i < NI; ++i)
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (32 * i + 4 * s + e == j) a[i][e] = beta;
-    }
-    if (4 * warp + 3 > j && tj != T(0))  // H_j on the columns right of j
-      reg_apply<T, NI, KEEP>(a, wj, j, tj, sc, c > j, s);
-    if (j + 1 < n && warp == ((j + 1) >> 2))  // the owner warp of column j+1 publishes its reflector
-      publish<T, NI>(a, W + (int64_t)(j + 1) * REG_MR, tau + j + 1, scl + j + 1, bet + j + 1, j + 1, s,
-                     g == ((j + 1) & 3));
+  if (warp == 0) form_reflector<T, NI>(a, V, tau, 0, lane, g == 0);
+  for (int j = 0; j + 1 < n; ++j) {
+    __syncthreads();                  // v_j and tau_j are in shared memory
+    if (4 * warp + 3 <= j) continue;  // no column of this warp lies right of j
+    const T *vj = V + (int64_t)j * REG_MR;
+    apply_reflector<T, NI, KEEP>(a, vj, tau[j], c > j, s);
+    if (warp == ((j + 1) >> 2))       // the owner of column j+1 forms its reflector
+      form_reflector<T, NI>(a, V + (int64_t)(j + 1) * REG_MR, tau + j + 1, j + 1, lane, g == ((j + 1) & 3));
   }
   __syncthreads();
   // R (n x n upper triangular) from the registers
@@ -211,17 +196,13 @@ __global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restric
   }
   // Explicit Q = H_0 H_1 ... H_{n-1} [I; 0], accumulated backwards on the
   // columns of [I; 0].  Column c is untouched by H_j for j > c (v_j is zero
-  // above row j, column c is e_c there), so a warp whose columns all lie
-  // left of j skips H_j.
+  // above row j, column c is e_c there), so warp w starts at j = 4w + 3.
 #pragma unroll
   for (int i = 0; i < NI; ++i)
 #pragma unroll
     for (int e = 0; e < 4; ++e) a[i][e] = (32 * i + 4 * s + e == c) ? T(1) : T(0);
-  for (int j = n - 1; j >= 0; --j) {
-    if (4 * warp + 3 < j) continue;
-    const T tj = tau[j];
-    if (tj != T(0)) reg_apply<T, NI, KEEP>(a, W + (int64_t)j * REG_MR, j, tj, scl[j], true, s);
-  }
+  for (int j = min(n - 1, 4 * warp + 3); j >= 0; --j)
+    apply_reflector<T, NI, KEEP>(a, V + (int64_t)j * REG_MR, tau[j], true, s);
   T *Q = static_cast<T *>(it.Q) + (int64_t)c * it.ldq;
   if (c < n) {
 #pragma unroll
@@ -237,7 +218,7 @@ __global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restric
 template <typename T, int NW, int NI>
 cudaError_t launch_qr_reg(const QrItem *d_items, int n_items, int max_n, cudaStream_t s) {
   constexpr bool kKeep = sizeof(T) * NI <= 32;  // FP32 keeps w in registers, FP64 reads it twice
-  const size_t smem = ((size_t)REG_MR * max_n + 3 * max_n) * sizeof(T);
+  const size_t smem = ((size_t)REG_MR * max_n + max_n) * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(qr_reg_kernel<T, NW, NI, kKeep>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   qr_reg_kernel<T, NW, NI, kKeep><<<n_items, NW * 32, smem, s>>>(d_items);
