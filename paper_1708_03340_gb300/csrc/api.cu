@@ -254,6 +254,7 @@ struct Launch {
   int variant = 0;              // GEMM: SIMT tile shape (gemm_tile_shape)
   bool comp = true;             // GEMM: compensated FP32 accumulation
   bool df = false;              // GEMM: double-float accumulation, FP64 output (square-root Gramians)
+  int uniform = 0;              // GEMM: tiles of every item when all items have the same count (else 0)
 };
 
 template <typename P>
@@ -546,13 +547,17 @@ void choose_gemm_variant(Plan &P, Launch &L) {
   int bm = 64, bn = 64;
   gemm_tile_shape(L.variant, &bm, &bn);
   int tiles = 0;
+  L.uniform = -1;
   for (int i = 0; i < L.n; ++i) {
     it[i].tiles_m = (it[i].M + bm - 1) / bm;
     it[i].tiles_n = (it[i].N + bn - 1) / bn;
     it[i].tile0 = tiles;
-    tiles += it[i].tiles_m * it[i].tiles_n * it[i].batch * it[i].ksplit;
+    const int per = it[i].tiles_m * it[i].tiles_n * it[i].batch * it[i].ksplit;
+    tiles += per;
+    L.uniform = (L.uniform == -1 || L.uniform == per) ? per : 0;
   }
   L.tiles = tiles;
+  if (L.uniform < 0) L.uniform = 0;
 }
 
 // Workspace size of a plan: persistent | scratch | metadata | items.
@@ -643,9 +648,9 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
         // FP32 launches whose flops sit mostly in tall items run on the tensor cores
         const bool tc = !f64 && tc_enabled() && L.tc_flops >= 0.5 * L.flops;
         e = f64 ? launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s, L.variant, false,
-                                      false)
+                                      false, L.uniform)
                 : launch_gemm<float>((const GemmItem *)items, L.n, L.tiles, rk, L.split,
-                                     (tc && !L.df) ? L.tc_tiles : 0, s, L.variant, L.comp, L.df);
+                                     (tc && !L.df) ? L.tc_tiles : 0, s, L.variant, L.comp, L.df, L.uniform);
         break;
       }
       case L_QR:

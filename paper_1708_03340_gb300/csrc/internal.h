@@ -121,9 +121,11 @@ struct RankItem {
 // out for that shape (gemm_tile_shape).  comp: Kahan-compensated FP32
 // accumulation across the BK-wide tiles of a CTA.  df (FP32 only): double-float
 // accumulation of exact products, FP64 output and split-K partials.
+// uniform > 0: every item has that many tiles (tile -> item by division).
 template <typename T>
 cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks,
-                        bool any_split, int tc_tiles, cudaStream_t s, int variant, bool comp, bool df);
+                        bool any_split, int tc_tiles, cudaStream_t s, int variant, bool comp, bool df,
+                        int uniform = 0);
 void gemm_tile_shape(int variant, int *bm, int *bn);
 cudaError_t launch_gemm_tc(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, cudaStream_t s);
 template <typename T>

@@ -85,7 +85,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <typename T, int BM, int BN, int TM, int TN, int BK, int kAcc>
 __global__ void __launch_bounds__(THREADS, sizeof(T) != 4 ? 1
                                            : (BM * BN <= 64 * 64 ? (kAcc == 0 ? 3 : 2) : (BM * BN <= 128 * 64 && kAcc == 0 ? 2 : 1)))
-    gemm_kernel(const GemmItem *__restrict__ items, int n_items,
+    gemm_kernel(const GemmItem *__restrict__ items, int n_items, int uniform,
                                                         const int *__restrict__ ranks) {
   constexpr bool kComp = (kAcc == 1);
   constexpr bool kDF = (kAcc == 2) && sizeof(T) == 4;  // double-float accumulation, FP64 output
@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) != 4 ? 1
   __shared__ __align__(16) T As[NS][BK][BM + PAD];
   __shared__ __align__(16) T Bs[NS][BK][BN + PAD];
   const int tile = blockIdx.x;
-  const GemmItem &it = items[find_item(items, n_items, tile)];
+  // all items of most launches have the same tile count: no search then
+  const GemmItem &it = items[uniform > 0 ? tile / uniform : find_item(items, n_items, tile)];
   int local = tile - it.tile0;
   const int tm = local % it.tiles_m;
   local /= it.tiles_m;
@@ -264,31 +265,59 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) != 4 ? 1
     }
     return (OutT)acc[i][j];
   };
+  // A thread's rows come in groups of 4 consecutive rows: where the output is
+  // FP32 with unit row stride, a group is one 16-byte store if aligned and
+  // inside M.
   if (it.ksplit > 1) {
     OutT *P = static_cast<OutT *>(it.part) + ((int64_t)chunk * it.batch + b) * (int64_t)it.M * it.N;
 #pragma unroll
-    for (int i = 0; i < TM; ++i)
+    for (int j = 0; j < TN; ++j) {
+      const int gn = n0 + col_of(j);
+      if (gn >= N) continue;
 #pragma unroll
-      for (int j = 0; j < TN; ++j) {
-        const int gm = m0 + row_of(i), gn = n0 + col_of(j);
-        if (gm < M && gn < N) P[(int64_t)gn * it.M + gm] = result(i, j);
+      for (int gi = 0; gi < TM / 4; ++gi) {
+        const int gm0 = m0 + row_of(4 * gi);
+        OutT *pp = P + (int64_t)gn * it.M + gm0;
+        if (sizeof(OutT) == 4 && gm0 + 3 < M && (reinterpret_cast<uintptr_t>(pp) & 15) == 0) {
+          *reinterpret_cast<float4 *>(pp) = make_float4((float)result(4 * gi, j), (float)result(4 * gi + 1, j),
+                                                        (float)result(4 * gi + 2, j), (float)result(4 * gi + 3, j));
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (gm0 + u < M) pp[u] = result(4 * gi + u, j);
+        }
       }
+    }
     return;
   }
   OutT *C = static_cast<OutT *>(it.C) + (int64_t)b * it.scb;
   const OutT alpha = OutT(it.alpha), beta = OutT(it.beta);
+  const bool vec = sizeof(OutT) == 4 && it.scm == 1 && beta == OutT(0);
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
+  for (int j = 0; j < TN; ++j) {
+    const int gn = n0 + col_of(j);
+    if (gn >= N) continue;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      const int gm = m0 + row_of(i), gn = n0 + col_of(j);
-      if (gm < M && gn < N) {
-        OutT *c = C + (int64_t)gm * it.scm + (int64_t)gn * it.scn;
-        OutT v = alpha * result(i, j);
-        if (beta != OutT(0)) v += beta * *c;
-        *c = v;
+    for (int gi = 0; gi < TM / 4; ++gi) {
+      const int gm0 = m0 + row_of(4 * gi);
+      OutT *cp = C + (int64_t)gm0 * it.scm + (int64_t)gn * it.scn;
+      if (vec && gm0 + 3 < M && (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+        *reinterpret_cast<float4 *>(cp) =
+            make_float4((float)(alpha * result(4 * gi, j)), (float)(alpha * result(4 * gi + 1, j)),
+                        (float)(alpha * result(4 * gi + 2, j)), (float)(alpha * result(4 * gi + 3, j)));
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (gm0 + u < M) {
+            OutT *c = cp + (int64_t)u * it.scm;
+            OutT v = alpha * result(4 * gi + u, j);
+            if (beta != OutT(0)) v += beta * *c;
+            *c = v;
+          }
+        }
       }
     }
+  }
 }
 
 // Sum the split-K partials of every split item in chunk order.
@@ -321,7 +350,7 @@ __global__ void gemm_reduce_kernel(const GemmItem *__restrict__ items, const int
 
 template <typename T>
 cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, bool any_split,
-                        int tc_tiles, cudaStream_t s, int variant, bool comp, bool df) {
+                        int tc_tiles, cudaStream_t s, int variant, bool comp, bool df, int uniform) {
   if (n_items <= 0 || total_tiles <= 0) return cudaSuccess;
   if (sizeof(T) == 4 && tc_tiles > 0) {
     cudaError_t e = launch_gemm_tc(d_items, n_items, tc_tiles, d_ranks, s);
@@ -331,15 +360,15 @@ cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, c
     // double-float accumulation (FP64 output) when asked for
     const bool c = (sizeof(T) == 4) && comp;
     if (sizeof(T) == 4 && df) {
-      gemm_kernel<T, 64, 64, 4, 4, 16, 2><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+      gemm_kernel<T, 64, 64, 4, 4, 16, 2><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, uniform, d_ranks);
     } else if (variant == 2 && !c) {
-      gemm_kernel<T, 128, 128, 8, 8, 16, 0><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+      gemm_kernel<T, 128, 128, 8, 8, 16, 0><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, uniform, d_ranks);
     } else if (variant >= 1) {
-      if (c) gemm_kernel<T, 128, 64, 8, 4, 16, 1><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
-      else gemm_kernel<T, 128, 64, 8, 4, 16, 0><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+      if (c) gemm_kernel<T, 128, 64, 8, 4, 16, 1><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, uniform, d_ranks);
+      else gemm_kernel<T, 128, 64, 8, 4, 16, 0><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, uniform, d_ranks);
     } else {
-      if (c) gemm_kernel<T, 64, 64, 4, 4, 16, 1><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
-      else gemm_kernel<T, 64, 64, 4, 4, 16, 0><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, d_ranks);
+      if (c) gemm_kernel<T, 64, 64, 4, 4, 16, 1><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, uniform, d_ranks);
+      else gemm_kernel<T, 64, 64, 4, 4, 16, 0><<<total_tiles, THREADS, 0, s>>>(d_items, n_items, uniform, d_ranks);
     }
     count_launch();
   }
@@ -357,9 +386,9 @@ cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, c
 }
 
 template cudaError_t launch_gemm<double>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t, int, bool,
-                                         bool);
+                                         bool, int);
 template cudaError_t launch_gemm<float>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t, int, bool,
-                                        bool);
+                                       bool, int);
 
 void gemm_tile_shape(int variant, int *bm, int *bn) {
   *bm = (variant >= 1) ? 128 : 64;

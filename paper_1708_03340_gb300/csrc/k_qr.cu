@@ -72,6 +72,23 @@ __device__ __forceinline__ T row_value(const T (&a)[NI][4], int j, int lane) {
   return __shfl_sync(0xffffffffu, (j >> 5) ? z : y, (lane & ~7) | ((j >> 2) & 7));
 }
 
+// Householder scalars of a column with diagonal entry alpha and squared norm
+// s2 below it: beta = R(j, j) = -sign(alpha) sqrt(alpha^2 + s2), tau = (beta
+// - alpha) / beta and scl = 1 / (alpha - beta), with IEEE square root and
+// divisions (reciprocal-square-root forms cost FP32 about twice the
+// orthogonality error on ||X||); the identity (tau = 0, scl = 0, beta =
+// alpha) when s2 = 0.
+template <typename T>
+__device__ __forceinline__ void reflector_scalars(T alpha, T s2, T &tj, T &sc, T &beta) {
+  tj = T(0), sc = T(0), beta = alpha;
+  if (s2 != T(0)) {
+    const T nrm = sqrt(alpha * alpha + s2);
+    beta = (alpha <= T(0)) ? nrm : -nrm;
+    tj = (beta - alpha) / beta;
+    sc = T(1) / (alpha - beta);
+  }
+}
+
 // Form column j's reflector from the lane's registers (called by the whole
 // warp that owns column j, after H_0..H_{j-1} reached it): the owner group
 // stores v_j into vj and tau_j, and its lanes set R(j, j) = beta_j in their
@@ -94,15 +111,8 @@ __device__ __forceinline__ void form_reflector(T (&a)[NI][4], T *vj, T *tau_j, i
   }
   const T s2 = group_sum((q0 + q1) + (q2 + q3));
   const T alpha = row_value<T, NI>(a, j, lane);
-  // beta = R(j, j) = -sign(alpha) sqrt(alpha^2 + s2), tau = (beta - alpha) / beta,
-  // scl = 1 / (alpha - beta); the identity (tau = 0, v = e_j) when s2 = 0
-  T tj = T(0), sc = T(0), beta = alpha;
-  if (s2 != T(0)) {
-    const T nrm = sqrt(alpha * alpha + s2);
-    beta = (alpha <= T(0)) ? nrm : -nrm;
-    tj = (beta - alpha) / beta;
-    sc = T(1) / (alpha - beta);
-  }
+  T tj, sc, beta;
+  reflector_scalars(alpha, s2, tj, sc, beta);
   if (!me) return;
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
