@@ -3,7 +3,7 @@
 
 One step = ht_add (Lemma "sum of two H-tensors") of seeded HT tensor pairs
 followed by the truncation of each sum (orthogonalization, reduced Gramians,
-FP64 eigendecompositions, rank selection, projection), replayed as one CUDA
+refined eigendecompositions, rank selection, projection), replayed as one CUDA
 graph (ht_graph_add_truncate / ht_graph_launch).  Workloads (--config):
 
   single   d=64, n=1000, k=32 -> rank 64, orthonormal Gaussian leaves,
@@ -384,7 +384,7 @@ def main():
         ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs))
         return dict(ms=ms, launches=htgb.ht_launch_count() - l0, prof=prof, X=X)
 
-    # ---- headline: graph replays of the FP32-storage path (FP64 eigensolves)
+    # ---- headline: graph replays of the FP32-storage path (FP32 eigensolves refined to FP64 level)
     clk_path = os.path.join(tempfile.gettempdir(), f"htgb_clocks_{os.getpid()}.csv")
     proc, fh = start_clock_sampler(clk_path)
     main_arm = graph_arm(htgb.HT_F32, htgb.HT_PREC_FP32, args.steps, args.warmup)
@@ -424,7 +424,7 @@ def main():
         "data": "synthetic (seeded SplitMix64/Box-Muller HT tensors)",
         "config": {"workload": args.config, "tensors_per_step": per_step, "shape": WORKLOADS[args.config]["desc"],
                    "l2": "flushed between steps (256 MB write)",
-                   "path": "FP32 storage and contractions, FP64 eigensolves, one batched launch per level, "
+                   "path": "FP32 storage and contractions, FP32 eigensolves refined in double-float, one batched launch per level, "
                            "CUDA-graph replay"},
         "gflops": work / (ms_per_step / 1e3) / 1e9,
         "direct_calls_ms_per_step": prof["ms"] / psteps,

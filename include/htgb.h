@@ -56,7 +56,9 @@ typedef enum { HT_F64 = 0, HT_F32 = 1 } ht_dtype;
 
 /* Arithmetic of the truncation.  HT_PREC_FP64: every step in FP64 (F64
  * tensors).  HT_PREC_FP32: storage and dense contractions in FP32, the small
- * k x k Gramian eigendecompositions in FP64 (F32 tensors).
+ * k x k Gramian eigendecompositions solved in FP32 and refined to FP64-level
+ * accuracy (one Ogita-Aishima step; its products in double-float, about
+ * 48 bits, for k <= 64, in FP64 beyond) (F32 tensors).
  * HT_PREC_FP32_SQRT: as HT_PREC_FP32, but the reduced Gramians of Sec. 3.3
  * are carried as square-root factors Ghat_t = S_t S_t^T (top-down: the sons'
  * Gramians are Gram products of B_t contracted with S_t, accumulated exactly
@@ -257,7 +259,7 @@ ht_status ht_eval_entries(const ht_tensor *x, const int64_t *idx, int64_t m, dou
 typedef enum {
   HT_K_GEMM = 0,    /* strided batched contractions (mode products, Gramians, leaf products, TSQR recombination) */
   HT_K_QR = 1,      /* Householder QR of shared-memory row blocks (TSQR) */
-  HT_K_EIG = 2,     /* FP64 symmetric eigensolver */
+  HT_K_EIG = 2,     /* symmetric eigensolver (FP64, or FP32 + refinement) */
   HT_K_COPY = 3,    /* copies, casts, identity fills */
   HT_K_COMPACT = 4, /* packing of projected transfer tensors */
   HT_K_RANKS = 5,   /* rank selection and ||X|| */

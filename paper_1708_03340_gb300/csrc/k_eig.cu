@@ -60,6 +60,19 @@ __device__ double block_max_d(double v, double *red) {
   return s;
 }
 
+// Position of eigenvalue i in descending order (ties by index; NaN last):
+// every thread ranks its own values, so the order costs O(k) per thread.
+template <typename T>
+__device__ __forceinline__ int desc_rank(const T *lam, int k, int i) {
+  const double li = isnan((double)lam[i]) ? -INFINITY : (double)lam[i];
+  int r = 0;
+  for (int j = 0; j < k; ++j) {
+    const double lj = isnan((double)lam[j]) ? -INFINITY : (double)lam[j];
+    r += (lj > li || (lj == li && j < i)) ? 1 : 0;
+  }
+  return r;
+}
+
 struct EigShared {
   int count;
   int lo;
@@ -316,17 +329,7 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
     __syncthreads();
   }
   // 4. sort descending, unscale
-  if (tid == 0) {
-    for (int i = 0; i < k; ++i) perm[i] = i;
-    for (int i = 0; i < k; ++i) {
-      int best = i;
-      for (int j = i + 1; j < k; ++j)
-        if (dg[perm[j]] > dg[perm[best]]) best = j;
-      int t = perm[i];
-      perm[i] = perm[best];
-      perm[best] = t;
-    }
-  }
+  for (int i = tid; i < k; i += nt) perm[desc_rank(dg, k, i)] = i;
   __syncthreads();
   for (int e = tid; e < k * k; e += nt) {
     int c = e / k, r = e - c * k;
@@ -429,23 +432,162 @@ __global__ void __launch_bounds__(EIG_THREADS) refine_kernel(const EigItem *__re
   small_gemm(X, W2, W1, k, false);  // W1 = X E
   __syncthreads();
   for (int e = tid; e < kk; e += nt) W1[e] += X[e];
-  if (tid == 0) {
-    for (int i = 0; i < k; ++i) perm[i] = i;
-    for (int i = 0; i < k; ++i) {
-      int best = i;
-      for (int j = i + 1; j < k; ++j)
-        if (lam[perm[j]] > lam[perm[best]]) best = j;
-      int t = perm[i];
-      perm[i] = perm[best];
-      perm[best] = t;
-    }
-  }
+  for (int i = tid; i < k; i += nt) perm[desc_rank(lam, k, i)] = i;
   __syncthreads();
   for (int e = tid; e < kk; e += nt) {
     const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
     it.V[e] = W1[(int64_t)perm[c] * k + r];
   }
   for (int c = tid; c < k; c += nt) it.lam[c] = lam[perm[c]] * scale;
+}
+
+// ---- double-float refinement (k <= kDfMaxK) ---------------------------------
+// The same Ogita-Aishima step with its four k x k products on the FP32 pipes:
+// every product of FP32 operands is carried exactly as a pair (p, e) with p =
+// a b rounded and e = fma(a, b, -p), and summed into a double-float (hi, lo)
+// with a two-sum (Dekker / Knuth error-free transformations); the symmetrised
+// scaled Gramian A is split into A_hi + A_lo (48 bits), the FP32 solve's
+// eigenvectors X are FP32 numbers.  The sums are accurate to about 2^-48
+// relative, far below the FP32 Gramian's own error; lambda, R, S and E are
+// formed in FP64 from the double-float results.  GB300 runs FP32 at 64 times
+// its FP64 rate, so this is several times faster than FP64 products.
+constexpr int kDfMaxK = 64;
+
+__device__ __forceinline__ void df_mac(float &hi, float &lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);  // a b = p + e exactly
+  const float t = __fadd_rn(hi, p);
+  const float bp = __fsub_rn(t, hi);
+  const float e2 = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));  // hi + p = t + e2 exactly
+  hi = t;
+  lo = __fadd_rn(lo, __fadd_rn(e2, e));
+}
+
+// C = op(A) B for k x k column-major matrices in shared memory (leading
+// dimension ld), A = Ah (+ Al), B = Bh (+ Bl): high parts multiplied exactly,
+// the cross terms rounded into the low word.  op(A)_il = A[i ld + l] when
+// kTransA, else A[l ld + i].  Each thread accumulates a 4 x 4 block; the
+// threads of a warp share their rows (broadcast reads of A).
+template <bool kTransA, bool kALo, bool kBLo>
+__device__ void df_gemm(const float *Ah, const float *Al, const float *Bh, const float *Bl, float *Ch, float *Cl,
+                        int k, int ld) {
+  const int tiles = (k + 3) / 4;
+  for (int t = threadIdx.x; t < tiles * tiles; t += blockDim.x) {
+    const int ti = (t / tiles) * 4, tj = (t % tiles) * 4;
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) hi[u][v] = lo[u][v] = 0.0f;
+    for (int l = 0; l < k; ++l) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = ti + u, j = tj + u;
+        const int ia = kTransA ? i * ld + l : l * ld + i;
+        ah[u] = (i < k) ? Ah[ia] : 0.0f;
+        al[u] = (kALo && i < k) ? Al[ia] : 0.0f;
+        bh[u] = (j < k) ? Bh[j * ld + l] : 0.0f;
+        bl[u] = (kBLo && j < k) ? Bl[j * ld + l] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          df_mac(hi[u][v], lo[u][v], ah[u], bh[v]);
+          if (kALo) lo[u][v] = __fmaf_rn(al[u], bh[v], lo[u][v]);
+          if (kBLo) lo[u][v] = __fmaf_rn(ah[u], bl[v], lo[u][v]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (ti + u < k && tj + v < k) {
+          const float s = __fadd_rn(hi[u][v], lo[u][v]);  // renormalise: |lo| <= ulp(hi) / 2
+          Ch[(tj + v) * ld + ti + u] = s;
+          Cl[(tj + v) * ld + ti + u] = __fsub_rn(lo[u][v], __fsub_rn(s, hi[u][v]));
+        }
+  }
+}
+
+size_t refine_df_smem(int max_k) {
+  return (size_t)(kDfMaxK + 32) * sizeof(double) + (size_t)kDfMaxK * sizeof(int) +
+         7 * (size_t)max_k * (max_k + 1) * sizeof(float);
+}
+
+__global__ void __launch_bounds__(EIG_THREADS) refine_df_kernel(const EigItem *__restrict__ items) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const EigItem it = items[blockIdx.x];
+  const int k = it.k, tid = threadIdx.x, nt = blockDim.x, ld = k + 1;  // odd ld: 2-way bank conflicts at most
+  const int sz = k * ld;
+  double *lam = reinterpret_cast<double *>(smem_raw);  // k
+  double *red = lam + kDfMaxK;                          // 32
+  int *rank = reinterpret_cast<int *>(red + 32);        // k
+  float *Ah = reinterpret_cast<float *>(rank + kDfMaxK);
+  float *Al = Ah + sz, *X = Al + sz, *Th = X + sz, *Tl = Th + sz, *Sh = Tl + sz, *Sl = Sh + sz;
+  double mx = 0.0;
+  for (int e = tid; e < k * k; e += nt) mx = fmax(mx, fabs(it.G[e]));
+  mx = block_max_d(mx, red);
+  const double scale = (mx > 0.0) ? mx : 1.0, inv_scale = 1.0 / scale;
+  for (int e = tid; e < k * k; e += nt) {
+    const int c = e / k, r = e - c * k;
+    const double a = 0.5 * (it.G[(int64_t)c * k + r] + it.G[(int64_t)r * k + c]) * inv_scale;
+    const float ah = (float)a;
+    Ah[c * ld + r] = ah;
+    Al[c * ld + r] = (float)(a - (double)ah);
+    X[c * ld + r] = (float)it.V[e];  // the FP32 solve's eigenvectors: exact
+  }
+  __syncthreads();
+  df_gemm<false, true, false>(Ah, Al, X, nullptr, Th, Tl, k, ld);  // T = A X
+  __syncthreads();
+  df_gemm<true, false, true>(X, nullptr, Th, Tl, Sh, Sl, k, ld);   // S = X^T T
+  __syncthreads();
+  df_gemm<true, false, false>(X, nullptr, X, nullptr, Ah, Al, k, ld);  // P = X^T X = I - R
+  __syncthreads();
+  // lambda_i = S_ii / (1 - R_ii) = S_ii / P_ii
+  for (int i = tid; i < k; i += nt)
+    lam[i] = ((double)Sh[i * ld + i] + (double)Sl[i * ld + i]) / ((double)Ah[i * ld + i] + (double)Al[i * ld + i]);
+  double so = 0.0, ro = 0.0;
+  for (int e = tid; e < k * k; e += nt) {
+    const int c = e / k, r = e - c * k;
+    const double P = (double)Ah[c * ld + r] + (double)Al[c * ld + r];
+    if (r != c) so = fmax(so, fabs((double)Sh[c * ld + r] + (double)Sl[c * ld + r]));
+    ro = fmax(ro, fabs((r == c ? 1.0 : 0.0) - P));
+  }
+  __syncthreads();
+  double lm = 0.0;
+  for (int i = tid; i < k; i += nt) lm = fmax(lm, fabs(lam[i]));
+  so = block_max_d(so, red);
+  ro = block_max_d(ro, red);
+  lm = block_max_d(lm, red);
+  const double delta = 2.0 * (so + lm * ro) * (double)k;
+  // E (FP64, stored as a float pair in T's place)
+  for (int e = tid; e < k * k; e += nt) {
+    const int c = e / k, r = e - c * k;
+    const double Rv = (r == c ? 1.0 : 0.0) - ((double)Ah[c * ld + r] + (double)Al[c * ld + r]);
+    double Ev;
+    if (r == c) {
+      Ev = 0.5 * Rv;
+    } else {
+      const double gap = lam[c] - lam[r];
+      const double Sv = (double)Sh[c * ld + r] + (double)Sl[c * ld + r];
+      Ev = (fabs(gap) > delta) ? (Sv + lam[c] * Rv) / gap : 0.5 * Rv;
+    }
+    const float eh = (float)Ev;
+    Th[c * ld + r] = eh;
+    Tl[c * ld + r] = (float)(Ev - (double)eh);
+  }
+  for (int i = tid; i < k; i += nt) rank[i] = desc_rank(lam, k, i);
+  __syncthreads();
+  df_gemm<false, false, true>(X, nullptr, Th, Tl, Sh, Sl, k, ld);  // X E
+  __syncthreads();
+  // X <- X (I + E), columns in descending eigenvalue order
+  for (int e = tid; e < k * k; e += nt) {
+    const int c = e / k, r = e - c * k;
+    it.V[(int64_t)rank[c] * k + r] = (double)X[c * ld + r] + ((double)Sh[c * ld + r] + (double)Sl[c * ld + r]);
+  }
+  for (int c = tid; c < k; c += nt) it.lam[rank[c]] = lam[c] * scale;
 }
 
 template <typename T>
@@ -520,13 +662,21 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
     count_launch();
     return cudaGetLastError();
   }
-  // FP32 QL, then one FP64 refinement step
+  // FP32 QL, then one refinement step (double-float for k <= kDfMaxK, else FP64)
   const size_t smem = ql_smem<float>(max_k);
   e = cudaFuncSetAttribute(eig_ql_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   eig_ql_kernel<float><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * max_k,
                                                             max_k <= kEigSmemK ? 1 : 0);
   count_launch();
+  if (max_k <= kDfMaxK) {  // double-float refinement in shared memory
+    const size_t dsm = refine_df_smem(max_k);
+    e = cudaFuncSetAttribute(refine_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    if (e != cudaSuccess) return e;
+    refine_df_kernel<<<n_items, EIG_THREADS, dsm, s>>>(d_items);
+    count_launch();
+    return cudaGetLastError();
+  }
   const size_t rsm = (max_k <= 64) ? (size_t)(4 * max_k * max_k + max_k + 32) * sizeof(double) + max_k * sizeof(int)
                                    : (size_t)(max_k + 32) * sizeof(double) + max_k * sizeof(int);
   e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
