@@ -115,13 +115,39 @@ __device__ __forceinline__ void givens(float f, float g, float &r, float &s, flo
   c = gs * ri;
 }
 
+// Leading dimension of a k x k eigenvector array in shared memory: k rounded
+// up to 32, plus 4, so that the 4 lanes of a quad reading consecutive rows of
+// 8 different columns hit 32 different banks.
+__host__ __device__ __forceinline__ int ql_ld(int k) { return ((k + 31) / 32) * 32 + 4; }
+
+// y[i] = alpha * sum_{l < L} Z[(o + i) ld + o + l] x[l] for i < L: column i of
+// the trailing block at (o, o) read down its rows, 4 lanes per output (lane
+// q takes l = q, q + 4, ...) and a 2-shuffle quad sum.  All threads call it.
+template <typename T>
+__device__ __forceinline__ void quad_colvec(const T *Z, int ld, int o, int L, const T *x, T *y, T alpha) {
+  const int q = threadIdx.x & 3;
+  for (int i0 = 0; i0 < L; i0 += (int)(blockDim.x >> 2)) {
+    const int i = i0 + (int)(threadIdx.x >> 2);
+    T acc = T(0);
+    if (i < L) {
+      const T *col = Z + (int64_t)(o + i) * ld + o;
+      for (int l = q; l < L; l += 4) acc += col[l] * x[l];
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (q == 0 && i < L) y[i] = alpha * acc;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__restrict__ items, void *scratch,
                                                              int64_t scratch_stride, int z_in_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EigItem it = items[blockIdx.x];
   const int k = it.k, tid = threadIdx.x, nt = blockDim.x;
-  // layout: [32 doubles][Z: k*k T, when the launch's largest k fits][6k + 32 T][k ints];
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int ld = ql_ld(k);
+  // layout: [32 doubles][Z: k x ld T, when the launch's largest k fits][8k + 32 T][k ints];
   // the FP64 scratch comes first so that it stays 8-byte aligned for any k.
   // z_in_smem is decided per launch (from its largest k), since the dynamic
   // shared memory is sized for the launch, not for the item.
@@ -130,73 +156,96 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
   T *tail;
   if (z_in_smem) {
     Z = reinterpret_cast<T *>(redd + 32);
-    tail = Z + (int64_t)k * k;
+    tail = Z + (int64_t)k * ld;
   } else {
     Z = static_cast<T *>(scratch) + (int64_t)blockIdx.x * scratch_stride;
     tail = reinterpret_cast<T *>(redd + 32);
   }
-  T *dg = tail;
-  T *eo = dg + k;
+  T *dg = tail;    // diagonal of the tridiagonal matrix, then eigenvalues
+  T *eo = dg + k;  // off-diagonal
   T *tau = eo + k;
-  T *pv = tau + k;
+  T *vv = tau + k;   // Householder vectors (vv[0] = 1) of the even steps
+  T *vv2 = vv + k;   // and of the odd steps
+  T *pv = vv2 + k;   // p of the current step
   T *rc = pv + k;
   T *rs = rc + k;
   T *red = rs + k;
   int *perm = reinterpret_cast<int *>(red + 32);
   __shared__ EigShared sh;
-  const int ld = k;
-  // scale to max |G| = 1 (symmetrised)
+  // scale to max |G| = 1 and symmetrise: coalesced copy, then the
+  // symmetrisation inside shared memory
   double mx = 0.0;
   for (int e = tid; e < k * k; e += nt) mx = fmax(mx, fabs(it.G[e]));
   mx = block_max_d(mx, redd);
   const double scale = (mx > 0.0) ? mx : 1.0;
   const double inv_scale = 1.0 / scale;
-  for (int e = tid; e < k * k; e += nt) {
-    int c = e / k, r = e - c * k;
-    Z[e] = T(0.5 * (it.G[(int64_t)c * k + r] + it.G[(int64_t)r * k + c]) * inv_scale);
-  }
+  for (int c = warp; c < k; c += nw)
+    for (int r = lane; r < k; r += 32) Z[(int64_t)c * ld + r] = T(it.G[(int64_t)c * k + r] * inv_scale);
   __syncthreads();
-  // 1. tridiagonalisation: step j annihilates Z[j+2:k, j]
-  for (int j = 0; j + 2 < k; ++j) {
+  for (int c = warp; c < k; c += nw)
+    for (int r = c + 1 + lane; r < k; r += 32) {
+      const T v = T(0.5) * (Z[(int64_t)c * ld + r] + Z[(int64_t)r * ld + c]);
+      Z[(int64_t)c * ld + r] = v;
+      Z[(int64_t)r * ld + c] = v;
+    }
+  __syncthreads();
+  // 1. tridiagonalisation: step j annihilates Z[j+2:k, j] with the reflector
+  //    I - tau v v^T (v(j+1) = 1, tail kept in Z[j+2:k, j]); the trailing
+  //    block A = Z[j+1:, j+1:] takes A - v w^T - w v^T, w = p - (tau/2)(p^T v) v, p = tau A v.
+  //    Two barriers per step: every warp forms (p^T v) itself, and warp 0,
+  //    which updates column j+1 first, forms reflector j+1 (into the other
+  //    vector buffer) while the other warps finish the update.
+  auto form = [&](int j, T *vb) {  // warp 0
+    const int o = j + 1;
     T *x = Z + (int64_t)j * ld;
     T part = T(0);
-    for (int r = j + 2 + tid; r < k; r += nt) part += x[r] * x[r];
-    const T s2 = block_sum_t(part, red);
-    const T alpha = x[j + 1];
-    T tj = T(0), beta = alpha;
+    for (int r = o + 1 + lane; r < k; r += 32) part += x[r] * x[r];
+    const T s2 = warp_sum_t(part);
+    const T alpha = x[o];
+    T tj = T(0), beta = alpha, inv_v0 = T(0);
     if (s2 != T(0)) {
       const T nrm = sqrt(alpha * alpha + s2);
       beta = (alpha <= T(0)) ? nrm : -nrm;
-      const T inv_v0 = T(1) / (alpha - beta);
+      inv_v0 = T(1) / (alpha - beta);
       tj = (beta - alpha) / beta;
-      for (int r = j + 2 + tid; r < k; r += nt) x[r] *= inv_v0;
     }
-    __syncthreads();
-    if (tid == 0) {
+    for (int r = o + 1 + lane; r < k; r += 32) {
+      const T v = x[r] * inv_v0;
+      x[r] = v;
+      vb[r - o] = v;
+    }
+    if (lane == 0) {
+      vb[0] = T(1);
       tau[j] = tj;
       dg[j] = x[j];
       eo[j] = beta;
     }
-    if (tj != T(0)) {
-      const int L = k - j - 1;
-      for (int rr = tid; rr < L; rr += nt) {
-        const int r = j + 1 + rr;
-        T s = Z[(int64_t)(j + 1) * ld + r];
-        for (int cc = 1; cc < L; ++cc) s += Z[(int64_t)(j + 1 + cc) * ld + r] * x[j + 1 + cc];
-        pv[rr] = tj * s;
-      }
+  };
+  if (warp == 0 && k >= 3) form(0, vv);
+  __syncthreads();
+  for (int j = 0; j + 2 < k; ++j) {
+    const int o = j + 1, L = k - o;
+    const T *vc = (j & 1) ? vv2 : vv;
+    T *vn = (j & 1) ? vv : vv2;
+    const bool next = (j + 3 < k);
+    const T tj = tau[j];
+    if (tj != T(0)) {  // uniform: every thread read the same tau
+      quad_colvec(Z, ld, o, L, vc, pv, tj);  // p = tau A v (A symmetric)
       __syncthreads();
-      T pp = T(0);
-      for (int rr = tid; rr < L; rr += nt) pp += pv[rr] * (rr == 0 ? T(1) : x[j + 1 + rr]);
-      const T kk = T(0.5) * tj * block_sum_t(pp, red);
-      for (int rr = tid; rr < L; rr += nt) pv[rr] -= kk * (rr == 0 ? T(1) : x[j + 1 + rr]);
-      __syncthreads();
-      for (int e = tid; e < L * L; e += nt) {
-        const int cc = e / L, rr = e - cc * L;
-        const T vr = (rr == 0) ? T(1) : x[j + 1 + rr];
-        const T vc = (cc == 0) ? T(1) : x[j + 1 + cc];
-        Z[(int64_t)(j + 1 + cc) * ld + (j + 1 + rr)] -= vr * pv[cc] + pv[rr] * vc;
+      T part = T(0);
+      for (int r = lane; r < L; r += 32) part += pv[r] * vc[r];
+      const T kk = T(0.5) * tj * warp_sum_t(part);  // the same value in every warp
+      for (int c = warp; c < L; c += nw) {
+        T *col = Z + (int64_t)(o + c) * ld + o;
+        const T vcc = vc[c], wc = pv[c] - kk * vcc;
+        for (int r = lane; r < L; r += 32) col[r] -= vc[r] * wc + (pv[r] - kk * vc[r]) * vcc;
+        if (c == 0 && next) {  // warp 0: column j+1 is final, form reflector j+1
+          __syncwarp();
+          form(j + 1, vn);
+        }
       }
+    } else if (warp == 0 && next) {
+      form(j + 1, vn);  // column j+1 is unchanged
     }
     __syncthreads();
   }
@@ -209,41 +258,52 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
     eo[k - 1] = T(0);
   }
   __syncthreads();
-  // 2. explicit H = H_0 ... H_{k-3}; column j+1 carries reflector j
-  for (int j = k - 3; j >= 0; --j) {
-    for (int r = j + 2 + tid; r < k; r += nt) Z[(int64_t)(j + 1) * ld + r] = Z[(int64_t)j * ld + r];
-    __syncthreads();
-  }
-  for (int e = tid; e < k; e += nt) {
-    Z[e] = (e == 0) ? T(1) : T(0);
-    if (e > 0) Z[(int64_t)e * ld] = T(0);
-  }
+  // 2. explicit H = H_0 ... H_{k-3} in place, backwards: after step j the
+  //    columns >= j+1 hold H_j ... H_{k-3} (restricted to rows/columns >= 1);
+  //    v_j is read from column j (consumed before column j is rewritten)
+  for (int r = tid; r < k; r += nt) Z[(int64_t)(k - 1) * ld + r] = (r == k - 1) ? T(1) : T(0);
   __syncthreads();
-  for (int c = k - 1; c >= 1; --c) {
-    const int j = c - 1;
-    const T tj = (j <= k - 3) ? tau[j] : T(0);
-    const T *v = Z + (int64_t)c * ld;
+  for (int j = k - 3; j >= 0; --j) {
+    const int o = j + 1, L = k - o;
+    const T tj = tau[j];
+    const T *v = Z + (int64_t)j * ld;  // v(o) = 1, v(o+1..) = column j below o
     if (tj != T(0)) {
-      const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-      for (int cc = c + 1 + warp; cc < k; cc += nw) {
-        T *y = Z + (int64_t)cc * ld;
-        T s = T(0);
-        for (int r = c + 1 + lane; r < k; r += 32) s += v[r] * y[r];
-        s = warp_sum_t(s) + y[c];
-        s *= tj;
-        if (lane == 0) y[c] -= s;
-        for (int r = c + 1 + lane; r < k; r += 32) y[r] -= s * v[r];
+      // w_c = v^T Z[o:, c] for the columns c > o; Z[o:, c] -= tau v w_c
+      const int q = tid & 3;
+      for (int i0 = 0; i0 < L - 1; i0 += nt >> 2) {
+        const int i = i0 + (tid >> 2);
+        T acc = T(0);
+        const T *col = Z + (int64_t)(o + 1 + i) * ld + o;
+        if (i < L - 1)
+          for (int l = q; l < L; l += 4) acc += col[l] * (l == 0 ? T(1) : v[o + l]);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (q == 0 && i < L - 1) pv[i] = tj * acc;
+      }
+      __syncthreads();
+      for (int c = warp; c < L - 1; c += nw) {
+        T *col = Z + (int64_t)(o + 1 + c) * ld + o;
+        const T wc = pv[c];
+        for (int r = lane; r < L; r += 32) col[r] -= (r == 0 ? T(1) : v[o + r]) * wc;
       }
     }
     __syncthreads();
-    T *x = Z + (int64_t)c * ld;
-    for (int r = 1 + tid; r < k; r += nt) {
-      if (r < c) x[r] = T(0);
-      else if (r == c) x[r] = T(1) - tj;
-      else x[r] = -tj * x[r];
+    // column o = H_j e_o: 1 - tau at row o, -tau v below, zero above
+    T *co = Z + (int64_t)o * ld;
+    for (int r = tid; r < k; r += nt) {
+      T val;
+      if (r < o) val = T(0);
+      else if (r == o) val = T(1) - tj;
+      else val = -tj * v[r];
+      co[r] = val;
     }
     __syncthreads();
   }
+  for (int r = tid; r < k; r += nt) {
+    Z[r] = (r == 0) ? T(1) : T(0);                  // column 0 = e_0
+    if (r > 0) Z[(int64_t)r * ld] = T(0);           // row 0 of the other columns
+  }
+  __syncthreads();
   // 3. implicit QL; deflation when |e_m| <= eps ||T|| (normwise: the Gramians
   //    need eigenvalues to within eps * lambda_max only)
   if (tid == 0) {
@@ -252,79 +312,105 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
   }
   int l = 0, iter = 0;
   T tol = T(0);
-  if (tid == 0) {
+  if (warp == 0) {
     T tn = T(0);
-    for (int i = 0; i < k; ++i) {
+    for (int i = lane; i < k; i += 32) {
       T v = fabs(dg[i]) + fabs(eo[i]) + (i > 0 ? fabs(eo[i - 1]) : T(0));
       tn = tn > v ? tn : v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const T o2 = __shfl_xor_sync(0xffffffffu, tn, off);
+      tn = tn > o2 ? tn : o2;
     }
     const T eps = (sizeof(T) == 8) ? T(2.220446049250313e-16) : T(1.1920929e-7);
     tol = eps * tn;
   }
   for (;;) {
-    if (tid == 0) {
-      sh.count = 0;
-      while (l < k && sh.count == 0) {
-        int mm;
-        for (mm = l; mm < k - 1; ++mm)
-          if (fabs(eo[mm]) <= tol) break;
+    // warp 0 finds the next unreduced block (a ballot over 32 off-diagonals
+    // at a time); lane 0 runs the sweep's rotation recurrence
+    if (warp == 0) {
+      int cnt = 0;
+      while (l < k && cnt == 0) {
+        int mm = k - 1;
+        for (int base = l; base < k - 1; base += 32) {
+          const int m = base + lane;
+          const unsigned hit = __ballot_sync(0xffffffffu, m < k - 1 && fabs(eo[m]) <= tol);
+          if (hit) {
+            mm = base + __ffs(hit) - 1;
+            break;
+          }
+        }
         if (mm == l) {
           ++l;
           iter = 0;
           continue;
         }
         if (++iter > 64) {
-          sh.status = 1;
+          if (lane == 0) sh.status = 1;
           ++l;
           iter = 0;
           continue;
         }
-        // Wilkinson-type shift from the leading 2x2 block
-        T g = (dg[l + 1] - dg[l]) / (T(2) * eo[l]);
-        T r = sqrt(g * g + T(1));
-        g = dg[mm] - dg[l] + eo[l] / (g + copysign(r, g));
-        T s = T(1), c = T(1), p = T(0);
-        bool deflated = false;
-        for (int i = mm - 1; i >= l; --i) {
-          const T f = s * eo[i], b = c * eo[i];
-          givens(f, g, r, s, c);
-          eo[i + 1] = r;
-          if (r == T(0)) {
-            dg[i + 1] -= p;
-            eo[mm] = T(0);
-            deflated = true;
-            break;
+        if (lane == 0) {
+          // Wilkinson-type shift from the leading 2x2 block
+          T g = (dg[l + 1] - dg[l]) / (T(2) * eo[l]);
+          T r = sqrt(g * g + T(1));
+          g = dg[mm] - dg[l] + eo[l] / (g + copysign(r, g));
+          T s = T(1), c = T(1), p = T(0);
+          bool deflated = false;
+          T e_i = eo[mm - 1], d_i = dg[mm - 1], d_i1 = dg[mm];  // operands of step i, loaded one step ahead
+          for (int i = mm - 1; i >= l; --i) {
+            const T e_n = (i > l) ? eo[i - 1] : T(0), d_n = (i > l) ? dg[i - 1] : T(0);
+            const T f = s * e_i, b = c * e_i;
+            givens(f, g, r, s, c);
+            eo[i + 1] = r;
+            if (r == T(0)) {
+              dg[i + 1] = d_i1 - p;
+              eo[mm] = T(0);
+              deflated = true;
+              break;
+            }
+            g = d_i1 - p;
+            r = (d_i - g) * s + T(2) * c * b;
+            p = s * r;
+            dg[i + 1] = g + p;
+            g = c * r - b;
+            rc[cnt] = c;
+            rs[cnt] = s;
+            ++cnt;
+            e_i = e_n;
+            d_i1 = d_i;
+            d_i = d_n;
           }
-          g = dg[i + 1] - p;
-          r = (dg[i] - g) * s + T(2) * c * b;
-          p = s * r;
-          dg[i + 1] = g + p;
-          g = c * r - b;
-          rc[sh.count] = c;
-          rs[sh.count] = s;
-          sh.count++;
+          sh.lo = mm - 1;
+          if (!deflated) {
+            dg[l] = d_i1 - p;
+            eo[l] = g;
+            eo[mm] = T(0);
+          }
         }
-        sh.lo = mm - 1;
-        if (!deflated) {
-          dg[l] -= p;
-          eo[l] = g;
-          eo[mm] = T(0);
-        }
+        cnt = __shfl_sync(0xffffffffu, cnt, 0);
+        __syncwarp();  // lane 0's updates of eo / dg before the next scan
       }
-      if (l >= k && sh.count == 0) sh.done = 1;
+      if (lane == 0) {
+        sh.count = cnt;
+        sh.done = (l >= k && cnt == 0) ? 1 : 0;
+      }
     }
     __syncthreads();
     if (sh.done) break;
     const int cnt = sh.count, i0 = sh.lo;
     for (int row = tid; row < k; row += nt) {
+      T zi1 = Z[(int64_t)(i0 + 1) * ld + row];
       for (int q = 0; q < cnt; ++q) {
         const int i = i0 - q;
-        T *zi = Z + (int64_t)i * ld + row;
-        T *zi1 = Z + (int64_t)(i + 1) * ld + row;
-        const T f = *zi1;
-        *zi1 = rs[q] * (*zi) + rc[q] * f;
-        *zi = rc[q] * (*zi) - rs[q] * f;
+        T *zp = Z + (int64_t)i * ld + row;
+        const T zi = *zp;
+        Z[(int64_t)(i + 1) * ld + row] = rs[q] * zi + rc[q] * zi1;
+        zi1 = rc[q] * zi - rs[q] * zi1;
       }
+      Z[(int64_t)(i0 + 1 - cnt) * ld + row] = zi1;
     }
     __syncthreads();
   }
@@ -592,8 +678,8 @@ __global__ void __launch_bounds__(EIG_THREADS) refine_df_kernel(const EigItem *_
 
 template <typename T>
 size_t ql_smem(int max_k) {
-  size_t tail = 32 * sizeof(double) + (size_t)(6 * max_k + 32) * sizeof(T) + (size_t)max_k * sizeof(int);
-  return (max_k <= kEigSmemK) ? (size_t)max_k * max_k * sizeof(T) + tail : tail;
+  size_t tail = 32 * sizeof(double) + (size_t)(8 * max_k + 32) * sizeof(T) + (size_t)max_k * sizeof(int);
+  return (max_k <= kEigSmemK) ? (size_t)max_k * ql_ld(max_k) * sizeof(T) + tail : tail;
 }
 
 // ---- semidefinite Cholesky (square-root Gramian factors) --------------------
@@ -657,7 +743,7 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
     const size_t smem = ql_smem<double>(max_k);
     e = cudaFuncSetAttribute(eig_ql_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    eig_ql_kernel<double><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * max_k,
+    eig_ql_kernel<double><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * ql_ld(max_k),
                                                              max_k <= kEigSmemK ? 1 : 0);
     count_launch();
     return cudaGetLastError();
@@ -666,7 +752,7 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
   const size_t smem = ql_smem<float>(max_k);
   e = cudaFuncSetAttribute(eig_ql_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  eig_ql_kernel<float><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * max_k,
+  eig_ql_kernel<float><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * ql_ld(max_k),
                                                             max_k <= kEigSmemK ? 1 : 0);
   count_launch();
   if (max_k <= kDfMaxK) {  // double-float refinement in shared memory
