@@ -520,6 +520,14 @@ const GemmTune &gemm_tune() {
   return t;
 }
 
+// Split-K factor of a launch with `tiles` output tiles: as many chunks as
+// keep every CTA of the launch resident in one round of two CTAs per SM
+// (rounded down: a second, nearly empty round would double the time).
+inline int split_for(int tiles, int ko) {
+  const int ks = (2 * kSmCount) / std::max(tiles, 1);
+  return std::max(1, std::min(ko, ks));
+}
+
 // SIMT tile shape of a GEMM launch, and the items' tile grid for it.  Items
 // with M >= tall_m are "tall", those also with N >= tall_m "square"; the
 // shares of the launch's flops in them pick 128 x 128 (uncompensated
@@ -844,7 +852,7 @@ void plan_tsqr_panels(Plan &P, const std::vector<Mat> &mats) {
           g.K = kChunk;
           g.Ko = ko;
           g.k_total = M.m;
-          g.ksplit = std::max(1, std::min(ko, (2 * kSmCount + tiles - 1) / std::max(tiles, 1)));
+          g.ksplit = split_for(tiles, ko);
           P.gemm(g, M.node);
         }
         // A_p -= Q_<p C
@@ -1327,7 +1335,7 @@ void plan_gramians_sqrt(Plan &P, std::vector<TState> &TS, const std::vector<doub
       P.gemm(g, J.S->node_base + J.t);
     }
     // Ghat_s1 = sum_{a,l} Y[a,p,l] Y[a,q,l], Ghat_s2 = sum_{a,j} Y[a,j,l] Y[a,j,l'] (double-float, FP64 out)
-    const int ksplit = std::max(1, (2 * kSmCount + tiles - 1) / std::max(tiles, 1));
+    const int ksplit = split_for(tiles, 1 << 30);
     P.begin(L_GEMM);
     P.cur().df = true;
     for (Job &J : jobs) {
@@ -1479,7 +1487,7 @@ void plan_gramians(Plan &P, std::vector<TState> &TS, const std::vector<double *>
     }
     // eqs. "acctransferSon1" and "acctransferSon2"; the reduction over the
     // parent index i is split across CTAs when the level has few nodes
-    int ksplit = std::max(1, (2 * kSmCount + tiles - 1) / std::max(tiles, 1));
+    int ksplit = split_for(tiles, 1 << 30);
     P.begin(L_GEMM);
     for (Job &J : jobs) {
       const ht_tree &T = J.S->x->tr;
@@ -1819,9 +1827,6 @@ void *plan_inner(Plan &P, const ht_tensor *x, const ht_tensor *y) {
     phi[t] = P.palloc_bytes((size_t)kx * ky * esz);
   }
   constexpr int kChunk = 256;
-  auto split_for = [&](int ko, int tiles_total) {
-    return std::max(1, std::min(ko, (2 * kSmCount + tiles_total - 1) / std::max(tiles_total, 1)));
-  };
   for (int h = 0; h <= T.max_height; ++h) {
     P.sreset();
     if (h == 0) {
@@ -1849,7 +1854,7 @@ void *plan_inner(Plan &P, const ht_tensor *x, const ht_tensor *y) {
         g.K = (int)std::min<int64_t>(n, kChunk);
         g.Ko = (int)((n + kChunk - 1) / kChunk);
         g.k_total = n;
-        g.ksplit = split_for(g.Ko, tiles);
+        g.ksplit = split_for(tiles, g.Ko);
         P.gemm(g, t);
       }
       continue;
@@ -1935,7 +1940,7 @@ void *plan_inner(Plan &P, const ht_tensor *x, const ht_tensor *y) {
       g.K = (int)std::min<int64_t>(red, kChunk);
       g.Ko = (int)((red + kChunk - 1) / kChunk);
       g.k_total = red;
-      g.ksplit = split_for(g.Ko, tiles);
+      g.ksplit = split_for(tiles, g.Ko);
       P.gemm(g, J.t);
     }
   }

@@ -20,19 +20,18 @@ constexpr int kRegRows = 256;  // rows of a register-resident block (32 x NI)
 // products reduce over the 8 lanes of its group (3 shuffles) and shared
 // vectors are read four rows at a time.
 //
-// Column j's reflector is kept in the scaled form H_j = I - tau_j v_j v_j^T
-// with v_j(j) = 1, v_j zero above row j and scl_j times the column below it
-// (|v_j| <= 1 entrywise, tau_j in [1, 2]).  The warp owning column j forms
-// ||.||^2 below the diagonal, beta_j = R(j, j), tau_j and scl_j from its
-// registers and stores v_j and tau_j in shared memory; after one barrier
-// every warp holding a column right of j applies H_j with one dot product
-// (one 8-lane sum) and one axpy: a -= tau_j (v_j^T a) v_j.  Row j needs no
-// special case, since v_j(j) = 1.  The owner of column j+1 forms the next
-// reflector right after its own update.  One barrier per column.
+// Column j's reflector is kept as H_j = I - kappa_j y_j y_j^T, y_j zero above
+// row j, y_j(j) = alpha_j - beta_j and the column itself below j (stored
+// before the scalars are known; kappa_j from one division).  The warp owning
+// column j forms ||.||^2 below the diagonal, beta_j = R(j, j) and kappa_j
+// from its registers and stores y_j and kappa_j in shared memory; after one
+// barrier every warp holding a column right of j applies H_j with one dot
+// product (one 8-lane sum) and one axpy: a -= kappa_j (y_j^T a) y_j.  Row j
+// needs no special case.  The owner of column j+1 forms the next reflector
+// right after its own update.  One barrier per column.
 //
-// The v_j stay in shared memory, so Q = H_0 ... H_{n-1} [I; 0] is then
-// accumulated backwards on the columns in registers without barriers, the
-// reflector of the next step loaded while the current one is applied.
+// The y_j stay in shared memory, so Q = H_0 ... H_{n-1} [I; 0] is then
+// accumulated backwards on the columns in registers without barriers.
 // ---------------------------------------------------------------------------
 constexpr int REG_MR = kRegRows;  // leading dimension of the reflector array (rows)
 
@@ -72,65 +71,63 @@ __device__ __forceinline__ T row_value(const T (&a)[NI][4], int j, int lane) {
   return __shfl_sync(0xffffffffu, (j >> 5) ? z : y, (lane & ~7) | ((j >> 2) & 7));
 }
 
-// Householder scalars of a column with diagonal entry alpha and squared norm
-// s2 below it: beta = R(j, j) = -sign(alpha) sqrt(alpha^2 + s2), tau = (beta
-// - alpha) / beta and scl = 1 / (alpha - beta), with IEEE square root and
-// divisions (reciprocal-square-root forms cost FP32 about twice the
-// orthogonality error on ||X||); the identity (tau = 0, scl = 0, beta =
-// alpha) when s2 = 0.
-template <typename T>
-__device__ __forceinline__ void reflector_scalars(T alpha, T s2, T &tj, T &sc, T &beta) {
-  tj = T(0), sc = T(0), beta = alpha;
-  if (s2 != T(0)) {
-    const T nrm = sqrt(alpha * alpha + s2);
-    beta = (alpha <= T(0)) ? nrm : -nrm;
-    tj = (beta - alpha) / beta;
-    sc = T(1) / (alpha - beta);
-  }
-}
+// Smallest alpha^2 + ||w||^2 for which the reflector is formed (4 x the
+// smallest normal number): below it the column is treated as zero (identity
+// reflector), which also keeps kappa below 1 / (4 x the smallest normal).
+__device__ __forceinline__ float min_norm2(float) { return 4.0f * 1.17549435e-38f; }
+__device__ __forceinline__ double min_norm2(double) { return 4.0 * 2.2250738585072014e-308; }
 
 // Form column j's reflector from the lane's registers (called by the whole
-// warp that owns column j, after H_0..H_{j-1} reached it): the owner group
-// stores v_j into vj and tau_j, and its lanes set R(j, j) = beta_j in their
-// registers (rows below j become free: they are held in vj).
+// warp that owns column j, after H_0..H_{j-1} reached it).  With alpha the
+// diagonal entry and w the part below it, beta = R(j, j) = -sign(alpha)
+// sqrt(alpha^2 + ||w||^2) and u = alpha - beta, the reflector is
+// H_j = I - kappa y y^T with y = [0; u; w] and kappa = -1 / (beta u)
+// (kappa ||y||^2 = 2).  The owner group stores w before the scalars are known
+// (one division, sqrt and IEEE division), then u and kappa; its lanes set
+// R(j, j) = beta in their registers (rows below j are held in y).
 template <typename T, int NI>
-__device__ __forceinline__ void form_reflector(T (&a)[NI][4], T *vj, T *tau_j, int j, int lane, bool me) {
+__device__ __forceinline__ void form_reflector(T (&a)[NI][4], T *yj, T *kappa_j, int j, int lane, bool me) {
   const int s = lane & 7;
   T q0 = T(0), q1 = T(0), q2 = T(0), q3 = T(0);
-#pragma unroll
-  for (int i = 0; i < NI; ++i) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int r = 32 * i + 4 * s + e;
-      const T x = (i >= 2 || r > j) ? a[i][e] : T(0);  // j < 64: rows of chunks i >= 2 lie below j
-      if (e == 0) q0 += x * x;
-      if (e == 1) q1 += x * x;
-      if (e == 2) q2 += x * x;
-      if (e == 3) q3 += x * x;
-    }
-  }
-  const T s2 = group_sum((q0 + q1) + (q2 + q3));
-  const T alpha = row_value<T, NI>(a, j, lane);
-  T tj, sc, beta;
-  reflector_scalars(alpha, s2, tj, sc, beta);
-  if (!me) return;
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     T x[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int r = 32 * i + 4 * s + e;
-      x[e] = (i >= 2 || r > j) ? sc * a[i][e] : (r == j ? T(1) : T(0));
-      if (i < 2 && r == j) a[i][e] = beta;
+      x[e] = (i >= 2 || r > j) ? a[i][e] : T(0);  // j < 64: rows of chunks i >= 2 lie below j
     }
-    st4(vj + 32 * i + 4 * s, x);
+    q0 += x[0] * x[0];
+    q1 += x[1] * x[1];
+    q2 += x[2] * x[2];
+    q3 += x[3] * x[3];
+    if (me) st4(yj + 32 * i + 4 * s, x);
   }
-  if (s == 0) *tau_j = tj;
+  const T s2 = group_sum((q0 + q1) + (q2 + q3));
+  const T alpha = row_value<T, NI>(a, j, lane);
+  T kappa = T(0), beta = alpha, u = T(0);
+  const T x2 = alpha * alpha + s2;
+  if (s2 != T(0) && x2 >= min_norm2(T(0))) {
+    const T nrm = sqrt(x2);
+    beta = (alpha <= T(0)) ? nrm : -nrm;
+    u = alpha - beta;
+    kappa = T(-1) / (beta * u);
+  }
+  if (!me) return;
+#pragma unroll
+  for (int i = 0; i < 2 && i < NI; ++i)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (32 * i + 4 * s + e == j) {
+        yj[j] = u;
+        a[i][e] = beta;
+      }
+  if (s == 0) *kappa_j = kappa;
 }
 
-// a <- a - tau (v^T a) v for the lane's column (v in shared memory; x holds
-// it on return when kKeep).  upd = false leaves a unchanged (the reduction
-// spans the warp, so every lane takes part).
+// a <- a - kappa (y^T a) y for the lane's column (y in shared memory).
+// upd = false leaves a unchanged (the reduction spans the warp, so every
+// lane takes part).  kKeep keeps y in registers between the two passes.
 template <typename T, int NI, bool kKeep>
 __device__ __forceinline__ void apply_reflector(T (&a)[NI][4], const T *vj, T tj, bool upd, int s) {
   T v[kKeep ? NI : 1][4];
@@ -169,8 +166,8 @@ __global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restric
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const QrItem it = items[blockIdx.x];
   const int m = it.m, n = it.n;
-  T *V = reinterpret_cast<T *>(smem_raw);  // REG_MR x n: v_j in column j
-  T *tau = V + (int64_t)REG_MR * n;        // n
+  T *V = reinterpret_cast<T *>(smem_raw);  // REG_MR x n: y_j in column j
+  T *tau = V + (int64_t)REG_MR * n;        // n: kappa_j
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 3, s = lane & 7;
   const int c = 4 * warp + g;  // this lane's column
@@ -185,7 +182,7 @@ __global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restric
     }
   if (warp == 0) form_reflector<T, NI>(a, V, tau, 0, lane, g == 0);
   for (int j = 0; j + 1 < n; ++j) {
-    __syncthreads();                  // v_j and tau_j are in shared memory
+    __syncthreads();                  // y_j and kappa_j are in shared memory
     if (4 * warp + 3 <= j) continue;  // no column of this warp lies right of j
     const T *vj = V + (int64_t)j * REG_MR;
     apply_reflector<T, NI, KEEP>(a, vj, tau[j], c > j, s);
