@@ -408,7 +408,7 @@ def main():
         per_launch_flops = rec["flops"] / rec["launches"]
         ach = per_launch_flops / (per_launch_ms / 1e3)
         kernel = {"qr": "qr_reg_kernel (FP32 TSQR blocks)", "gemm": "gemm_kernel (FP32 SIMT, compensated)",
-                  "eig": "eig_ql_kernel<float> + refine_kernel (FP64)"}.get(name, name)
+                  "eig": "eig_ql_kernel<float> + refine_df_kernel (double-float)"}.get(name, name)
         peak = FP64_PEAK if name == "eig" else FP32_PEAK
         roofline = {"kernel": kernel, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
                     "unit": "TFLOP/s", "frac": ach / peak,

@@ -57,8 +57,8 @@ typedef enum { HT_F64 = 0, HT_F32 = 1 } ht_dtype;
 /* Arithmetic of the truncation.  HT_PREC_FP64: every step in FP64 (F64
  * tensors).  HT_PREC_FP32: storage and dense contractions in FP32, the small
  * k x k Gramian eigendecompositions solved in FP32 and refined to FP64-level
- * accuracy (one Ogita-Aishima step; its products in double-float, about
- * 48 bits, for k <= 64, in FP64 beyond) (F32 tensors).
+ * accuracy (one Ogita-Aishima step with double-float products, about 48
+ * bits) (F32 tensors).
  * HT_PREC_FP32_SQRT: as HT_PREC_FP32, but the reduced Gramians of Sec. 3.3
  * are carried as square-root factors Ghat_t = S_t S_t^T (top-down: the sons'
  * Gramians are Gram products of B_t contracted with S_t, accumulated exactly

@@ -130,7 +130,7 @@ void gemm_tile_shape(int variant, int *bm, int *bn);
 cudaError_t launch_gemm_tc(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, cudaStream_t s);
 template <typename T>
 cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s);
-// mode 0: FP64 QL; mode 1: FP32 QL followed by one FP64 refinement step.
+// mode 0: FP64 QL; mode 1: FP32 QL followed by one double-float refinement step.
 // scratch: 4 * max_k^2 doubles per item when max_k exceeds the shared-memory sizes (eig_scratch_needed).
 cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s, int mode);
 cudaError_t launch_copy(const CopyItem *d_items, int n_items, const int *d_ranks, int f64_any, cudaStream_t s);

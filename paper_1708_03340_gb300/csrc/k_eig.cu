@@ -10,7 +10,7 @@
 // ~64 cycles and an FP64 divide or square root ~430-670 cycles, so the
 // recurrence uses one reciprocal square root per rotation and no divides.
 //
-// refine_kernel: one step of the Ogita-Aishima iterative refinement
+// refine_df_kernel: one step of the Ogita-Aishima iterative refinement
 // (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue
 // decomposition", Japan J. Indust. Appl. Math. 35, 2018), written from its
 // first-order conditions: with X the current eigenvectors, R = I - X^T X,
@@ -18,8 +18,8 @@
 // E + E^T = R, (S + E^T S + S E) diagonal to first order:
 //   E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)   if |lambda_i - lambda_j| > delta
 //   E_ij = R_ij / 2                                           otherwise (cluster)
-// X <- X (I + E).  Used in FP64 after an FP32 QL solve: the dense products
-// keep every warp's FP64 pipe busy instead of a one-lane scalar chain.
+// X <- X (I + E).  Used after an FP32 QL solve, with its dense products in
+// double-float on the FP32 pipes (see the kernel).
 #include "internal.h"
 
 namespace htgb {
@@ -424,110 +424,7 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
   for (int c = tid; c < k; c += nt) it.lam[c] = (double)dg[perm[c]] * scale;
 }
 
-// ---- FP64 refinement ---------------------------------------------------------
-// C = op(A) * B for k x k column-major matrices in shared or global memory;
-// transA: C[i][j] = sum_l A[l][i] B[l][j].  Each thread computes 4x4 outputs.
-__device__ void small_gemm(const double *A, const double *B, double *C, int k, bool transA) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int tiles = (k + 3) / 4;
-  for (int t = tid; t < tiles * tiles; t += nt) {
-    const int ti = (t % tiles) * 4, tj = (t / tiles) * 4;
-    double acc[4][4] = {};
-    for (int l = 0; l < k; ++l) {
-      double a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = ti + u, j = tj + u;
-        a[u] = (i < k) ? (transA ? A[(int64_t)i * k + l] : A[(int64_t)l * k + i]) : 0.0;
-        b[u] = (j < k) ? B[(int64_t)j * k + l] : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (ti + u < k && tj + v < k) C[(int64_t)(tj + v) * k + ti + u] = acc[u][v];
-  }
-}
-
-__global__ void __launch_bounds__(EIG_THREADS) refine_kernel(const EigItem *__restrict__ items, double *scratch,
-                                                             int64_t scratch_stride, int buf_in_smem) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const EigItem it = items[blockIdx.x];
-  const int k = it.k, tid = threadIdx.x, nt = blockDim.x;
-  const int64_t kk = (int64_t)k * k;
-  // buf_in_smem: decided per launch from its largest k (the shared memory is sized for the launch)
-  double *buf = buf_in_smem ? reinterpret_cast<double *>(smem_raw) : scratch + (int64_t)blockIdx.x * scratch_stride;
-  double *A = buf, *X = buf + kk, *W1 = buf + 2 * kk, *W2 = buf + 3 * kk;
-  double *small = buf_in_smem ? buf + 4 * kk : reinterpret_cast<double *>(smem_raw);
-  double *lam = small;          // k
-  double *red = small + k;      // 32
-  int *perm = reinterpret_cast<int *>(red + 32);
-  double mx = 0.0;
-  for (int e = tid; e < kk; e += nt) mx = fmax(mx, fabs(it.G[e]));
-  mx = block_max_d(mx, red);
-  const double scale = (mx > 0.0) ? mx : 1.0, inv_scale = 1.0 / scale;
-  for (int e = tid; e < kk; e += nt) {
-    const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
-    A[e] = 0.5 * (it.G[(int64_t)c * k + r] + it.G[(int64_t)r * k + c]) * inv_scale;
-    X[e] = it.V[e];
-  }
-  __syncthreads();
-  small_gemm(A, X, W1, k, false);  // W1 = A X
-  __syncthreads();
-  small_gemm(X, W1, W2, k, true);  // W2 = S = X^T A X
-  __syncthreads();
-  small_gemm(X, X, W1, k, true);   // W1 = X^T X
-  __syncthreads();
-  for (int e = tid; e < kk; e += nt) {
-    const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
-    W1[e] = ((r == c) ? 1.0 : 0.0) - W1[e];  // R = I - X^T X
-  }
-  __syncthreads();
-  for (int i = tid; i < k; i += nt) lam[i] = W2[(int64_t)i * k + i] / (1.0 - W1[(int64_t)i * k + i]);
-  // cluster threshold from the sizes of the first-order residuals
-  double so = 0.0, ro = 0.0, lm = 0.0;
-  for (int e = tid; e < kk; e += nt) {
-    const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
-    if (r != c) so = fmax(so, fabs(W2[e]));
-    ro = fmax(ro, fabs(W1[e]));
-  }
-  __syncthreads();
-  for (int i = tid; i < k; i += nt) lm = fmax(lm, fabs(lam[i]));
-  so = block_max_d(so, red);
-  ro = block_max_d(ro, red);
-  lm = block_max_d(lm, red);
-  const double delta = 2.0 * (so + lm * ro) * (double)k;
-  for (int e = tid; e < kk; e += nt) {
-    const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
-    const double Rv = W1[e];
-    double Ev;
-    if (r == c) {
-      Ev = 0.5 * Rv;
-    } else {
-      const double gap = lam[c] - lam[r];
-      Ev = (fabs(gap) > delta) ? (W2[e] + lam[c] * Rv) / gap : 0.5 * Rv;
-    }
-    W2[e] = Ev;
-  }
-  __syncthreads();
-  small_gemm(X, W2, W1, k, false);  // W1 = X E
-  __syncthreads();
-  for (int e = tid; e < kk; e += nt) W1[e] += X[e];
-  for (int i = tid; i < k; i += nt) perm[desc_rank(lam, k, i)] = i;
-  __syncthreads();
-  for (int e = tid; e < kk; e += nt) {
-    const int c = (int)(e / k), r = (int)(e - (int64_t)c * k);
-    it.V[e] = W1[(int64_t)perm[c] * k + r];
-  }
-  for (int c = tid; c < k; c += nt) it.lam[c] = lam[perm[c]] * scale;
-}
-
-// ---- double-float refinement (k <= kDfMaxK) ---------------------------------
+// ---- double-float refinement --------------------------------------------------
 // The same Ogita-Aishima step with its four k x k products on the FP32 pipes:
 // every product of FP32 operands is carried exactly as a pair (p, e) with p =
 // a b rounded and e = fma(a, b, -p), and summed into a double-float (hi, lo)
@@ -597,20 +494,26 @@ __device__ void df_gemm(const float *Ah, const float *Al, const float *Bh, const
   }
 }
 
-size_t refine_df_smem(int max_k) {
-  return (size_t)(kDfMaxK + 32) * sizeof(double) + (size_t)kDfMaxK * sizeof(int) +
-         7 * (size_t)max_k * (max_k + 1) * sizeof(float);
+// Shared memory of the refinement: lambda (max_k doubles), 32 doubles, the
+// ranks (max_k ints), and the seven k x (k+1) float arrays when they fit
+// (max_k <= kDfMaxK); larger Gramians keep the arrays in a global scratch
+// slab per item (L2-resident).
+__host__ __device__ size_t refine_df_smem(int max_k, bool arrays) {
+  const size_t base = (size_t)(max_k + 32) * sizeof(double) + (((size_t)max_k * sizeof(int) + 15) & ~size_t(15));
+  return base + (arrays ? 7 * (size_t)max_k * (max_k + 1) * sizeof(float) : 0);
 }
 
-__global__ void __launch_bounds__(EIG_THREADS) refine_df_kernel(const EigItem *__restrict__ items) {
+__global__ void __launch_bounds__(EIG_THREADS) refine_df_kernel(const EigItem *__restrict__ items, double *scratch,
+                                                                int64_t scratch_stride, int max_k, int in_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EigItem it = items[blockIdx.x];
   const int k = it.k, tid = threadIdx.x, nt = blockDim.x, ld = k + 1;  // odd ld: 2-way bank conflicts at most
   const int sz = k * ld;
   double *lam = reinterpret_cast<double *>(smem_raw);  // k
-  double *red = lam + kDfMaxK;                          // 32
+  double *red = lam + max_k;                            // 32
   int *rank = reinterpret_cast<int *>(red + 32);        // k
-  float *Ah = reinterpret_cast<float *>(rank + kDfMaxK);
+  float *Ah = in_smem ? reinterpret_cast<float *>(smem_raw + refine_df_smem(max_k, false))
+                      : reinterpret_cast<float *>(scratch + (int64_t)blockIdx.x * scratch_stride);
   float *Al = Ah + sz, *X = Al + sz, *Th = X + sz, *Tl = Th + sz, *Sh = Tl + sz, *Sl = Sh + sz;
   double mx = 0.0;
   for (int e = tid; e < k * k; e += nt) mx = fmax(mx, fabs(it.G[e]));
@@ -748,26 +651,20 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
     count_launch();
     return cudaGetLastError();
   }
-  // FP32 QL, then one refinement step (double-float for k <= kDfMaxK, else FP64)
+  // FP32 QL, then one double-float refinement step
   const size_t smem = ql_smem<float>(max_k);
   e = cudaFuncSetAttribute(eig_ql_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   eig_ql_kernel<float><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * ql_ld(max_k),
                                                             max_k <= kEigSmemK ? 1 : 0);
   count_launch();
-  if (max_k <= kDfMaxK) {  // double-float refinement in shared memory
-    const size_t dsm = refine_df_smem(max_k);
-    e = cudaFuncSetAttribute(refine_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-    if (e != cudaSuccess) return e;
-    refine_df_kernel<<<n_items, EIG_THREADS, dsm, s>>>(d_items);
-    count_launch();
-    return cudaGetLastError();
-  }
-  const size_t rsm = (max_k <= 64) ? (size_t)(4 * max_k * max_k + max_k + 32) * sizeof(double) + max_k * sizeof(int)
-                                   : (size_t)(max_k + 32) * sizeof(double) + max_k * sizeof(int);
-  e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+  const bool in_smem = max_k <= kDfMaxK;  // else the arrays use the scratch slab (4 max_k^2 doubles per item)
+  if (!in_smem && !scratch) return cudaErrorInvalidValue;
+  const size_t dsm = refine_df_smem(max_k, in_smem);
+  e = cudaFuncSetAttribute(refine_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
   if (e != cudaSuccess) return e;
-  refine_kernel<<<n_items, EIG_THREADS, rsm, s>>>(d_items, scratch, 4 * (int64_t)max_k * max_k, max_k <= 64 ? 1 : 0);
+  refine_df_kernel<<<n_items, EIG_THREADS, dsm, s>>>(d_items, scratch, 4 * (int64_t)max_k * max_k, max_k,
+                                                     in_smem ? 1 : 0);
   count_launch();
   return cudaGetLastError();
 }
