@@ -45,7 +45,6 @@ sys.path.insert(0, ROOT)
 from paper_1708_03340_gb300 import inputs as I  # noqa: E402
 
 METRIC = "HT truncations/s + roofline fraction, mixed vs plain FP64 GPU at stated rel err"
-FP64_PEAK = 152 * 2 * 2 * 2.070e9   # SMs x FP64 FMA/clk/SM x 2 flop x max clock (recipe: 1.25 TFLOP/s)
 FP32_PEAK = 152 * 128 * 2 * 2.070e9  # SMs x FP32 lanes x 2 flop x max clock (80.5 TFLOP/s)
 
 
@@ -103,8 +102,9 @@ WORKLOADS = {
 
 # DRAM bytes (read + write) per launch of the dominant kernel family, averaged
 # over one step's launches of that family, from one ncu capture of the current
-# kernels (profiles/gemm_kernel_single_d64_fp32.md); None where not captured.
-TRAFFIC_PER_LAUNCH = {("single", "gemm"): 15.52e6}
+# kernels (profiles/gemm_kernel_single_d64_fp32.md, profiles/qr_reg_kernel_single_d64_fp32.md);
+# None where not captured.
+TRAFFIC_PER_LAUNCH = {("single", "gemm"): 15.62e6, ("single", "qr"): 6.29e6}
 
 
 def model_flops(d, n, K, r):
@@ -409,11 +409,11 @@ def main():
         ach = per_launch_flops / (per_launch_ms / 1e3)
         kernel = {"qr": "qr_reg_kernel (FP32 TSQR blocks)", "gemm": "gemm_kernel (FP32 SIMT, compensated)",
                   "eig": "eig_ql_kernel<float> + refine_df_kernel (double-float)"}.get(name, name)
-        peak = FP64_PEAK if name == "eig" else FP32_PEAK
+        peak = FP32_PEAK  # every family of the FP32 path runs on the FP32 pipes (the refinement in double-float)
         roofline = {"kernel": kernel, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
                     "unit": "TFLOP/s", "frac": ach / peak,
                     "traffic": TRAFFIC_PER_LAUNCH.get((args.config, name)),
-                    "peak_source": ("FP64" if name == "eig" else "FP32") + " unit count x max SM clock (recipe)",
+                    "peak_source": "FP32 unit count x max SM clock (recipe)",
                     "launches_per_step": rec["launches"] / psteps, "ms_per_launch": per_launch_ms,
                     "flops_per_launch": per_launch_flops}
 
