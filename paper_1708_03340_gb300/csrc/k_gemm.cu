@@ -62,6 +62,12 @@ __device__ __forceinline__ void cp_async_elem(T *dst_smem, const T *src, bool va
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
+// 16-byte asynchronous copy with zero-fill beyond `bytes` (0..16); src is a
+// 16-byte aligned address inside the operand even when bytes == 0.
+__device__ __forceinline__ void cp_async_16(void *dst_smem, const void *src, int bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -125,28 +131,54 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) != 4 ? 1
   auto col_of = [&](int j) { return (j >> 2) * (4 * (BN / TN)) + 4 * ty + (j & 3); };
   const bool a_mfast = (it.sam == 1);
   const bool b_nfast = (it.sbn == 1) && (it.sbk != 1);
+  // FP32 operands whose fast dimension is the tile's (A along m, B along n)
+  // and whose every 4-element chunk starts 16-byte aligned are copied 16 bytes
+  // at a time (chunks cut by M or N are zero-filled past the edge)
+  constexpr int LAV = (BM * BK) / (4 * THREADS), LBV = (BN * BK) / (4 * THREADS);
+  const bool vecA = sizeof(T) == 4 && LAV >= 1 && a_mfast && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
+                    (it.sak & 3) == 0 && (it.sako & 3) == 0;
+  const bool vecB = sizeof(T) == 4 && LBV >= 1 && b_nfast && (reinterpret_cast<uintptr_t>(B) & 15) == 0 &&
+                    (it.sbk & 3) == 0 && (it.sbko & 3) == 0;
 
   // Per copied element of this thread: its place in the tile and its global
   // offset without the k tile (fixed for the CTA); a tile adds k0 and ko.
   int offa[LA], offb[LB];  // 32-bit: the plan keeps every tile offset below 2^31 elements
   unsigned vmask = 0;  // bit r: row of A element r inside M; bit LA + r: column of B element r inside N
+  if (vecA) {  // chunk r: rows m0 + 4 (e % (BM/4)) .. +3 of tile row e / (BM/4)
 #pragma unroll
-  for (int r = 0; r < LA; ++r) {
-    const int e = tid + r * THREADS;
-    int mm, kk;
-    if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
-    const int gm = m0 + mm;
-    offa[r] = (gm < M) ? (int)((int64_t)gm * it.sam + (int64_t)kk * it.sak) : 0;
-    if (gm < M) vmask |= 1u << r;
+    for (int r = 0; r < LAV; ++r) {
+      const int e = tid + r * THREADS;
+      const int gm = m0 + 4 * (e % (BM / 4)), kk = e / (BM / 4);
+      offa[r] = (gm < M) ? (int)(gm + (int64_t)kk * it.sak) : 0;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < LA; ++r) {
+      const int e = tid + r * THREADS;
+      int mm, kk;
+      if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+      const int gm = m0 + mm;
+      offa[r] = (gm < M) ? (int)((int64_t)gm * it.sam + (int64_t)kk * it.sak) : 0;
+      if (gm < M) vmask |= 1u << r;
+    }
   }
+  if (vecB) {  // chunk r: columns n0 + 4 (e % (BN/4)) .. +3 of tile row e / (BN/4)
 #pragma unroll
-  for (int r = 0; r < LB; ++r) {
-    const int e = tid + r * THREADS;
-    int nn, kk;
-    if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
-    const int gn = n0 + nn;
-    offb[r] = (gn < N) ? (int)((int64_t)kk * it.sbk + (int64_t)gn * it.sbn) : 0;
-    if (gn < N) vmask |= 1u << (LA + r);
+    for (int r = 0; r < LBV; ++r) {
+      const int e = tid + r * THREADS;
+      const int gn = n0 + 4 * (e % (BN / 4)), kk = e / (BN / 4);
+      offb[r] = (gn < N) ? (int)((int64_t)kk * it.sbk + gn) : 0;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < LB; ++r) {
+      const int e = tid + r * THREADS;
+      int nn, kk;
+      if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+      const int gn = n0 + nn;
+      offb[r] = (gn < N) ? (int)((int64_t)kk * it.sbk + (int64_t)gn * it.sbn) : 0;
+      if (gn < N) vmask |= 1u << (LA + r);
+    }
   }
   // issue the copies of BK-tile q into stage st (one commit group per call)
   auto issue = [&](int q, int st) {
@@ -160,21 +192,43 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) != 4 ? 1
         const int64_t rest = it.k_total - ((int64_t)ko * K + k0);
         if (rest < klim) klim = (int)(rest > 0 ? rest : 0);
       }
+      if (vecA) {
 #pragma unroll
-      for (int r = 0; r < LA; ++r) {
-        const int e = tid + r * THREADS;
-        int mm, kk;
-        if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
-        const bool v = ((vmask >> r) & 1u) && kk < klim;
-        cp_async_elem<T>(&As[st][kk][mm], Ak + (v ? offa[r] : 0), v);
+        for (int r = 0; r < LAV; ++r) {
+          const int e = tid + r * THREADS;
+          const int mm = 4 * (e % (BM / 4)), kk = e / (BM / 4);
+          const int rows = M - (m0 + mm);
+          const int bytes = (kk < klim) ? 4 * (rows < 0 ? 0 : (rows > 4 ? 4 : rows)) : 0;
+          cp_async_16(&As[st][kk][mm], Ak + (bytes ? offa[r] : 0), bytes);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < LA; ++r) {
+          const int e = tid + r * THREADS;
+          int mm, kk;
+          if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+          const bool v = ((vmask >> r) & 1u) && kk < klim;
+          cp_async_elem<T>(&As[st][kk][mm], Ak + (v ? offa[r] : 0), v);
+        }
       }
+      if (vecB) {
 #pragma unroll
-      for (int r = 0; r < LB; ++r) {
-        const int e = tid + r * THREADS;
-        int nn, kk;
-        if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
-        const bool v = ((vmask >> (LA + r)) & 1u) && kk < klim;
-        cp_async_elem<T>(&Bs[st][kk][nn], Bk + (v ? offb[r] : 0), v);
+        for (int r = 0; r < LBV; ++r) {
+          const int e = tid + r * THREADS;
+          const int nn = 4 * (e % (BN / 4)), kk = e / (BN / 4);
+          const int cols = N - (n0 + nn);
+          const int bytes = (kk < klim) ? 4 * (cols < 0 ? 0 : (cols > 4 ? 4 : cols)) : 0;
+          cp_async_16(&Bs[st][kk][nn], Bk + (bytes ? offb[r] : 0), bytes);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+          const int e = tid + r * THREADS;
+          int nn, kk;
+          if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+          const bool v = ((vmask >> (LA + r)) & 1u) && kk < klim;
+          cp_async_elem<T>(&Bs[st][kk][nn], Bk + (v ? offb[r] : 0), v);
+        }
       }
     }
     cp_async_commit();
