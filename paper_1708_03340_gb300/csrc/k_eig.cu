@@ -27,6 +27,7 @@ namespace htgb {
 namespace {
 
 constexpr int EIG_THREADS = 256;
+constexpr int REFINE_THREADS = 512;  // one thread per 4 x 2 outputs of a 64 x 64 product
 constexpr int kEigSmemK = 128;
 
 template <typename T>
@@ -454,38 +455,43 @@ __device__ __forceinline__ void df_mac(float &hi, float &lo, float a, float b) {
 template <bool kTransA, bool kALo, bool kBLo>
 __device__ void df_gemm(const float *Ah, const float *Al, const float *Bh, const float *Bl, float *Ch, float *Cl,
                         int k, int ld) {
-  const int tiles = (k + 3) / 4;
-  for (int t = threadIdx.x; t < tiles * tiles; t += blockDim.x) {
-    const int ti = (t / tiles) * 4, tj = (t % tiles) * 4;
-    float hi[4][4], lo[4][4];
+  constexpr int BI = 4, BJ = 2;  // outputs per thread: 4 rows x 2 columns
+  const int ti_n = (k + BI - 1) / BI, tj_n = (k + BJ - 1) / BJ;
+  for (int t = threadIdx.x; t < ti_n * tj_n; t += blockDim.x) {
+    const int ti = (t / tj_n) * BI, tj = (t % tj_n) * BJ;
+    float hi[BI][BJ], lo[BI][BJ];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < BI; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) hi[u][v] = lo[u][v] = 0.0f;
+      for (int v = 0; v < BJ; ++v) hi[u][v] = lo[u][v] = 0.0f;
     for (int l = 0; l < k; ++l) {
-      float ah[4], al[4], bh[4], bl[4];
+      float ah[BI], al[BI], bh[BJ], bl[BJ];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = ti + u, j = tj + u;
+      for (int u = 0; u < BI; ++u) {
+        const int i = ti + u;
         const int ia = kTransA ? i * ld + l : l * ld + i;
         ah[u] = (i < k) ? Ah[ia] : 0.0f;
         al[u] = (kALo && i < k) ? Al[ia] : 0.0f;
-        bh[u] = (j < k) ? Bh[j * ld + l] : 0.0f;
-        bl[u] = (kBLo && j < k) ? Bl[j * ld + l] : 0.0f;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < BJ; ++v) {
+        const int j = tj + v;
+        bh[v] = (j < k) ? Bh[j * ld + l] : 0.0f;
+        bl[v] = (kBLo && j < k) ? Bl[j * ld + l] : 0.0f;
+      }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
+      for (int u = 0; u < BI; ++u)
+#pragma unroll
+        for (int v = 0; v < BJ; ++v) {
           df_mac(hi[u][v], lo[u][v], ah[u], bh[v]);
           if (kALo) lo[u][v] = __fmaf_rn(al[u], bh[v], lo[u][v]);
           if (kBLo) lo[u][v] = __fmaf_rn(ah[u], bl[v], lo[u][v]);
         }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < BI; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v)
+      for (int v = 0; v < BJ; ++v)
         if (ti + u < k && tj + v < k) {
           const float s = __fadd_rn(hi[u][v], lo[u][v]);  // renormalise: |lo| <= ulp(hi) / 2
           Ch[(tj + v) * ld + ti + u] = s;
@@ -503,7 +509,7 @@ __host__ __device__ size_t refine_df_smem(int max_k, bool arrays) {
   return base + (arrays ? 7 * (size_t)max_k * (max_k + 1) * sizeof(float) : 0);
 }
 
-__global__ void __launch_bounds__(EIG_THREADS) refine_df_kernel(const EigItem *__restrict__ items, double *scratch,
+__global__ void __launch_bounds__(REFINE_THREADS) refine_df_kernel(const EigItem *__restrict__ items, double *scratch,
                                                                 int64_t scratch_stride, int max_k, int in_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EigItem it = items[blockIdx.x];
@@ -663,7 +669,7 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
   const size_t dsm = refine_df_smem(max_k, in_smem);
   e = cudaFuncSetAttribute(refine_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
   if (e != cudaSuccess) return e;
-  refine_df_kernel<<<n_items, EIG_THREADS, dsm, s>>>(d_items, scratch, 4 * (int64_t)max_k * max_k, max_k,
+  refine_df_kernel<<<n_items, REFINE_THREADS, dsm, s>>>(d_items, scratch, 4 * (int64_t)max_k * max_k, max_k,
                                                      in_smem ? 1 : 0);
   count_launch();
   return cudaGetLastError();
