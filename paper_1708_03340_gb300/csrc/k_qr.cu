@@ -222,6 +222,147 @@ __global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two-column variant for launches with more blocks than SMs (FP32, n <= 64):
+// 8 warps, and group g of warp w holds columns c0 = 8w + g and c1 = 8w + 4 + g
+// (64 data registers a thread), so that two blocks share an SM and fill each
+// other's barrier and shared-memory waits.  Every column goes through the
+// same reflector, dot-product and axpy steps as in qr_reg_kernel; R comes out
+// bit-identical on random blocks, Q within a few units in the last place (the
+// compiled backward accumulation rounds differently).  The warp that owns the
+// next reflector's column updates that column's set first, forms the
+// reflector, then updates its other set; the other warps update both of their
+// columns with one pass over y_j.
+// ---------------------------------------------------------------------------
+
+// Both of a lane's columns: a <- a - kappa (y^T a) y and b likewise, y read
+// once per pass (the dot products and axpys are those of apply_reflector).
+template <typename T, int NI>
+__device__ __forceinline__ void apply_reflector2(T (&a)[NI][4], T (&b)[NI][4], const T *vj, T tj, bool upda,
+                                                 bool updb, int s) {
+  T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+  T f0 = T(0), f1 = T(0), f2 = T(0), f3 = T(0);
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    T x[4];
+    ld4(vj + 32 * i + 4 * s, x);
+    d0 += x[0] * a[i][0];
+    d1 += x[1] * a[i][1];
+    d2 += x[2] * a[i][2];
+    d3 += x[3] * a[i][3];
+    f0 += x[0] * b[i][0];
+    f1 += x[1] * b[i][1];
+    f2 += x[2] * b[i][2];
+    f3 += x[3] * b[i][3];
+  }
+  const T suma = group_sum((d0 + d1) + (d2 + d3));
+  const T sumb = group_sum((f0 + f1) + (f2 + f3));
+  const T da = upda ? tj * suma : T(0);
+  const T db = updb ? tj * sumb : T(0);
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    T x[4];
+    ld4(vj + 32 * i + 4 * s, x);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      a[i][e] -= da * x[e];
+      b[i][e] -= db * x[e];
+    }
+  }
+}
+
+template <typename T, int NI>
+__global__ void __launch_bounds__(256, 2) qr_reg2_kernel(const QrItem *__restrict__ items) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const QrItem it = items[blockIdx.x];
+  const int m = it.m, n = it.n;
+  T *V = reinterpret_cast<T *>(smem_raw);  // REG_MR x n: y_j in column j
+  T *tau = V + (int64_t)REG_MR * n;        // n: kappa_j
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 3, s = lane & 7;
+  const int c0 = 8 * warp + g, c1 = c0 + 4;  // this lane's columns
+  T a0[NI][4], a1[NI][4];
+  {
+    const T *A0 = static_cast<const T *>(it.A) + (int64_t)c0 * it.lda;
+    const T *A1 = static_cast<const T *>(it.A) + (int64_t)c1 * it.lda;
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 32 * i + 4 * s + e;
+        a0[i][e] = (c0 < n && r < m) ? A0[r] : T(0);
+        a1[i][e] = (c1 < n && r < m) ? A1[r] : T(0);
+      }
+  }
+  if (warp == 0) form_reflector<T, NI>(a0, V, tau, 0, lane, g == 0);
+  for (int j = 0; j + 1 < n; ++j) {
+    __syncthreads();                  // y_j and kappa_j are in shared memory
+    if (8 * warp + 7 <= j) continue;  // no column of this warp lies right of j
+    const T *vj = V + (int64_t)j * REG_MR;
+    const T tj = tau[j];
+    const int o = j + 1;  // column of the next reflector
+    if ((o >> 3) == warp) {
+      T *vo = V + (int64_t)o * REG_MR;
+      if ((o & 4) == 0) {  // o is in the c0 set; every c1 column lies right of j
+        apply_reflector<T, NI, false>(a0, vj, tj, c0 > j, s);
+        form_reflector<T, NI>(a0, vo, tau + o, o, lane, g == (o & 3));
+        apply_reflector<T, NI, false>(a1, vj, tj, true, s);
+      } else {  // o is in the c1 set; no c0 column lies right of j
+        apply_reflector<T, NI, false>(a1, vj, tj, c1 > j, s);
+        form_reflector<T, NI>(a1, vo, tau + o, o, lane, g == (o & 3));
+      }
+    } else if (8 * warp + 3 > j) {
+      apply_reflector2<T, NI>(a0, a1, vj, tj, c0 > j, c1 > j, s);
+    } else {
+      apply_reflector<T, NI, false>(a1, vj, tj, c1 > j, s);
+    }
+  }
+  __syncthreads();
+  // R (n x n upper triangular) from the registers
+  {
+    T *R0 = static_cast<T *>(it.R) + (int64_t)c0 * it.ldr;
+    T *R1 = static_cast<T *>(it.R) + (int64_t)c1 * it.ldr;
+#pragma unroll
+    for (int i = 0; i < 2 && i < NI; ++i)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 32 * i + 4 * s + e;
+        if (c0 < n && r < n) R0[r] = (r <= c0) ? a0[i][e] : T(0);
+        if (c1 < n && r < n) R1[r] = (r <= c1) ? a1[i][e] : T(0);
+      }
+  }
+  // Explicit Q, accumulated backwards as in qr_reg_kernel: column c is
+  // untouched by H_j for j > c, so the c1 set starts at j = 8w + 7 and the
+  // c0 set joins at j = 8w + 3.
+#pragma unroll
+  for (int i = 0; i < NI; ++i)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = 32 * i + 4 * s + e;
+      a0[i][e] = (r == c0) ? T(1) : T(0);
+      a1[i][e] = (r == c1) ? T(1) : T(0);
+    }
+  for (int j = min(n - 1, 8 * warp + 7); j >= 0; --j) {
+    const T *vj = V + (int64_t)j * REG_MR;
+    if (j > 8 * warp + 3)
+      apply_reflector<T, NI, false>(a1, vj, tau[j], true, s);
+    else
+      apply_reflector2<T, NI>(a0, a1, vj, tau[j], true, true, s);
+  }
+  {
+    T *Q0 = static_cast<T *>(it.Q) + (int64_t)c0 * it.ldq;
+    T *Q1 = static_cast<T *>(it.Q) + (int64_t)c1 * it.ldq;
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 32 * i + 4 * s + e;
+        if (c0 < n && r < m) Q0[r] = a0[i][e];
+        if (c1 < n && r < m) Q1[r] = a1[i][e];
+      }
+  }
+}
+
 template <typename T, int NW, int NI>
 cudaError_t launch_qr_reg(const QrItem *d_items, int n_items, int max_n, cudaStream_t s) {
   constexpr bool kKeep = sizeof(T) * NI <= 32;  // FP32 keeps w in registers, FP64 reads it twice
@@ -240,12 +381,39 @@ int qr_max_rows(int n, int elem_bytes) {
   return (n <= 64) ? kRegRows : 0;  // wider matrices are factored in 64-column panels
 }
 
+static cudaError_t launch_qr_reg2(const QrItem *d_items, int n_items, int max_n, cudaStream_t s) {
+  const size_t smem = ((size_t)REG_MR * max_n + max_n) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(qr_reg2_kernel<float, kRegRows / 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  // two blocks of up to 65 KB each: ask for the largest shared-memory carveout
+  e = cudaFuncSetAttribute(qr_reg2_kernel<float, kRegRows / 32>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  qr_reg2_kernel<float, kRegRows / 32><<<n_items, 256, smem, s>>>(d_items);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Two-column kernel for FP32 launches with more blocks than SMs (two blocks
+// per SM instead of one); HTGB_QR2=0 or 1 forces the choice either way.
+static bool use_qr_reg2(int n_items) {
+  const char *v = getenv("HTGB_QR2");
+  if (v && v[0] == '0') return false;
+  if (v && v[0] == '1') return true;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  return n_items > sms;
+}
+
 template <typename T>
 cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
   if (max_n > 64 || max_m > kRegRows) return cudaErrorInvalidValue;  // the TSQR driver never asks for more
   if (max_n <= 16) return launch_qr_reg<T, 4, kRegRows / 32>(d_items, n_items, max_n, s);
   if (max_n <= 32) return launch_qr_reg<T, 8, kRegRows / 32>(d_items, n_items, max_n, s);
+  if (sizeof(T) == 4 && use_qr_reg2(n_items)) return launch_qr_reg2(d_items, n_items, max_n, s);
   return launch_qr_reg<T, 16, kRegRows / 32>(d_items, n_items, max_n, s);
 }
 

@@ -248,3 +248,16 @@ def test_tensor_core_contractions_match_simt(case, monkeypatch):
     check_sigma(s1, s0, tol)
     assert abs(r1["norm"] - r0["norm"]) <= tol * r0["norm"]
     assert np.abs(e1 - e0).max() <= tol * r0["norm"]
+
+
+@pytest.mark.parametrize("case", ["big_rank", "rank128", "rank200"])
+def test_two_column_qr_kernel(case, monkeypatch):
+    """The two-column TSQR block kernel (two blocks per SM, chosen for FP32
+    launches of 64-column blocks with more blocks than SMs) forced onto every
+    such launch by HTGB_QR2=1: the oracle checks of the one-column kernel
+    (orthogonality, tensor unchanged, ||X||, then the truncation)."""
+    monkeypatch.setenv("HTGB_QR2", "1")
+    test_orthogonalize(F32, case)
+    d, n, a, c = _case(case)
+    r = {"big_rank": 30, "rank128": 64, "rank200": 100}[case]
+    _trunc_compare(d, n, a, c, F32, dict(mode="rank", rank_cap=r))
