@@ -101,10 +101,10 @@ WORKLOADS = {
 }
 
 # DRAM bytes (read + write) per launch of the dominant kernel family, averaged
-# over one step's launches of that family, from one ncu capture of the current
-# kernels (profiles/gemm_kernel_single_d64_fp32.md, profiles/qr_reg_kernel_single_d64_fp32.md);
-# None where not captured.
-TRAFFIC_PER_LAUNCH = {("single", "gemm"): 15.62e6, ("single", "qr"): 6.29e6}
+# over one step's launches of that family (17 TSQR, 39 contraction launches),
+# from one ncu capture of the current kernels
+# (profiles/launches_single_d64_n1000_k32_fp32.md); None where not captured.
+TRAFFIC_PER_LAUNCH = {("single", "gemm"): 15.56e6, ("single", "qr"): 6.27e6}
 
 
 def model_flops(d, n, K, r):
@@ -407,7 +407,7 @@ def main():
         per_launch_ms = rec["ms"] / rec["launches"]
         per_launch_flops = rec["flops"] / rec["launches"]
         ach = per_launch_flops / (per_launch_ms / 1e3)
-        kernel = {"qr": "qr_reg_kernel (FP32 TSQR blocks)", "gemm": "gemm_kernel (FP32 SIMT, compensated)",
+        kernel = {"qr": "qr_reg_kernel + qr_reg2_kernel (FP32 TSQR blocks)", "gemm": "gemm_kernel (FP32 SIMT, compensated)",
                   "eig": "eig_ql_kernel<float> + refine_df_kernel (double-float)"}.get(name, name)
         peak = FP32_PEAK  # every family of the FP32 path runs on the FP32 pipes (the refinement in double-float)
         roofline = {"kernel": kernel, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
