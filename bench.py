@@ -102,8 +102,8 @@ WORKLOADS = {
 
 # DRAM bytes (read + write) per launch of the dominant kernel family, averaged
 # over one step's launches of that family (17 TSQR, 39 contraction launches),
-# from one ncu capture of the current kernels
-# (profiles/launches_single_d64_n1000_k32_fp32.md); None where not captured.
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# current kernels on the same workload; None where not captured.
 TRAFFIC_PER_LAUNCH = {("single", "gemm"): 15.56e6, ("single", "qr"): 6.27e6}
 
 
