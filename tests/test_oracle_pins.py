@@ -275,6 +275,35 @@ def test_eps_truncation_meets_eps():
         assert abs(res["norm"] - np.linalg.norm(full)) < 1e-13 * np.linalg.norm(full)
 
 
+
+@pytest.mark.parametrize("seed,eps", [(5, 3e-1), (5, 1e-1), (7, 3e-2), (7, 1e-2), (2, 1e-3)])
+def test_eps_rank_rule_against_full_svds(seed, eps):
+    """The eps rank rule (the paper cites [Gr10] without stating it; reading:
+    r_t is the smallest r >= 1 whose tail sum_{i>r} (sigma_{t,i}^2 + nu_t)
+    fits (eps ||A||)^2 / (2d-3), nu_t = 4 sqrt(2d-1) 2^-53 sigma_{t,1}^2, the
+    root's two sons share the rank of the first) against singular values of
+    the full tensor's matricizations: a divisor of 2d-2 or 2d-1, or a cut one
+    place late, changes some rank in these cases.  (That the root pair's tail
+    is counted once is pinned by the discarded energy in the bounds test.)"""
+    (n, ka, xa), (_, kc, xc) = I.brute_pair(seed)
+    d = 4
+    k, x = O.add(d, n, ka, xa, kc, xc)
+    full = _full(d, n, k, x)
+    budget = (eps * np.linalg.norm(full)) ** 2 / (2 * d - 3)
+    res = O.truncate(d, n, k, x, mode="eps", eps=eps, eps_relative=True)
+    tr = I.tree(d)
+    want = [1] * (2 * d - 1)
+    for t in range(1, 2 * d - 1):
+        s = np.linalg.svd(F.matricization(full, tr["lo"][t], tr["hi"][t]), compute_uv=False)[: int(res["korth"][t])]
+        lam = s ** 2 + 4.0 * np.sqrt(2 * d - 1) * 2.0 ** -53 * s[0] ** 2
+        tails = [float(np.sum(lam[r:])) for r in range(len(lam) + 1)]
+        # no tail within 1e-9 of the budget: the cut is decided by the reading, not by rounding
+        assert all(abs(tl - budget) > 1e-9 * budget for tl in tails)
+        want[t] = next(r for r in range(1, len(lam) + 1) if tails[r] <= budget)
+    want[tr["son2"][0]] = want[tr["son1"][0]]
+    assert list(res["k"]) == want
+    assert len(set(want[1:])) > 1  # the cases cut at different ranks per node
+
 def test_golden_diagonal_tensor():
     g = json.load(open(os.path.join(GOLDEN, "diag_d4.json")))
     d, n, k, x = g["d"], np.array(g["n"]), np.array(g["ranks"]), np.array(g["blob"])
