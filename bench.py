@@ -137,10 +137,21 @@ def start_clock_sampler(path):
          "clocks_event_reasons.sw_power_cap")
     try:
         f = open(path, "w")
-        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
-                                stdout=f, stderr=subprocess.DEVNULL), f
+        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "50"],
+                                stdout=f, stderr=subprocess.DEVNULL)
     except Exception:
         return None, None
+    # the timed region of a short run lasts well under a second: start it only
+    # once the sampler writes (at most 3 s of waiting)
+    t0 = time.time()
+    while time.time() - t0 < 3.0 and proc.poll() is None:
+        try:
+            if os.path.getsize(path) > 0:
+                break
+        except OSError:
+            break
+        time.sleep(0.01)
+    return proc, f
 
 
 def read_clocks(proc, f, path, gpu_index):
