@@ -137,7 +137,7 @@ def start_clock_sampler(path):
          "clocks_event_reasons.sw_power_cap")
     try:
         f = open(path, "w")
-        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "50"],
+        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
                                 stdout=f, stderr=subprocess.DEVNULL)
     except Exception:
         return None, None
