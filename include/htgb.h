@@ -81,11 +81,12 @@ typedef enum { HT_SCHED_LEVEL = 0, HT_SCHED_NODE = 1 } ht_schedule;
  *         rank_cap if > 0, rank available after orthogonalization).
  *  mode = HT_TRUNC_EPS:  r_t = smallest r >= 1 with sum_{i>r} (sigma_{t,i}^2 + nu_t)
  *         <= eps_abs^2 / (2d-3), eps_abs = eps * ||X|| if eps_relative, then
- *         capped as above.  nu_t = 4 sqrt(2d-1) u sigma_{t,1}^2 is the noise
- *         floor of a computed eigenvalue (u = 2^-53 for HT_PREC_FP64, 2^-24 for
- *         HT_PREC_FP32): an eps below what the arithmetic resolves keeps rank.
- *         The two sons of the root have the same singular values and share
- *         one rank (decided on the first son).
+ *         capped as above.  On F64 tensors nu_t = 0: the computed tail alone
+ *         decides.  On F32 tensors nu_t = 4 sqrt(2d-1) u_32 sigma_{t,1}^2 (its
+ *         square for HT_PREC_FP32_SQRT) is the noise floor of an eigenvalue of
+ *         an FP32-computed Gramian: an eps below what that arithmetic resolves
+ *         keeps rank.  The two sons of the root have the same singular values
+ *         and share one rank (decided on the first son).
  *  prec: HT_PREC_FP64 needs an F64 tensor, HT_PREC_FP32 an F32 tensor.
  *  tensor_caps: NULL, or (batch calls) one rank cap per tensor, host array of
  *         count entries, used instead of rank_cap for that tensor. */
@@ -98,9 +99,15 @@ typedef struct {
   int prec;
   int schedule;
   const int *tensor_caps; /* host, one per tensor of a batch call, or NULL */
+  int qr_kernel;          /* TSQR row-block kernel: 0 by shape and launch size (default),
+                             1 the one-column kernel, 2 the two-column kernel (F32
+                             blocks of 64 columns; smaller blocks keep their kernel) */
 } ht_trunc_opts;
 
-/* Optional report (pass NULL to skip; synchronises when given).
+/* Optional report (pass NULL to skip; synchronises when given).  With a
+ * report the truncation returns HT_ENUMERIC (after filling the report) when a
+ * tensor's ||X|| or one of its Gramian eigenvalues is not finite, e.g. NaN or
+ * Inf in the input; without one, ht_device_status reports it.
  *  norm         ||X|| = ||B_D||_F after orthogonalization (Sec. 3.4)
  *  discarded_sq sum over non-root nodes of the discarded sigma^2 (root pair once)
  *  bound        sqrt(discarded_sq): the a-priori error bound of [Gr10]
@@ -202,6 +209,8 @@ ht_status ht_gramians(ht_tensor *x_orth, double *dev_out, int prec);
  * several host threads) race on it and must be serialised by the caller. */
 #define HT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 ht_status ht_gramians_noalloc(ht_tensor *x_orth, double *dev_out, int prec);
+/* (The fixed array used is the current device's: the tensor's stream must run
+ * on the current device, else HT_EINVAL.) */
 
 /* HSVD truncation T(X), Sec. 3.3 after Sec. 3.4, in place: orthogonalize,
  * Gramians of all non-root nodes, their eigendecompositions (singular values
@@ -281,14 +290,31 @@ ht_status ht_profile_read(int kind, int64_t *launches, double *total_ms, double 
 /* Number of kernels this library has launched since it was loaded (all kinds). */
 ht_status ht_launch_count(int64_t *total);
 
-/* Synchronises the device, then reports the device-side error word of the
- * kernels whose threads wait on one another inside a CTA (the opt-in tcgen05
- * contraction's mbarrier waits).  Every such wait is bounded; one that gave
- * up (never expected: the waiting and the signalling threads belong to one
- * resident CTA) marks its results invalid and sets the word.  Returns HT_ETIMEOUT if a
- * word was set since the last call (and clears it), HT_ECUDA if the device
- * reports an error, else HT_OK. */
+/* Synchronises the device, then reads and clears the library's device
+ * status words:
+ *  - bounded waits: every wait of a library kernel (the tcgen05 contractions'
+ *    mbarrier waits, the self-test below) is limited in time; one that gave
+ *    up marks its results invalid, sets a word and returns -> HT_ETIMEOUT;
+ *  - an eigensolver sweep that reached its iteration limit -> HT_ENUMERIC;
+ *  - a non-finite ||X|| or Gramian eigenvalue met by a truncation (NaN or Inf
+ *    in the input) -> HT_ENUMERIC.
+ * HT_ECUDA if the device reports an error, else HT_OK. */
 ht_status ht_device_status(void);
+
+/* Self-test of the bounded-wait machinery (no counterpart in the paper):
+ * enqueues on `stream` one kernel whose single thread waits for a device flag
+ * that no code ever sets, with the library's time bound set to limit_ms
+ * (0 <= limit_ms <= 1000); the wait runs out, marks the wait status word and
+ * the kernel returns.  The next ht_device_status returns HT_ETIMEOUT and the
+ * context stays usable.  Errors: HT_EINVAL (limit), HT_ECUDA (launch). */
+ht_status ht_selftest_wait(double limit_ms, void *stream);
+
+/* Tile-shape rule of the SIMT contraction kernel: launches whose flops lie
+ * mostly (share >= tall_share) in items with M >= tall_m use 128-row tiles,
+ * those with square_share in items with M, N >= tall_m 128 x 128 tiles.  The
+ * defaults are the committed autotuner table; tall_m < 0 restores them.  Used
+ * by the autotuner to time candidates without rebuilding; not thread-safe. */
+ht_status ht_set_gemm_tuning(int tall_m, double tall_share, double square_share);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *ht_last_error(void);

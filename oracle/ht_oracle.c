@@ -509,16 +509,19 @@ typedef struct {
   int eps_relative;  /* 1: eps_abs = eps * ||X|| */
   int rank_cap;      /* <= 0: none */
   const int *ranks;  /* mode 0: target rank per node (pre-order), or NULL = rank_cap */
+  double noise;      /* mode 1: charge per dropped eigenvalue, relative to the node's largest (0: none) */
 } ho_opts;
 
 /* Rank rule for one node (reading of the eps truncation of [Gr10]): the
- * smallest r >= 1 whose discarded tail sum_{i>r} max(lambda_i,0) is <= tail2,
- * then capped. */
-static int eps_rank(const double *lam, int k, double tail2) {
+ * smallest r >= 1 whose discarded tail sum_{i>r} (max(lambda_i,0) + nu) is
+ * <= tail2, then capped.  nu = noise * max(lambda_1, 0) is an optional charge
+ * per dropped eigenvalue (0 gives the plain rule: the computed tail alone). */
+static int eps_rank(const double *lam, int k, double tail2, double noise) {
+  const double nu = noise * (lam[0] > 0.0 ? lam[0] : 0.0);
   double tail = 0.0;
   int r = k;
   for (int i = k - 1; i >= 1; --i) { /* can we drop lambda_i (0-based)? */
-    double l = lam[i] > 0.0 ? lam[i] : 0.0;
+    double l = (lam[i] > 0.0 ? lam[i] : 0.0) + nu;
     if (tail + l <= tail2) {
       tail += l;
       r = i;
@@ -599,7 +602,7 @@ int ho_truncate(int d, const int64_t *n, int *k, const double *x, const ho_opts 
     int avail = korth[t];
     int rt;
     if (opts->mode == 1) {
-      rt = eps_rank(lam + ol[t], avail, tail2);
+      rt = eps_rank(lam + ol[t], avail, tail2, opts->noise);
     } else {
       rt = (opts->ranks) ? opts->ranks[t] : opts->rank_cap;
       if (rt <= 0) rt = avail;

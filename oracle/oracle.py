@@ -70,6 +70,7 @@ class _Opts(ctypes.Structure):
         ("eps_relative", ctypes.c_int),
         ("rank_cap", ctypes.c_int),
         ("ranks", ctypes.POINTER(ctypes.c_int)),
+        ("noise", ctypes.c_double),
     ]
 
 
@@ -156,14 +157,16 @@ def gramians(d, n, k, x):
     return out
 
 
-def truncate(d, n, k, x, mode="rank", eps=0.0, eps_relative=True, rank_cap=0, ranks=None):
+def truncate(d, n, k, x, mode="rank", eps=0.0, eps_relative=True, rank_cap=0, ranks=None, noise=0.0):
     """HSVD truncation T(X) (Sec. 3.3 after Sec. 3.4).
 
     Returns a dict with ``k`` (truncated ranks), ``x`` (truncated blob),
     ``korth`` (ranks after orthogonalization), ``sigma`` (list per node of
     the singular values, root entry empty), ``norm`` (||X||),
     ``discarded_sq`` (sum of discarded sigma^2, root pair counted once) and
-    ``tail2`` (per-node squared threshold in eps mode).
+    ``tail2`` (per-node squared threshold in eps mode).  ``noise``: charge
+    per dropped eigenvalue in eps mode, relative to the node's largest
+    eigenvalue (0, the default, is the plain rule on the computed tail).
     """
     n, x = _i64(n), _f64(x)
     kk = _i32(k).copy()
@@ -176,6 +179,7 @@ def truncate(d, n, k, x, mode="rank", eps=0.0, eps_relative=True, rank_cap=0, ra
     opts.eps = float(eps)
     opts.eps_relative = 1 if eps_relative else 0
     opts.rank_cap = int(rank_cap)
+    opts.noise = float(noise)
     rk = None
     if ranks is not None:
         rk = _i32(ranks)

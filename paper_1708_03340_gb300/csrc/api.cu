@@ -277,6 +277,7 @@ struct Plan {
   size_t p_bytes = 0, s_bytes = 0, s_peak = 0;
   bool node_sched = false;
   bool sqrt_gram = false;  // Gramians from square-root factors (HT_PREC_FP32_SQRT)
+  int qr_kernel = 0;       // TSQR block kernel choice (ht_trunc_opts.qr_kernel)
   int dtype = HT_F64;
   size_t esz = 8;
   std::string err;  // set by a planning step that cannot handle its input
@@ -497,28 +498,14 @@ void reloc_items<RankItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
 
 
 // Tuning table (gemm_tune.h, written by tune_gemm.py); the autotuner sweeps
-// it through HTGB_TUNE="tall_m,tall_share,square_share" without rebuilding.
+// candidates through ht_set_gemm_tuning without rebuilding.
 struct GemmTune {
   int tall_m = kTuneTallM;
   double tall_share = kTuneTallShare;
   double square_share = kTuneSquareShare;
 };
-const GemmTune &gemm_tune() {
-  static GemmTune t = [] {
-    GemmTune v;
-    if (const char *e = getenv("HTGB_TUNE")) {
-      int m = 0;
-      double a = 0.0, b = 0.0;
-      if (sscanf(e, "%d,%lf,%lf", &m, &a, &b) == 3) {
-        v.tall_m = m;
-        v.tall_share = a;
-        v.square_share = b;
-      }
-    }
-    return v;
-  }();
-  return t;
-}
+GemmTune g_gemm_tune;
+const GemmTune &gemm_tune() { return g_gemm_tune; }
 
 // Split-K factor of a launch with `tiles` output tiles: as many chunks as
 // keep every CTA of the launch resident in one round of two CTAs per SM
@@ -662,8 +649,8 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
         break;
       }
       case L_QR:
-        e = f64 ? launch_qr<double>((const QrItem *)items, L.n, L.max_m, L.max_n, s)
-                : launch_qr<float>((const QrItem *)items, L.n, L.max_m, L.max_n, s);
+        e = f64 ? launch_qr<double>((const QrItem *)items, L.n, L.max_m, L.max_n, s, P.qr_kernel)
+                : launch_qr<float>((const QrItem *)items, L.n, L.max_m, L.max_n, s, P.qr_kernel);
         break;
       case L_EIG:
         // square-root Gramians carry eigenvalues far below the FP32 solve's resolution,
@@ -1614,11 +1601,17 @@ void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, in
     r.eps_rel = o.eps_relative;
     r.cap = o.tensor_caps ? o.tensor_caps[i] : o.rank_cap;
     r.eps = o.eps;
-    // noise floor of a computed Gramian eigenvalue: 4 sqrt(2d-1) u lambda_max,
-    // u the unit roundoff of the path (every node's rounding perturbs X independently)
-    r.noise = 4.0 * std::sqrt(2.0 * T.d - 1.0) * (P.dtype == HT_F64 ? 0x1p-53 : 0x1p-24);
-    // square-root Gramians: rounding perturbs the singular values, not their squares
-    if (P.sqrt_gram) r.noise = r.noise * r.noise;
+    // FP64 storage: the plain rule on the computed tail (as the oracle).  FP32
+    // storage: every dropped eigenvalue is also charged the noise floor of an
+    // FP32-computed Gramian eigenvalue, 4 sqrt(2d-1) u_32 lambda_max (every
+    // node's rounding perturbs X independently), so that an eps below what the
+    // path resolves keeps rank instead of cutting noise; square-root Gramians
+    // perturb the singular values, not their squares: the square of that.
+    r.noise = 0.0;
+    if (P.dtype != HT_F64) {
+      r.noise = 4.0 * std::sqrt(2.0 * T.d - 1.0) * 0x1p-24;
+      if (P.sqrt_gram) r.noise = r.noise * r.noise;
+    }
     P.rank(r, S.node_base);
   }
 }
@@ -2006,8 +1999,33 @@ ht_status ht_device_status(void) {
   const cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
   const int t = tc_take_wait_error();
-  if (t < 0) return fail(HT_ECUDA, "reading the device error word failed");
+  const unsigned w = wait_take_status();
+  const unsigned q = eig_take_status();
+  const unsigned m = misc_take_status();
+  if (t < 0 || w == ~0u || q == ~0u || m == ~0u) return fail(HT_ECUDA, "reading a device status word failed");
   if (t) return fail(HT_ETIMEOUT, "a tcgen05 contraction's bounded wait gave up");
+  if (w) return fail(HT_ETIMEOUT, "a bounded device-side wait gave up");
+  if (q) return fail(HT_ENUMERIC, "an eigensolver sweep reached its iteration limit");
+  if (m) return fail(HT_ENUMERIC, "||X|| or a Gramian eigenvalue was not finite (NaN or Inf in the input)");
+  return HT_OK;
+}
+
+ht_status ht_selftest_wait(double limit_ms, void *stream) {
+  if (!(limit_ms >= 0.0) || limit_ms > 1000.0) return fail(HT_EINVAL, "limit_ms must lie in [0, 1000]");
+  const cudaError_t e = launch_selftest_wait((int64_t)(limit_ms * 1e6), static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(HT_ECUDA, std::string("self-test launch failed: ") + cudaGetErrorString(e));
+  return HT_OK;
+}
+
+ht_status ht_set_gemm_tuning(int tall_m, double tall_share, double square_share) {
+  if (tall_m < 0) {
+    g_gemm_tune = GemmTune();
+    return HT_OK;
+  }
+  if (!(tall_share >= 0.0) || !(square_share >= 0.0)) return fail(HT_EINVAL, "shares must be >= 0");
+  g_gemm_tune.tall_m = tall_m;
+  g_gemm_tune.tall_share = tall_share;
+  g_gemm_tune.square_share = square_share;
   return HT_OK;
 }
 
@@ -2402,6 +2420,16 @@ static ht_status noalloc_scratch(char **out) {
 ht_status ht_gramians_noalloc(ht_tensor *x, double *dev_out, int prec) {
   if (!x || !dev_out) return fail(HT_EINVAL, "null argument");
   HT_TRY(check_prec(x, prec));
+  {
+    // the fixed array looked up below is the current device's: the tensor's
+    // stream must run on that device
+    int cur = -1, sdev = -1;
+    HT_CU(cudaGetDevice(&cur));
+    HT_CU(cudaStreamGetDevice(x->stream, &sdev));
+    if (sdev != cur)
+      return fail(HT_EINVAL, "the tensor's stream runs on device " + std::to_string(sdev) + ", the current device is " +
+                                 std::to_string(cur) + ": make the stream's device current");
+  }
   char *scratch = nullptr;
   HT_TRY(noalloc_scratch(&scratch));
   HT_TRY(sync_ranks(x));
@@ -2421,6 +2449,7 @@ static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_o
   if (!xs || count < 1 || !o) return fail(HT_EINVAL, "null argument");
   if (o->mode != HT_TRUNC_RANK && o->mode != HT_TRUNC_EPS) return fail(HT_EINVAL, "bad mode");
   if (o->mode == HT_TRUNC_EPS && !(o->eps >= 0.0)) return fail(HT_EINVAL, "eps must be >= 0");
+  if (o->qr_kernel < 0 || o->qr_kernel > 2) return fail(HT_EINVAL, "qr_kernel must be 0, 1 or 2");
   const int dtype = xs[0]->dtype;
   cudaStream_t s = xs[0]->stream;
   for (int i = 0; i < count; ++i) {
@@ -2435,6 +2464,7 @@ static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_o
   P.esz = (dtype == HT_F64) ? 8 : 4;
   P.node_sched = (o->schedule == HT_SCHED_NODE);
   P.sqrt_gram = (o->prec == HT_PREC_FP32_SQRT);
+  P.qr_kernel = o->qr_kernel;
   std::vector<TState> TS(count);
   int total_nodes = 0;
   for (int i = 0; i < count; ++i) {
@@ -2459,19 +2489,25 @@ static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_o
     x->ranks_ok = false;
     x->orthogonal = false;
   }
+  int nonfinite = -1;  // first tensor whose report flags non-finite values
+  bool eig_limit = false;  // an eigensolver sweep hit its iteration limit (any call since the last check)
   if (rep) {
     std::vector<int> r(total_nodes);
     HT_CU(cudaMemcpyAsync(r.data(), d_r, sizeof(int) * total_nodes, cudaMemcpyDeviceToHost, s));
     std::vector<std::vector<double>> stats(count, std::vector<double>(4)), lam(count);
     for (int i = 0; i < count; ++i) {
       const double *st = reinterpret_cast<const double *>(reloc(TS[i].stats, pb, nullptr, nullptr));
-      HT_CU(cudaMemcpyAsync(stats[i].data(), st, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      HT_CU(cudaMemcpyAsync(stats[i].data(), st, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
       lam[i].resize(TS[i].lam_off.back() + TS[i].ko.back());
       const double *lp = reinterpret_cast<const double *>(reloc(TS[i].lam, pb, nullptr, nullptr));
       HT_CU(cudaMemcpyAsync(lam[i].data(), lp, lam[i].size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     HT_CU(cudaStreamSynchronize(s));
+    const unsigned q = eig_take_status();
+    if (q == ~0u) return fail(HT_ECUDA, "reading the eigensolver status word failed");
+    if (q) eig_limit = true;
     for (int i = 0; i < count; ++i) {
+      if (stats[i][3] != 0.0) nonfinite = i;
       ht_trunc_report &R = rep[i];
       R.norm = stats[i][0];
       R.discarded_sq = stats[i][1];
@@ -2490,6 +2526,12 @@ static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_o
     }
   }
   HT_CU(cudaFreeAsync(pb, s));
+  if (nonfinite >= 0) {
+    misc_take_status();  // this call's non-finite values are reported here
+    return fail(HT_ENUMERIC, "tensor " + std::to_string(nonfinite) +
+                                 " of the call: ||X|| or a Gramian eigenvalue is not finite (NaN or Inf in the input)");
+  }
+  if (eig_limit) return fail(HT_ENUMERIC, "an eigensolver sweep reached its iteration limit");
   return HT_OK;
 }
 
@@ -2532,6 +2574,7 @@ ht_status ht_graph_add_truncate(const ht_tensor *const *a, const ht_tensor *cons
   if (o->mode != HT_TRUNC_RANK && o->mode != HT_TRUNC_EPS) return fail(HT_EINVAL, "bad mode");
   if (o->mode == HT_TRUNC_EPS && !(o->eps >= 0.0)) return fail(HT_EINVAL, "eps must be >= 0");
   if (count > 1 && o->ranks) return fail(HT_EINVAL, "per-node target ranks are only accepted for a single tensor");
+  if (o->qr_kernel < 0 || o->qr_kernel > 2) return fail(HT_EINVAL, "qr_kernel must be 0, 1 or 2");
   cudaStream_t s = out[0] ? out[0]->stream : nullptr;
   for (int i = 0; i < count; ++i) {
     HT_TRY(add_check(a[i], c[i]));
@@ -2563,6 +2606,7 @@ ht_status ht_graph_add_truncate(const ht_tensor *const *a, const ht_tensor *cons
   P.esz = (P.dtype == HT_F64) ? 8 : 4;
   P.node_sched = (o->schedule == HT_SCHED_NODE);
   P.sqrt_gram = (o->prec == HT_PREC_FP32_SQRT);
+  P.qr_kernel = o->qr_kernel;
   std::vector<TState> TS(count);
   int total_nodes = 0;
   for (int i = 0; i < count; ++i) {

@@ -111,6 +111,8 @@ struct RankItem {
   double eps;
   double noise;  // per-eigenvalue noise floor, relative to the node's largest eigenvalue
 };
+// RankItem.stats: [0] ||X||, [1] discarded sigma^2 (root pair once), [2] per-node
+// squared threshold, [3] 1 if ||X|| or an eigenvalue was not finite, else 0.
 
 // ---------------------------------------------------------------------------
 // launchers (stream-ordered; return cudaGetLastError())
@@ -128,8 +130,10 @@ cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, c
                         int uniform = 0);
 void gemm_tile_shape(int variant, int *bm, int *bn);
 cudaError_t launch_gemm_tc(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, cudaStream_t s);
+// qr_kernel: 0 picks the block kernel by shape and launch size; 1 forces the
+// one-column kernel, 2 the two-column kernel (FP32, 64-column blocks).
 template <typename T>
-cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s);
+cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s, int qr_kernel = 0);
 // mode 0: FP64 QL; mode 1: FP32 QL followed by one double-float refinement step.
 // scratch: 4 * max_k^2 doubles per item when max_k exceeds the shared-memory sizes (eig_scratch_needed).
 cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s, int mode);
@@ -159,6 +163,16 @@ cudaError_t launch_scale(void *x, int64_t count, double alpha, cudaStream_t s);
 // read and clear; 1 if a wait gave up since the last call, 0 if not, -1 if
 // the read failed.  Synchronises the device (symbol copies).
 int tc_take_wait_error();
+// Status words of the eigensolvers (bit 0: a QL sweep hit its iteration
+// limit) and of the rank selection (bit 0: a non-finite norm or eigenvalue):
+// read and clear; ~0u if the read failed.  Synchronise the device.
+unsigned eig_take_status();
+unsigned misc_take_status();
+// Bounded-wait self-test (k_misc.cu): one kernel waits limit_ns on a flag that
+// nothing sets, then marks the wait status word (read and cleared by
+// wait_take_status) and returns.
+cudaError_t launch_selftest_wait(int64_t limit_ns, cudaStream_t s);
+unsigned wait_take_status();
 
 // launch accounting / tracing (api.cu)
 void count_launch(int n = 1);

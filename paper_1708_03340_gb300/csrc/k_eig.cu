@@ -24,6 +24,12 @@
 
 namespace htgb {
 
+// Device status word of the eigensolvers: bit 0 is set when a QL sweep gave
+// up on an eigenvalue after its iteration limit (the result is then not an
+// eigendecomposition to working accuracy).  Read and cleared by eig_take_status.
+__device__ unsigned g_eig_status = 0;
+
+
 namespace {
 
 constexpr int EIG_THREADS = 256;
@@ -348,7 +354,10 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
           continue;
         }
         if (++iter > 64) {
-          if (lane == 0) sh.status = 1;
+          if (lane == 0) {
+            sh.status = 1;
+            atomicOr(&g_eig_status, 1u);  // reported by ht_device_status / truncation reports
+          }
           ++l;
           iter = 0;
           continue;
@@ -676,5 +685,15 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
 }
 
 int eig_smem_k() { return kEigSmemK; }
+
+unsigned eig_take_status() {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_eig_status, sizeof(v)) != cudaSuccess) return ~0u;
+  if (v) {
+    const unsigned z = 0;
+    if (cudaMemcpyToSymbol(g_eig_status, &z, sizeof(z)) != cudaSuccess) return ~0u;
+  }
+  return v;
+}
 
 }  // namespace htgb

@@ -7,6 +7,7 @@
 //   * entry evaluation (Sec. 3.1, eq. "transfermult"),
 //   * sum of squares and scaling.
 #include "internal.h"
+#include "wait.cuh"
 
 namespace htgb {
 
@@ -62,6 +63,35 @@ __global__ void compact_kernel(const CompactItem *__restrict__ items, const int 
   }
 }
 
+// Device status word of the rank selection: bit 0 is set when ||X|| or a
+// Gramian eigenvalue is not finite (NaN or Inf in the input, or produced on
+// the way).  Read and cleared by misc_take_status.
+__device__ unsigned g_numeric_status = 0;
+
+
+// ---- bounded-wait self-test -------------------------------------------------
+// Status word of the bounded waits outside the tensor-core kernels: bit 0 is
+// set when a wait gave up.  The self-test kernel waits on a flag that no code
+// sets, so its wait always runs out after limit_ns and the kernel returns:
+// it exercises the time bound, the status word and the host's report without
+// any fault or hang.
+__device__ unsigned g_wait_status = 0;
+__device__ int g_selftest_flag = 0;  // never written
+
+__global__ void selftest_wait_kernel(int64_t limit_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    if (*(volatile int *)&g_selftest_flag != 0) return;
+    if ((int64_t)(globaltimer_ns() - t0) >= limit_ns) {
+      atomicOr(&g_wait_status, 1u);
+      return;
+    }
+    __nanosleep(1000);
+  }
+}
+
+
+
 // ---- rank selection ---------------------------------------------------------
 // One CTA per tensor.  ||X|| from the orthogonalized root; per node the rank
 // rule; the root pair shares one rank; discarded energy with the root pair
@@ -84,6 +114,11 @@ __global__ void ranks_kernel(const RankItem *__restrict__ items) {
     for (int w = 0; w < (nt >> 5); ++w) s += red[w];
     const double nrm = sqrt(s);
     it.stats[0] = nrm;
+    it.stats[3] = 0.0;
+    if (!isfinite(nrm)) {
+      it.stats[3] = 1.0;
+      atomicOr(&g_numeric_status, 1u);
+    }
     double tail2 = 0.0;
     if (it.mode == 1) {
       const double e = it.eps_rel ? it.eps * nrm : it.eps;
@@ -99,6 +134,13 @@ __global__ void ranks_kernel(const RankItem *__restrict__ items) {
   for (int t = 1 + tid; t < it.nn; t += nt) {
     const int avail = it.korth[t];
     const double *lam = it.lam + it.lam_off[t];
+    for (int i = 0; i < avail; ++i) {
+      if (!isfinite(lam[i])) {  // a non-finite input or Gramian: report, never a silent rank
+        it.stats[3] = 1.0;
+        atomicOr(&g_numeric_status, 1u);
+        break;
+      }
+    }
     int r;
     if (it.mode == 1) {
       // a dropped eigenvalue is charged its computed value plus the noise
@@ -379,5 +421,33 @@ cudaError_t launch_scale(void *x, int64_t count, double alpha, cudaStream_t s) {
 }
 template cudaError_t launch_scale<double>(void *, int64_t, double, cudaStream_t);
 template cudaError_t launch_scale<float>(void *, int64_t, double, cudaStream_t);
+
+unsigned misc_take_status() {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_numeric_status, sizeof(v)) != cudaSuccess) return ~0u;
+  if (v) {
+    const unsigned z = 0;
+    if (cudaMemcpyToSymbol(g_numeric_status, &z, sizeof(z)) != cudaSuccess) return ~0u;
+  }
+  return v;
+}
+
+cudaError_t launch_selftest_wait(int64_t limit_ns, cudaStream_t s) {
+  if (limit_ns < 0) limit_ns = 0;
+  if (limit_ns > kWaitLimitNs * 5) limit_ns = kWaitLimitNs * 5;
+  selftest_wait_kernel<<<1, 1, 0, s>>>(limit_ns);
+  count_launch();
+  return cudaGetLastError();
+}
+
+unsigned wait_take_status() {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_wait_status, sizeof(v)) != cudaSuccess) return ~0u;
+  if (v) {
+    const unsigned z = 0;
+    if (cudaMemcpyToSymbol(g_wait_status, &z, sizeof(z)) != cudaSuccess) return ~0u;
+  }
+  return v;
+}
 
 }  // namespace htgb

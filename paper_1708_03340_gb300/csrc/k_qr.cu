@@ -396,11 +396,10 @@ static cudaError_t launch_qr_reg2(const QrItem *d_items, int n_items, int max_n,
 }
 
 // Two-column kernel for FP32 launches with more blocks than SMs (two blocks
-// per SM instead of one); HTGB_QR2=0 or 1 forces the choice either way.
-static bool use_qr_reg2(int n_items) {
-  const char *v = getenv("HTGB_QR2");
-  if (v && v[0] == '0') return false;
-  if (v && v[0] == '1') return true;
+// per SM instead of one); qr_kernel 1 or 2 forces the choice either way.
+static bool use_qr_reg2(int n_items, int qr_kernel) {
+  if (qr_kernel == 1) return false;
+  if (qr_kernel == 2) return true;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return false;
@@ -408,16 +407,16 @@ static bool use_qr_reg2(int n_items) {
 }
 
 template <typename T>
-cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s) {
+cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s, int qr_kernel) {
   if (n_items <= 0) return cudaSuccess;
   if (max_n > 64 || max_m > kRegRows) return cudaErrorInvalidValue;  // the TSQR driver never asks for more
   if (max_n <= 16) return launch_qr_reg<T, 4, kRegRows / 32>(d_items, n_items, max_n, s);
   if (max_n <= 32) return launch_qr_reg<T, 8, kRegRows / 32>(d_items, n_items, max_n, s);
-  if (sizeof(T) == 4 && use_qr_reg2(n_items)) return launch_qr_reg2(d_items, n_items, max_n, s);
+  if (sizeof(T) == 4 && use_qr_reg2(n_items, qr_kernel)) return launch_qr_reg2(d_items, n_items, max_n, s);
   return launch_qr_reg<T, 16, kRegRows / 32>(d_items, n_items, max_n, s);
 }
 
-template cudaError_t launch_qr<double>(const QrItem *, int, int, int, cudaStream_t);
-template cudaError_t launch_qr<float>(const QrItem *, int, int, int, cudaStream_t);
+template cudaError_t launch_qr<double>(const QrItem *, int, int, int, cudaStream_t, int);
+template cudaError_t launch_qr<float>(const QrItem *, int, int, int, cudaStream_t, int);
 
 }  // namespace htgb

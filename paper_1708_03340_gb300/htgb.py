@@ -34,7 +34,7 @@ EXPORTS = [
     "ht_truncate_batch", "ht_norm", "ht_eval_entries", "ht_last_error",
     "ht_profile_set", "ht_profile_read", "ht_launch_count", "ht_gramians_noalloc",
     "ht_graph_add_truncate", "ht_graph_launch", "ht_graph_kernels", "ht_graph_free", "ht_inner", "ht_apply",
-    "ht_device_status",
+    "ht_device_status", "ht_selftest_wait", "ht_set_gemm_tuning",
 ]
 HT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 HT_K_GEMM, HT_K_QR, HT_K_EIG, HT_K_COPY, HT_K_COMPACT, HT_K_RANKS, HT_K_ADD, HT_K_EVAL, HT_K_MISC = range(9)
@@ -57,6 +57,7 @@ class TruncOpts(ctypes.Structure):
         ("prec", ctypes.c_int),
         ("schedule", ctypes.c_int),
         ("tensor_caps", ctypes.POINTER(ctypes.c_int)),
+        ("qr_kernel", ctypes.c_int),
     ]
 
 
@@ -117,6 +118,8 @@ def load(build_if_missing: bool = True):
             "ht_launch_count": ([i64p], ctypes.c_int),
             "ht_device_status": ([], ctypes.c_int),
             "ht_gramians_noalloc": ([vp, vp, ctypes.c_int], ctypes.c_int),
+            "ht_selftest_wait": ([ctypes.c_double, vp], ctypes.c_int),
+            "ht_set_gemm_tuning": ([ctypes.c_int, ctypes.c_double, ctypes.c_double], ctypes.c_int),
             "ht_graph_add_truncate": ([ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
                                        ctypes.POINTER(TruncOpts), ctypes.POINTER(vp)], ctypes.c_int),
             "ht_graph_launch": ([vp], ctypes.c_int),
@@ -235,7 +238,7 @@ def ht_gramians_noalloc(x, dev_ptr, prec=HT_PREC_FP64):
 
 
 def make_opts(mode="rank", eps=0.0, eps_relative=True, rank_cap=0, ranks=None, prec=HT_PREC_FP64,
-              schedule=HT_SCHED_LEVEL, tensor_caps=None):
+              schedule=HT_SCHED_LEVEL, tensor_caps=None, qr_kernel=0):
     o = TruncOpts()
     o.mode = HT_TRUNC_EPS if mode in ("eps", HT_TRUNC_EPS) else HT_TRUNC_RANK
     o.eps = float(eps)
@@ -243,6 +246,7 @@ def make_opts(mode="rank", eps=0.0, eps_relative=True, rank_cap=0, ranks=None, p
     o.rank_cap = int(rank_cap)
     o.prec = int(prec)
     o.schedule = int(schedule)
+    o.qr_kernel = int(qr_kernel)
     keep = None
     if ranks is not None:
         keep = np.ascontiguousarray(ranks, dtype=np.int32)
@@ -348,8 +352,20 @@ def ht_launch_count() -> int:
 
 
 def ht_device_status() -> None:
-    """Synchronises; raises HTError(HT_ETIMEOUT) if a kernel's bounded wait gave up since the last call."""
+    """Synchronises; raises HTError(HT_ETIMEOUT) if a kernel's bounded wait gave
+    up, HTError(HT_ENUMERIC) if an eigensolver hit its iteration limit or a
+    truncation met non-finite values, since the last call."""
     _check(load().ht_device_status())
+
+
+def ht_selftest_wait(limit_ms: float, stream=None) -> None:
+    """Enqueue the bounded-wait self-test kernel (its wait always runs out)."""
+    _check(load().ht_selftest_wait(float(limit_ms), _stream_handle(stream)))
+
+
+def ht_set_gemm_tuning(tall_m: int, tall_share: float, square_share: float) -> None:
+    """Tile-shape rule of the SIMT contraction kernel (tall_m < 0: the committed table)."""
+    _check(load().ht_set_gemm_tuning(int(tall_m), float(tall_share), float(square_share)))
 
 
 # ---------------------------------------------------------------------------

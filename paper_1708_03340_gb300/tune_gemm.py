@@ -5,7 +5,7 @@ The library picks, per contraction launch, one of three tile shapes (64 x 64,
 (M >= tall_m) and "square" (M, N >= tall_m) items.  This script times the
 add + truncate step of representative workloads (CUDA-graph replays, FP32
 path) for every candidate (tall_m, tall_share, square_share), each in a fresh
-process with HTGB_TUNE set, and writes the fastest candidate (geometric mean
+process that sets it through ht_set_gemm_tuning, and writes the fastest candidate (geometric mean
 of the step times over the workloads) into csrc/gemm_tune.h together with a
 results table, gemm_tune_results.md.  The accuracy threshold kTuneCompLen is
 not tuned.
@@ -107,10 +107,9 @@ def worker(name, steps, warmup):
 
 
 def run_candidate(name, cand, steps, warmup):
-    env = dict(os.environ, HTGB_TUNE="%d,%g,%g" % cand)
     out = subprocess.run([sys.executable, "-m", "paper_1708_03340_gb300.tune_gemm", "--worker", name,
-                          "--steps", str(steps), "--warmup", str(warmup)],
-                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+                          "--steps", str(steps), "--warmup", str(warmup), "--cand", "%d,%g,%g" % cand],
+                         cwd=ROOT, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         raise RuntimeError(f"worker {name} {cand} failed:\n{out.stderr[-2000:]}")
     return json.loads(out.stdout.strip().splitlines()[-1])["ms"]
@@ -130,12 +129,17 @@ def write_header(best, path=HEADER):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--worker", default=None)
+    ap.add_argument("--cand", default=None, help="tall_m,tall_share,square_share (worker processes)")
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--no-write", action="store_true")
     ap.add_argument("--out", default=None, help="write gemm_tune.h and the results table here instead of in place")
     args = ap.parse_args()
     if args.worker:
+        if args.cand:
+            from paper_1708_03340_gb300 import htgb
+            m, a, b = args.cand.split(",")
+            htgb.ht_set_gemm_tuning(int(m), float(a), float(b))
         return worker(args.worker, args.steps, args.warmup)
     table = {}
     for cand in CANDIDATES:

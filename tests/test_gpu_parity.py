@@ -11,7 +11,7 @@ import pytest
 from oracle import oracle as O
 from paper_1708_03340_gb300 import htgb
 from paper_1708_03340_gb300 import inputs as I
-from tests.gpu_util import as_stored, check_ranks, check_sigma, gpu_sum, sample_idx, split_sigma
+from tests.gpu_util import as_stored, check_ranks, check_sigma, gpu_sum, noise_floor, sample_idx, split_sigma
 
 pytestmark = pytest.mark.gpu
 
@@ -125,12 +125,12 @@ def test_gramians(dtype):
         assert np.abs(lam - lam_ref).max() <= TOL[dtype] * lam_ref[0], t
 
 
-def _trunc_compare(d, n, a, c, dtype, opts, entries_tol_scale=10.0, floor=0.0):
+def _trunc_compare(d, n, a, c, dtype, opts, entries_tol_scale=10.0, floor=0.0, **kernel_opts):
     tree, A, C, X = gpu_sum(d, n, a, c, dtype)
     k, x = O.add(d, n, a[1], as_stored(a[2], dtype), c[1], as_stored(c[2], dtype))
-    ref = O.truncate(d, n, k, x, **opts)
+    ref = O.truncate(d, n, k, x, noise=noise_floor(d, dtype), **opts)
     prec = htgb.HT_PREC_FP64 if dtype == F64 else htgb.HT_PREC_FP32
-    rep = X.truncate(prec=prec, **opts)
+    rep = X.truncate(prec=prec, **opts, **kernel_opts)
     assert list(rep["korth"]) == list(ref["korth"])
     assert list(X.ranks()) == list(rep["ranks"])
     differ, energy = check_ranks(rep["ranks"], ref, TOL[dtype], opts.get("mode") == "eps", d, dtype)
@@ -251,13 +251,12 @@ def test_tensor_core_contractions_match_simt(case, monkeypatch):
 
 
 @pytest.mark.parametrize("case", ["big_rank", "rank128", "rank200"])
-def test_two_column_qr_kernel(case, monkeypatch):
+def test_two_column_qr_kernel(case):
     """The two-column TSQR block kernel (two blocks per SM, chosen for FP32
     launches of 64-column blocks with more blocks than SMs) forced onto every
-    such launch by HTGB_QR2=1: the oracle checks of the one-column kernel
-    (orthogonality, tensor unchanged, ||X||, then the truncation)."""
-    monkeypatch.setenv("HTGB_QR2", "1")
-    test_orthogonalize(F32, case)
+    such launch (qr_kernel = 2), then the one-column kernel forced everywhere
+    (qr_kernel = 1): both truncations against the oracle."""
     d, n, a, c = _case(case)
     r = {"big_rank": 30, "rank128": 64, "rank200": 100}[case]
-    _trunc_compare(d, n, a, c, F32, dict(mode="rank", rank_cap=r))
+    for qk in (2, 1):
+        _trunc_compare(d, n, a, c, F32, dict(mode="rank", rank_cap=r), qr_kernel=qk)

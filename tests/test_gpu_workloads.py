@@ -18,7 +18,8 @@ import pytest
 from oracle import oracle as O
 from paper_1708_03340_gb300 import htgb
 from paper_1708_03340_gb300 import inputs as I
-from tests.gpu_util import as_stored, check_ranks, check_sigma, fp32_tol, fp32_tol_sigma, gpu_sum, split_sigma
+from tests.gpu_util import (as_stored, check_ranks, check_sigma, fp32_tol, fp32_tol_sigma, gpu_sum, noise_floor,
+                            split_sigma)
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +31,7 @@ def single(request):
     dtype = request.param
     (n, ka, xa), (_, kc, xc) = I.single_pair(11)
     k, x = O.add(D, n, ka, as_stored(xa, dtype), kc, as_stored(xc, dtype))
-    ref = O.truncate(D, n, k, x, **I.SINGLE_OPTS)
+    ref = O.truncate(D, n, k, x, noise=noise_floor(D, dtype), **I.SINGLE_OPTS)
     return dtype, n, (n, ka, xa), (n, kc, xc), k, x, ref
 
 

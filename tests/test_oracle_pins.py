@@ -99,12 +99,35 @@ def _full(d, n, k, x):
     return F.frames(d, n, k, x)[1]
 
 
-def test_eval_matches_full_tensor():
-    (n, ka, xa), _ = I.brute_pair(3)
-    full = _full(4, n, ka, xa)
+@pytest.mark.parametrize("case", ["brute", "uneven"])
+def test_eval_matches_full_tensor(case):
+    """Sec. 3.1 (eq. "transfermult") against the full tensor built from the
+    definition of the transfer tensors (tests/fulltensor.py, numpy only).  The
+    uneven case has distinct mode sizes and unequal ranks of the two sons of
+    every node, so a swap of the sons' indices (j, l) of B_t, of two modes, or
+    of the parent index with a son's index changes the values."""
+    if case == "brute":
+        (n, k, x), _ = I.brute_pair(3)
+        d = 4
+    else:
+        d, n = 5, np.array([3, 4, 2, 5, 6])
+        tr = I.tree(d)
+        k = np.array([1] + [2 + (t % 3) for t in range(1, 2 * d - 1)], np.int32)
+        rng = np.random.default_rng(11)
+        nodes = []
+        for t in range(2 * d - 1):
+            if tr["son1"][t] < 0:
+                nodes.append(rng.standard_normal((int(n[tr["lo"][t]]), int(k[t]))))
+            else:
+                kt = 1 if t == 0 else int(k[t])
+                B = rng.standard_normal((kt, int(k[tr["son1"][t]]), int(k[tr["son2"][t]])))
+                nodes.append(B[0] if t == 0 else B)
+        x = I.nodes_blob(d, nodes)
+        assert any(k[tr["son1"][t]] != k[tr["son2"][t]] for t in range(2 * d - 1) if tr["son1"][t] >= 0)
+    full = F.frames(d, n, k, x)[1]
     rng = np.random.default_rng(0)
-    idx = np.stack([rng.integers(0, int(v), 50) for v in n], axis=1)
-    vals = O.eval_entries(4, n, ka, xa, idx)
+    idx = np.stack([rng.integers(0, int(v), 80) for v in n], axis=1)
+    vals = O.eval_entries(d, n, k, x, idx)
     ref = full[tuple(idx.T)]
     assert np.abs(vals - ref).max() < 1e-15 * np.abs(full).max() * 10
 
@@ -276,33 +299,61 @@ def test_eps_truncation_meets_eps():
 
 
 
-@pytest.mark.parametrize("seed,eps", [(5, 3e-1), (5, 1e-1), (7, 3e-2), (7, 1e-2), (2, 1e-3)])
-def test_eps_rank_rule_against_full_svds(seed, eps):
-    """The eps rank rule (the paper cites [Gr10] without stating it; reading:
-    r_t is the smallest r >= 1 whose tail sum_{i>r} (sigma_{t,i}^2 + nu_t)
-    fits (eps ||A||)^2 / (2d-3), nu_t = 4 sqrt(2d-1) 2^-53 sigma_{t,1}^2, the
-    root's two sons share the rank of the first) against singular values of
-    the full tensor's matricizations: a divisor of 2d-2 or 2d-1, or a cut one
-    place late, changes some rank in these cases.  (That the root pair's tail
-    is counted once is pinned by the discarded energy in the bounds test.)"""
-    (n, ka, xa), (_, kc, xc) = I.brute_pair(seed)
-    d = 4
-    k, x = O.add(d, n, ka, xa, kc, xc)
-    full = _full(d, n, k, x)
+def _eps_ranks_from_svds(d, full, korth, eps, noise):
+    """Ranks of the eps rule written out on the singular values of the full
+    tensor's matricizations: r_t = smallest r >= 1 with
+    sum_{i>r} (sigma_{t,i}^2 + nu_t) <= (eps ||A||)^2 / (2d-3), nu_t = noise sigma_{t,1}^2,
+    the root's second son taking the first son's rank."""
     budget = (eps * np.linalg.norm(full)) ** 2 / (2 * d - 3)
-    res = O.truncate(d, n, k, x, mode="eps", eps=eps, eps_relative=True)
     tr = I.tree(d)
     want = [1] * (2 * d - 1)
     for t in range(1, 2 * d - 1):
-        s = np.linalg.svd(F.matricization(full, tr["lo"][t], tr["hi"][t]), compute_uv=False)[: int(res["korth"][t])]
-        lam = s ** 2 + 4.0 * np.sqrt(2 * d - 1) * 2.0 ** -53 * s[0] ** 2
+        s = np.linalg.svd(F.matricization(full, tr["lo"][t], tr["hi"][t]), compute_uv=False)[: int(korth[t])]
+        lam = s ** 2 + noise * s[0] ** 2
         tails = [float(np.sum(lam[r:])) for r in range(len(lam) + 1)]
         # no tail within 1e-9 of the budget: the cut is decided by the reading, not by rounding
         assert all(abs(tl - budget) > 1e-9 * budget for tl in tails)
         want[t] = next(r for r in range(1, len(lam) + 1) if tails[r] <= budget)
     want[tr["son2"][0]] = want[tr["son1"][0]]
+    return want
+
+
+@pytest.mark.parametrize("seed,eps", [(5, 3e-1), (5, 1e-1), (7, 3e-2), (7, 1e-2), (2, 1e-3)])
+def test_eps_rank_rule_against_full_svds(seed, eps):
+    """The eps rank rule (the paper cites [Gr10] without stating it; reading:
+    r_t is the smallest r >= 1 whose tail sum_{i>r} sigma_{t,i}^2 fits
+    (eps ||A||)^2 / (2d-3), the root's two sons share the rank of the first)
+    against singular values of the full tensor's matricizations: a divisor of
+    2d-2 or 2d-1, or a cut one place late, changes some rank in these cases.
+    (That the root pair's tail is counted once is pinned by the discarded
+    energy in the bounds test.)"""
+    (n, ka, xa), (_, kc, xc) = I.brute_pair(seed)
+    d = 4
+    k, x = O.add(d, n, ka, xa, kc, xc)
+    full = F.frames(d, n, k, x)[1]
+    res = O.truncate(d, n, k, x, mode="eps", eps=eps, eps_relative=True)
+    want = _eps_ranks_from_svds(d, full, res["korth"], eps, 0.0)
     assert list(res["k"]) == want
     assert len(set(want[1:])) > 1  # the cases cut at different ranks per node
+
+
+@pytest.mark.parametrize("seed,eps,noise", [(7, 1e-2, 3e-6), (7, 3e-2, 1e-5), (5, 1e-1, 3e-4), (5, 3e-1, 3e-3)])
+def test_eps_rank_rule_noise_floor(seed, eps, noise):
+    """The rule with a charge nu_t = noise * sigma_{t,1}^2 per dropped
+    eigenvalue (the charge the FP32 paths apply: an eps below what their
+    arithmetic resolves keeps rank) against the full-tensor singular values.
+    In these cases the charge decides: the plain rule cuts lower at some node,
+    so an oracle that ignored the charge would fail."""
+    (n, ka, xa), (_, kc, xc) = I.brute_pair(seed)
+    d = 4
+    k, x = O.add(d, n, ka, xa, kc, xc)
+    full = F.frames(d, n, k, x)[1]
+    res = O.truncate(d, n, k, x, mode="eps", eps=eps, eps_relative=True, noise=noise)
+    want = _eps_ranks_from_svds(d, full, res["korth"], eps, noise)
+    plain = _eps_ranks_from_svds(d, full, res["korth"], eps, 0.0)
+    assert list(res["k"]) == want
+    assert want != plain and all(w >= p for w, p in zip(want, plain))
+
 
 def test_golden_diagonal_tensor():
     g = json.load(open(os.path.join(GOLDEN, "diag_d4.json")))
@@ -318,8 +369,10 @@ def test_golden_diagonal_tensor():
     assert list(res["k"][1:]) == [g["eps_rank"]] * 6
 
 
-def _full(d, n, k, x):
-    """All entries of an HT tensor by the oracle's evaluation (pinned above), C order."""
+def _full_by_eval(d, n, k, x):
+    """All entries of an HT tensor by the oracle's evaluation (pinned above
+    against the definition), C order.  Used only by the operator-application
+    pins below, whose operators live on index pairs."""
     n = np.broadcast_to(np.asarray(n, np.int64), (d,))
     idx = np.stack(np.meshgrid(*[np.arange(v) for v in n], indexing="ij"), axis=-1).reshape(-1, d)
     return O.eval_entries(d, n, k, x, idx).reshape(tuple(int(v) for v in n))
@@ -334,11 +387,11 @@ def test_operator_application_equals_full_matrix_vector():
     x = I.random_ht(d, n, 3, 32)
     kc, xc = O.apply(d, n, m, op[1], op[2], x[1], x[2])
     assert list(kc[1:]) == [2 * 3] * (2 * d - 2)
-    L = _full(d, m * n, op[1], op[2])          # L[(j1,i1), ..., (j4,i4)]
+    L = _full_by_eval(d, m * n, op[1], op[2])          # L[(j1,i1), ..., (j4,i4)]
     L = L.reshape(n, m, n, m, n, m, n, m)        # axis pair (i, j) from e = j + i m
-    X = _full(d, n, x[1], x[2])
+    X = _full_by_eval(d, n, x[1], x[2])
     C = np.einsum("aebfcgdh,abcd->efgh", L, X)   # axes (i1, j1, ..., i4, j4); C[j] = sum_i L[(j,i)] X[i]
-    got = _full(d, m, kc, xc)
+    got = _full_by_eval(d, m, kc, xc)
     assert np.abs(got - C).max() <= 1e-12 * np.abs(C).max()
 
 
