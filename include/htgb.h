@@ -66,8 +66,18 @@ typedef enum { HT_F64 = 0, HT_F32 = 1 } ht_dtype;
  * factor), so FP32 rounding perturbs the singular values by O(u_32 sigma_max)
  * instead of O(sqrt(u_32) sigma_max); the eps rule's noise floor becomes
  * (4 sqrt(2d-1) u_32)^2 sigma_{t,1}^2.  F32 tensors.  This is the direction
- * the paper's conclusion names for avoiding B^T B products. */
-typedef enum { HT_PREC_FP64 = 0, HT_PREC_FP32 = 1, HT_PREC_FP32_SQRT = 2 } ht_prec;
+ * the paper's conclusion names for avoiding B^T B products.
+ * HT_PREC_MIXED: F64 tensors; the R-factor QRs (Sec. 3.4) and the Gramian
+ * eigendecompositions stay in FP64, and every dense contraction (mode products
+ * of Lemma "transfer tensor transformation", Gramian contractions of eqs.
+ * "acctransferSon1/2", leaf products, TSQR recombination) runs on the tcgen05
+ * tensor cores: each FP64 operand row is put on a common fixed-point grid and
+ * cut into 5 BF16 slices of 8 bits, the slice products with index sum <= 4 are
+ * accumulated in FP32 (exactly for the leading ones, over chunks of at most
+ * 256 products) and the chunks are summed in FP64.  Per product about 2^-40
+ * of |a| |b| (normwise), against 2^-53 for FP64 and 2^-24 for FP32; the eps
+ * rule is the FP64 one (nu_t = 0). */
+typedef enum { HT_PREC_FP64 = 0, HT_PREC_FP32 = 1, HT_PREC_FP32_SQRT = 2, HT_PREC_MIXED = 3 } ht_prec;
 
 typedef enum { HT_TRUNC_RANK = 0, HT_TRUNC_EPS = 1 } ht_trunc_mode;
 
@@ -87,7 +97,8 @@ typedef enum { HT_SCHED_LEVEL = 0, HT_SCHED_NODE = 1 } ht_schedule;
  *         an FP32-computed Gramian: an eps below what that arithmetic resolves
  *         keeps rank.  The two sons of the root have the same singular values
  *         and share one rank (decided on the first son).
- *  prec: HT_PREC_FP64 needs an F64 tensor, HT_PREC_FP32 an F32 tensor.
+ *  prec: HT_PREC_FP64 and HT_PREC_MIXED need an F64 tensor, HT_PREC_FP32 and
+ *         HT_PREC_FP32_SQRT an F32 tensor.
  *  tensor_caps: NULL, or (batch calls) one rank cap per tensor, host array of
  *         count entries, used instead of rank_cap for that tensor. */
 typedef struct {

@@ -247,8 +247,8 @@ struct Launch {
   bool split = false;
   int node = -1;
   double flops = 0.0;  // algorithmic flops of the launch (literal, i.e. maximal, dims)
-  int tc_tiles = 0;    // GEMM: tiles of the tensor-core kernel
-  double tc_flops = 0.0;  // flops of items whose shape suits 128-row tensor-core tiles
+  int tc_tiles = 0;    // GEMM: tiles of the tensor-core kernel (mixed path)
+  int oz_split = 0;    // GEMM: CTAs of the tensor-core path's split launch
   const void *ranks = nullptr;  // tagged pointer to the rank array used by the launch
   void *scratch = nullptr;      // eig scratch (tagged)
   int variant = 0;              // GEMM: SIMT tile shape (gemm_tile_shape)
@@ -262,13 +262,11 @@ inline P *tagp(uint64_t tag, size_t off) {
   return reinterpret_cast<P *>(tag | (uint64_t)off);
 }
 
-// The tensor-core contraction kernel (k_tc.cu) runs the FP32 contractions
-// when HTGB_TC=1 (opt-in; see the kernel's header for its precision).
-bool tc_enabled() {
-  const char *v = getenv("HTGB_TC");
-  return v && v[0] == '1';
-}
-constexpr int kTcMaxK = 512;  // products one tensor-core CTA accumulates in TMEM
+// Mixed path: products per exactness chunk of the tensor-core kernel (k_oz.cu)
+// and its default number of BF16 slices per FP64 operand (5 slices: about
+// 2^-40 of the row scale per product).
+constexpr int kOzChunk = 256;
+constexpr int kOzSlices = 5;
 
 struct Plan {
   std::vector<uint8_t> items;
@@ -277,6 +275,8 @@ struct Plan {
   size_t p_bytes = 0, s_bytes = 0, s_peak = 0;
   bool node_sched = false;
   bool sqrt_gram = false;  // Gramians from square-root factors (HT_PREC_FP32_SQRT)
+  bool mixed = false;      // HT_PREC_MIXED: contractions on the tensor cores (k_oz.cu)
+  int oz_slices = kOzSlices;
   int qr_kernel = 0;       // TSQR block kernel choice (ht_trunc_opts.qr_kernel)
   int dtype = HT_F64;
   size_t esz = 8;
@@ -352,7 +352,7 @@ struct Plan {
       if (oa >= (int64_t)INT32_MAX || ob >= (int64_t)INT32_MAX)
         err = "contraction operand spans 2^31 elements or more within one tile row/column";
     }
-    if (dtype == HT_F32 && g.M < 128 && g.N >= 128 && g.m_ref < 0 && g.n_ref < 0) {
+    if ((dtype == HT_F32 || mixed) && g.M < 128 && g.N >= 128 && g.m_ref < 0 && g.n_ref < 0) {
       // C^T = B^T A^T puts the long dimension on the 128-row MMA tiles
       std::swap(g.A, g.B);
       const int64_t am = g.sam, ak = g.sak, ako = g.sako, ab = g.sab;
@@ -361,17 +361,19 @@ struct Plan {
       std::swap(g.scm, g.scn);
       std::swap(g.M, g.N);
     }
-    if (dtype == HT_F32 && tc_enabled()) {
-      // the tensor-core kernel accumulates a CTA's whole reduction in TMEM (FP32):
-      // keep it at most kTcMaxK products by splitting the outer range across CTAs
-      const int64_t red = (int64_t)g.K * g.Ko;
-      if (g.K <= kTcMaxK && red > (int64_t)kTcMaxK * g.ksplit)
-        g.ksplit = (int)std::min<int64_t>(g.Ko, (red + kTcMaxK - 1) / kTcMaxK);
+    if (mixed) {
+      // exactness chunks of at most kOzChunk products: split the outer range
+      if (g.K > kOzChunk) {
+        err = "mixed path: a contraction with more than " + std::to_string(kOzChunk) + " products per outer index";
+        return;
+      }
+      const int per = std::max(1, kOzChunk / g.K);
+      g.ksplit = std::max(g.ksplit, (g.Ko + per - 1) / per);
     }
     g.tiles_m = (g.M + 63) / 64;
     g.tiles_n = (g.N + 63) / 64;
     g.tc_tiles_m = (g.M + 127) / 128;
-    g.tc_tiles_n = (g.N + 63) / 64;
+    g.tc_tiles_n = (g.N + 127) / 128;
     if (node_sched && cur().n > 0 && cur().node != node) {
       LKind k = cur().kind;
       const void *r = cur().ranks;
@@ -384,9 +386,21 @@ struct Plan {
     L.tiles += g.tiles_m * g.tiles_n * g.batch * g.ksplit;
     g.tc_tile0 = L.tc_tiles;
     L.tc_tiles += g.tc_tiles_m * g.tc_tiles_n * g.batch * g.ksplit;
+    if (mixed) {
+      // BF16 slice blocks (stages of oz_stage_k() reduction indices) and exponents
+      const int max_ko = (g.Ko + g.ksplit - 1) / g.ksplit;
+      const int sk = oz_stage_k();
+      g.oz_stages = (g.K * max_ko + sk - 1) / sk;
+      const size_t blk = (size_t)oz_block_bytes() * oz_slices * g.oz_stages * g.ksplit * g.batch;
+      g.oza = salloc_bytes(blk * g.tc_tiles_m);
+      g.ozb = salloc_bytes(blk * g.tc_tiles_n);
+      g.oea = static_cast<int *>(salloc_bytes(sizeof(int) * (size_t)g.batch * g.tc_tiles_m * oz_tile_m() * g.ksplit));
+      g.oeb = static_cast<int *>(salloc_bytes(sizeof(int) * (size_t)g.batch * g.tc_tiles_n * oz_tile_n() * g.ksplit));
+      g.oz_split0 = L.oz_split;
+      L.oz_split += g.batch * g.ksplit * (g.tc_tiles_m + g.tc_tiles_n);
+    }
     const double fl = 2.0 * g.M * g.N * (double)g.K * g.Ko * g.batch;
     L.flops += fl;
-    if (g.M >= 128) L.tc_flops += fl;
     if (g.ksplit > 1) {
       L.split = true;
       g.part = salloc_bytes((size_t)g.ksplit * g.batch * g.M * g.N * (L.df ? sizeof(double) : esz));
@@ -431,6 +445,10 @@ void reloc_items<GemmItem>(uint8_t *base, int n, char *pb, char *sb, char *mb) {
     it[i].B = reloc(it[i].B, pb, sb, mb);
     it[i].C = reloc(it[i].C, pb, sb, mb);
     it[i].part = reloc(it[i].part, pb, sb, mb);
+    it[i].oza = reloc(it[i].oza, pb, sb, mb);
+    it[i].ozb = reloc(it[i].ozb, pb, sb, mb);
+    it[i].oea = static_cast<int *>(reloc(it[i].oea, pb, sb, mb));
+    it[i].oeb = static_cast<int *>(reloc(it[i].oeb, pb, sb, mb));
   }
 }
 template <>
@@ -640,12 +658,14 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
     prof_begin((int)L.kind, s);
     switch (L.kind) {
       case L_GEMM: {
-        // FP32 launches whose flops sit mostly in tall items run on the tensor cores
-        const bool tc = !f64 && tc_enabled() && L.tc_flops >= 0.5 * L.flops;
-        e = f64 ? launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s, L.variant, false,
-                                      false, L.uniform)
-                : launch_gemm<float>((const GemmItem *)items, L.n, L.tiles, rk, L.split,
-                                     (tc && !L.df) ? L.tc_tiles : 0, s, L.variant, L.comp, L.df, L.uniform);
+        if (P.mixed)
+          e = launch_gemm_oz((const GemmItem *)items, L.n, L.oz_split, L.tc_tiles, rk, L.split, P.oz_slices, s);
+        else if (f64)
+          e = launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s, L.variant, false, false,
+                                  L.uniform);
+        else
+          e = launch_gemm<float>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s, L.variant, L.comp, L.df,
+                                 L.uniform);
         break;
       }
       case L_QR:
@@ -1941,11 +1961,11 @@ void *plan_inner(Plan &P, const ht_tensor *x, const ht_tensor *y) {
 }
 
 ht_status check_prec(const ht_tensor *x, int prec) {
-  if (prec == HT_PREC_FP64 && x->dtype != HT_F64)
-    return fail(HT_EUNSUPPORTED, "HT_PREC_FP64 needs an HT_F64 tensor");
+  if ((prec == HT_PREC_FP64 || prec == HT_PREC_MIXED) && x->dtype != HT_F64)
+    return fail(HT_EUNSUPPORTED, "HT_PREC_FP64 and HT_PREC_MIXED need an HT_F64 tensor");
   if ((prec == HT_PREC_FP32 || prec == HT_PREC_FP32_SQRT) && x->dtype != HT_F32)
     return fail(HT_EUNSUPPORTED, "HT_PREC_FP32 and HT_PREC_FP32_SQRT need an HT_F32 tensor");
-  if (prec != HT_PREC_FP64 && prec != HT_PREC_FP32 && prec != HT_PREC_FP32_SQRT)
+  if (prec != HT_PREC_FP64 && prec != HT_PREC_FP32 && prec != HT_PREC_FP32_SQRT && prec != HT_PREC_MIXED)
     return fail(HT_EINVAL, "unknown precision");
   return HT_OK;
 }
@@ -1998,12 +2018,12 @@ ht_status ht_profile_read(int kind, int64_t *launches, double *total_ms, double 
 ht_status ht_device_status(void) {
   const cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(HT_ECUDA, cudaGetErrorString(e));
-  const int t = tc_take_wait_error();
+  const unsigned t = oz_take_status();
   const unsigned w = wait_take_status();
   const unsigned q = eig_take_status();
   const unsigned m = misc_take_status();
-  if (t < 0 || w == ~0u || q == ~0u || m == ~0u) return fail(HT_ECUDA, "reading a device status word failed");
-  if (t) return fail(HT_ETIMEOUT, "a tcgen05 contraction's bounded wait gave up");
+  if (t == ~0u || w == ~0u || q == ~0u || m == ~0u) return fail(HT_ECUDA, "reading a device status word failed");
+  if (t) return fail(HT_ETIMEOUT, "a bounded wait of the tensor-core contraction gave up (its results are NaN)");
   if (w) return fail(HT_ETIMEOUT, "a bounded device-side wait gave up");
   if (q) return fail(HT_ENUMERIC, "an eigensolver sweep reached its iteration limit");
   if (m) return fail(HT_ENUMERIC, "||X|| or a Gramian eigenvalue was not finite (NaN or Inf in the input)");
@@ -2363,6 +2383,7 @@ ht_status ht_orthogonalize(ht_tensor *x, int prec) {
   Plan P;
   P.dtype = x->dtype;
   P.esz = x->esz;
+  P.mixed = (prec == HT_PREC_MIXED);
   std::vector<TState> TS(1);
   TS[0].x = x;
   plan_orthogonalize(P, TS);
@@ -2378,6 +2399,7 @@ ht_status ht_gramians(ht_tensor *x, double *dev_out, int prec) {
   HT_TRY(sync_ranks(x));
   Plan P;
   P.sqrt_gram = (prec == HT_PREC_FP32_SQRT);
+  P.mixed = (prec == HT_PREC_MIXED);
   P.dtype = x->dtype;
   P.esz = x->esz;
   std::vector<TState> TS(1);
@@ -2435,6 +2457,7 @@ ht_status ht_gramians_noalloc(ht_tensor *x, double *dev_out, int prec) {
   HT_TRY(sync_ranks(x));
   Plan P;
   P.sqrt_gram = (prec == HT_PREC_FP32_SQRT);
+  P.mixed = (prec == HT_PREC_MIXED);
   P.dtype = x->dtype;
   P.esz = x->esz;
   std::vector<TState> TS(1);
@@ -2464,6 +2487,7 @@ static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_o
   P.esz = (dtype == HT_F64) ? 8 : 4;
   P.node_sched = (o->schedule == HT_SCHED_NODE);
   P.sqrt_gram = (o->prec == HT_PREC_FP32_SQRT);
+  P.mixed = (o->prec == HT_PREC_MIXED);
   P.qr_kernel = o->qr_kernel;
   std::vector<TState> TS(count);
   int total_nodes = 0;
@@ -2606,6 +2630,7 @@ ht_status ht_graph_add_truncate(const ht_tensor *const *a, const ht_tensor *cons
   P.esz = (P.dtype == HT_F64) ? 8 : 4;
   P.node_sched = (o->schedule == HT_SCHED_NODE);
   P.sqrt_gram = (o->prec == HT_PREC_FP32_SQRT);
+  P.mixed = (o->prec == HT_PREC_MIXED);
   P.qr_kernel = o->qr_kernel;
   std::vector<TState> TS(count);
   int total_nodes = 0;

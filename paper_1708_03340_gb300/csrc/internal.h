@@ -36,8 +36,14 @@ struct GemmItem {
   double alpha, beta;
   int tiles_m, tiles_n;  // tile grid at the literal (maximal) dims
   int tile0;             // first global tile index of this item
-  int tc_tiles_m, tc_tiles_n, tc_tile0;  // same for the tensor-core kernel's 128 x 64 tiles
+  int tc_tiles_m, tc_tiles_n, tc_tile0;  // same for the tensor-core kernel's 128 x 128 tiles (k_oz.cu)
   int64_t k_total;  // >= 0: only flat reduction indices ko * K + k < k_total take part (ragged last chunk)
+  // tensor-core path (k_oz.cu): BF16 slices of A and B in 8 KB stage blocks,
+  // per-(row, chunk) exponents, stages per chunk, first CTA of the split launch
+  void *oza, *ozb;
+  int *oea, *oeb;
+  int oz_stages;
+  int oz_split0;
 };
 
 // Householder QR of one row block (m >= n) held in shared memory.
@@ -117,7 +123,6 @@ struct RankItem {
 // ---------------------------------------------------------------------------
 // launchers (stream-ordered; return cudaGetLastError())
 // ---------------------------------------------------------------------------
-// tc_tiles > 0: run the FP32 items on the tcgen05 kernel (k_tc.cu) with that many tiles
 // variant: SIMT tile shape (0: 64 x 64, 1: 128 x 64, 2: 128 x 128, the last
 // without compensation only); items' tiles_m / tiles_n / tile0 must be laid
 // out for that shape (gemm_tile_shape).  comp: Kahan-compensated FP32
@@ -129,7 +134,20 @@ cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, c
                         bool any_split, int tc_tiles, cudaStream_t s, int variant, bool comp, bool df,
                         int uniform = 0);
 void gemm_tile_shape(int variant, int *bm, int *bn);
-cudaError_t launch_gemm_tc(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, cudaStream_t s);
+// Split-K partial sums of FP64 items added in chunk order (k_gemm.cu).
+cudaError_t launch_gemm_reduce_f64(const GemmItem *d_items, int n_items, const int *d_ranks, cudaStream_t s);
+// FP64 contractions on the tensor cores by exact BF16 slicing (k_oz.cu): the
+// split launch (split_blocks CTAs) then the GEMM launch (tiles CTAs of
+// oz_tile_m() x oz_tile_n()), then the split-K reduction if any_split.  Every
+// item needs K * ceil(Ko / ksplit) <= 256 (products per exactness chunk),
+// slices in [2, 6].
+cudaError_t launch_gemm_oz(const GemmItem *d_items, int n_items, int split_blocks, int tiles, const int *d_ranks,
+                           bool any_split, int slices, cudaStream_t s);
+int oz_tile_m();
+int oz_tile_n();
+int oz_stage_k();
+int oz_block_bytes();
+unsigned oz_take_status();  // bit 0: a bounded wait of the tensor-core kernel gave up (read and clear)
 // qr_kernel: 0 picks the block kernel by shape and launch size; 1 forces the
 // one-column kernel, 2 the two-column kernel (FP32, 64-column blocks).
 template <typename T>
@@ -159,10 +177,6 @@ cudaError_t launch_sumsq(const void *x, int64_t count, double *out, cudaStream_t
 template <typename T>
 cudaError_t launch_scale(void *x, int64_t count, double alpha, cudaStream_t s);
 
-// Device error word of the kernel with bounded waits (tcgen05 contraction):
-// read and clear; 1 if a wait gave up since the last call, 0 if not, -1 if
-// the read failed.  Synchronises the device (symbol copies).
-int tc_take_wait_error();
 // Status words of the eigensolvers (bit 0: a QL sweep hit its iteration
 // limit) and of the rank selection (bit 0: a non-finite norm or eigenvalue):
 // read and clear; ~0u if the read failed.  Synchronise the device.

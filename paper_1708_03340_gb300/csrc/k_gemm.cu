@@ -406,10 +406,8 @@ template <typename T>
 cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, const int *d_ranks, bool any_split,
                         int tc_tiles, cudaStream_t s, int variant, bool comp, bool df, int uniform) {
   if (n_items <= 0 || total_tiles <= 0) return cudaSuccess;
-  if (sizeof(T) == 4 && tc_tiles > 0) {
-    cudaError_t e = launch_gemm_tc(d_items, n_items, tc_tiles, d_ranks, s);
-    if (e != cudaSuccess) return e;
-  } else {
+  (void)tc_tiles;
+  {
     // Kahan compensation only for FP32 launches with long per-CTA reductions;
     // double-float accumulation (FP64 output) when asked for
     const bool c = (sizeof(T) == 4) && comp;
@@ -443,6 +441,15 @@ template cudaError_t launch_gemm<double>(const GemmItem *, int, int, const int *
                                          bool, int);
 template cudaError_t launch_gemm<float>(const GemmItem *, int, int, const int *, bool, int, cudaStream_t, int, bool,
                                        bool, int);
+
+cudaError_t launch_gemm_reduce_f64(const GemmItem *d_items, int n_items, const int *d_ranks, cudaStream_t s) {
+  for (int base = 0; base < n_items; base += 65535) {
+    const int cnt = n_items - base < 65535 ? n_items - base : 65535;
+    gemm_reduce_kernel<double><<<dim3(64, cnt), 256, 0, s>>>(d_items + base, d_ranks);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
 
 void gemm_tile_shape(int variant, int *bm, int *bn) {
   *bm = (variant >= 1) ? 128 : 64;

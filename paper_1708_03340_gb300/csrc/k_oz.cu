@@ -1,0 +1,542 @@
+// k_oz.cu -- strided batched contractions of FP64 data on the 5th-generation
+// tensor cores (tcgen05, sm_103a) by exact fixed-point slicing.  Same work
+// items and semantics as the SIMT kernel (k_gemm.cu): the transfer-tensor
+// mode products of Lemma "transfer tensor transformation" (R-apply of Sec. 3.4,
+// projection of eq. "transfertransformationtrunc"), the reduced-Gramian
+// contractions of eqs. "acctransferSon1/2", the leaf products and the TSQR
+// recombination.  Used by the mixed-precision path (F64 storage, FP64 QR and
+// eigensolves, contractions here).
+//
+// Arithmetic (the splitting idea of Ozaki et al., "Error-free transformations
+// of matrix multiplication", written here for BF16 tensor-core operands):
+//   * Every operand row (a row of A, a column of B) of one reduction chunk of at
+//     most kOzChunk products is put on a common grid: with E the exponent of the
+//     row's largest magnitude (|x| < 2^E), X = x 2^-E lies in (-1, 1) and is
+//     rounded to an integer F = round(|X| 2^(8S)) < 2^(8S) + 1.
+//   * F is cut into S signed base-256 digits, F = sum_i d_i 256^(S-1-i), with
+//     d_0 in [0, 256] and d_i in [-128, 127] for i > 0 (balanced digits), and
+//     slice i of x is sign(x) d_i 2^(-8(i+1)).  Every slice is an integer of at
+//     most 9 significant bits times a power of two: a BF16 value, exactly.
+//   * The tensor core multiplies BF16 slices exactly (16-bit products) and
+//     accumulates in FP32.  Products of slices i and j sit on the grid
+//     2^(-8(i+j+2)); summed over <= 256 reduction indices, the diagonals
+//     i+j = 0 (|d_0 d_0'| <= 2^16) and i+j = 1 (<= 2^16 per index) stay below
+//     2^24 grid units, i.e. their FP32 sums are exact whatever the order of
+//     the additions; i+j = 2 rounds at most at 2^-24 of its own size, which is
+//     2^-40 of the result's scale, and all products with i+j >= 3 share a
+//     fourth accumulator (rounding at about 2^-48 of the scale).
+//   * Products with i+j >= S are dropped; with the rounding of F this leaves a
+//     normwise error of about 2^-(8S) |A| |B| per product: S = 5 gives about
+//     2^-40 of the row scale, far below what the 1e-6 results of the mixed
+//     path need and well beyond FP32 (2^-24).
+//   * The four accumulators are read from TMEM, summed in FP64, scaled by
+//     2^(E_row + E_col) and written (or written as a split-K partial; the
+//     chunks of a long reduction are added in FP64 by the reduction kernel of
+//     k_gemm.cu).
+//
+// Kernels:
+//   oz_split_kernel  one CTA per (item, operand, batch, 128-row tile, chunk):
+//                    pass 1 finds every row's exponent, pass 2 writes the S
+//                    BF16 slices straight into the tensor core's canonical
+//                    no-swizzle K-major shared-memory layout (core matrices of
+//                    8 rows x 16 bytes), one 8 KB block per slice and 32-wide
+//                    reduction stage, so that the GEMM fetches a stage of all
+//                    slices with one bulk copy per operand.
+//   oz_gemm_kernel   one CTA per 128 x 128 output tile and chunk, 192 threads:
+//                    warp 4 issues the bulk copies (cp.async.bulk, mbarrier
+//                    transaction counts) into two stage buffers, one thread of
+//                    warp 5 issues the MMAs (tcgen05.mma kind::f16, BF16 x
+//                    BF16 -> FP32, M = N = 128, K = 16) into four accumulators
+//                    of 128 TMEM columns each and commits each stage's MMAs to
+//                    that buffer's "empty" barrier, and warps 0-3 (TMEM lanes
+//                    0-127) read the accumulators with tcgen05.ld once all
+//                    MMAs have committed.  Every mbarrier wait is bounded by
+//                    time (wait.cuh); one that gives up sets g_oz_status, lets
+//                    the issued MMAs finish (bounded) before the TMEM is freed,
+//                    writes NaN in place of its results and returns.
+#include <stdint.h>
+
+#include "internal.h"
+#include "wait.cuh"
+
+namespace htgb {
+
+// Status word of this file's bounded waits: bit 0 set when a wait gave up.
+__device__ unsigned g_oz_status = 0;
+
+namespace {
+
+constexpr int OZ_M = 128;                       // rows of a tile (MMA M); also the rows of one split block
+constexpr int OZ_N = 128;                       // columns of a tile (MMA N)
+constexpr int OZ_KC = 32;                       // reduction indices per stage
+constexpr uint32_t OZ_BLK = OZ_M * OZ_KC * 2;   // bytes of one slice block of one stage (8 KB)
+constexpr int OZ_THREADS = 192;                 // warps 0-3 epilogue, 4 producer, 5 MMA
+constexpr int OZ_TMEM_COLS = 512;               // four FP32 accumulators of 128 columns
+constexpr int OZ_EXP_NONFINITE = 0x7FF0;        // exponent marking a row with NaN / Inf
+
+__device__ __forceinline__ int eff_dim(int lit, int ref, int mult, const int *ranks) {
+  if (ref < 0) return lit;
+  int v = ranks[ref] * mult;
+  return v < lit ? v : lit;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of element (row, k) of a 128 x 32 BF16 block: core matrix
+// (row / 8, k / 8) of 8 rows x 16 bytes at ((row / 8) * 4 + k / 8) * 128
+__device__ __forceinline__ uint32_t oz_off(int row, int k) {
+  return ((uint32_t)(row >> 3) * (OZ_KC / 8) + (uint32_t)(k >> 3)) * 128u + (uint32_t)(row & 7) * 16u +
+         (uint32_t)(k & 7) * 2u;
+}
+
+// shared memory matrix descriptor of a K-major no-swizzle operand: start
+// address, leading-dimension byte offset (next core matrix along K: 128 B),
+// stride-dimension byte offset (next 8-row group: 4 core matrices = 512 B),
+// descriptor version 1 at bit 46
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  const uint64_t lbo = 128, sbo = (OZ_KC / 8) * 128;
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D = F32 (1 << 4), A = B = BF16 (1 << 7,
+// 1 << 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((int64_t)(globaltimer_ns() - t0) > kWaitLimitNs) return false;
+  }
+}
+
+// Chunk c of an item: reduction indices [f0, f1) of the flat index ko * K + k.
+__device__ __forceinline__ void chunk_range(const GemmItem &it, int chunk, int64_t &f0, int64_t &f1) {
+  const int ko0 = (int)((int64_t)chunk * it.Ko / it.ksplit);
+  const int ko1 = (int)((int64_t)(chunk + 1) * it.Ko / it.ksplit);
+  f0 = (int64_t)ko0 * it.K;
+  f1 = (int64_t)ko1 * it.K;
+  if (it.k_total >= 0 && f1 > it.k_total) f1 = it.k_total;
+  if (f1 < f0) f1 = f0;
+}
+
+// Balanced base-256 digits of x on the grid of exponent E (|x| < 2^E):
+// F = round(|x| 2^(8S - E)), F = sum_i d_i 256^(S-1-i), d_0 in [0, 256],
+// d_i in [-128, 127]; the digits carry the sign of x.  Integer operations
+// only (no FP64 arithmetic).  Zeros and subnormals give zero digits.
+template <int S>
+__device__ __forceinline__ void oz_digits(double x, int E, int (&d)[S]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned long long F = 0;
+  if (ex != 0) {
+    const int sh = 1075 + E - ex - 8 * S;  // |x| 2^(8S - E) = mant 2^(-sh)
+    if (sh <= 0) F = mant << (-sh);         // only for S = 7 (then -sh <= 3)
+    else if (sh < 60) F = (mant + (1ull << (sh - 1))) >> sh;
+  }
+#pragma unroll
+  for (int i = S - 1; i >= 1; --i) {
+    int t = (int)(F & 255ull);
+    F >>= 8;
+    if (t >= 128) {
+      t -= 256;
+      F += 1;
+    }
+    d[i] = t;
+  }
+  d[0] = (int)F;
+  if (bits >> 63) {
+#pragma unroll
+    for (int i = 0; i < S; ++i) d[i] = -d[i];
+  }
+}
+
+// BF16 bits of d 2^(-8(i+1)) (|d| <= 256: exact)
+__device__ __forceinline__ uint32_t slice_bf16(int d, int i) {
+  const float f = (float)d * __uint_as_float((uint32_t)(127 - 8 * (i + 1)) << 23);
+  return __float_as_uint(f) >> 16;
+}
+
+__device__ __forceinline__ int find_split(const GemmItem *items, int n, int blk) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (items[mid].oz_split0 <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int find_tile(const GemmItem *items, int n, int tile) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (items[mid].tc_tile0 <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// split: one CTA (256 threads) per (item, operand, batch, 128-row tile, chunk)
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restrict__ items, int n_items,
+                                                       const int *__restrict__ ranks) {
+  __shared__ double red[2][OZ_M];
+  __shared__ int sexp[OZ_M];
+  const GemmItem &it = items[find_split(items, n_items, blockIdx.x)];
+  int local = blockIdx.x - it.oz_split0;
+  const int per_a = it.batch * it.tc_tiles_m * it.ksplit;
+  const int op = local < per_a ? 0 : 1;
+  if (op) local -= per_a;
+  const int tiles = op ? it.tc_tiles_n : it.tc_tiles_m;
+  const int tile = local % tiles;
+  local /= tiles;
+  const int chunk = local % it.ksplit;
+  const int b = local / it.ksplit;
+  const int rows = op ? eff_dim(it.N, it.n_ref, it.n_mult, ranks) : eff_dim(it.M, it.m_ref, 1, ranks);
+  const int batch = eff_dim(it.batch, it.b_ref, it.b_mult, ranks);
+  if (b >= batch) return;  // the GEMM skips these batches as well
+  const double *X = static_cast<const double *>(op ? it.B : it.A) + (int64_t)b * (op ? it.sbb : it.sab);
+  const int64_t sr = op ? it.sbn : it.sam, sk = op ? it.sbk : it.sak, sko = op ? it.sbko : it.sako;
+  int64_t f0, f1;
+  chunk_range(it, chunk, f0, f1);
+  const int K = it.K;
+  const int tid = threadIdx.x;
+  const int r = tid & (OZ_M - 1), h = tid >> 7;
+  const int grow = tile * OZ_M + r;
+  const bool row_in = grow < rows;
+  auto elem = [&](int64_t f) -> double {
+    const int64_t ko = f / K, k = f - ko * K;
+    return X[(int64_t)grow * sr + k * sk + ko * sko];
+  };
+  // pass 1: largest magnitude of the row over the chunk (NaN / Inf flagged)
+  double m = 0.0;
+  bool bad = false;
+  if (row_in) {
+    for (int64_t f = f0 + h; f < f1; f += 2) {
+      const double v = fabs(elem(f));
+      if (!(v <= 1.7976931348623157e308)) bad = true;
+      m = v > m ? v : m;
+    }
+  }
+  red[h][r] = bad ? -1.0 : m;
+  __syncthreads();
+  if (h == 0) {
+    const double a = red[0][r], c = red[1][r];
+    int E = 0;
+    if (a < 0.0 || c < 0.0) {
+      E = OZ_EXP_NONFINITE;
+    } else {
+      const double mx = a > c ? a : c;
+      const int ex = (int)(((unsigned long long)__double_as_longlong(mx) >> 52) & 0x7FF);
+      E = ex ? ex - 1022 : 0;  // mx = 1.f 2^(ex-1023) < 2^(ex-1022); zero / subnormal rows: digits 0
+    }
+    sexp[r] = E;
+    int *Ex = op ? it.oeb : it.oea;
+    Ex[((int64_t)b * tiles * OZ_M + grow) * it.ksplit + chunk] = E;
+  }
+  __syncthreads();
+  const int E = sexp[r];
+  // pass 2: slices, 8 reduction indices of one row per step (16 bytes per slice)
+  const int nst = it.oz_stages;
+  unsigned char *out = static_cast<unsigned char *>(op ? it.ozb : it.oza) +
+                       ((((int64_t)b * tiles + tile) * it.ksplit + chunk) * nst) * S * (int64_t)OZ_BLK;
+  for (int g = h; g < nst * (OZ_KC / 8); g += 2) {
+    const int q = g / (OZ_KC / 8), kk0 = (g % (OZ_KC / 8)) * 8;
+    uint32_t w[S][4];
+#pragma unroll
+    for (int i = 0; i < S; ++i) w[i][0] = w[i][1] = w[i][2] = w[i][3] = 0u;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int64_t f = f0 + (int64_t)q * OZ_KC + kk0 + e;
+      double v = 0.0;
+      if (row_in && f < f1 && E != OZ_EXP_NONFINITE) v = elem(f);
+      int d[S];
+      oz_digits<S>(v, E, d);
+#pragma unroll
+      for (int i = 0; i < S; ++i) w[i][e >> 1] |= slice_bf16(d[i], i) << ((e & 1) * 16);
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+      *reinterpret_cast<uint4 *>(out + ((int64_t)q * S + i) * OZ_BLK + oz_off(r, kk0)) =
+          make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GEMM: one CTA per (item, 128-row tile, 128-column tile, batch, chunk)
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *__restrict__ items, int n_items,
+                                                                const int *__restrict__ ranks) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_acc;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const GemmItem &it = items[find_tile(items, n_items, blockIdx.x)];
+  int local = blockIdx.x - it.tc_tile0;
+  const int tm = local % it.tc_tiles_m;
+  local /= it.tc_tiles_m;
+  const int tn = local % it.tc_tiles_n;
+  local /= it.tc_tiles_n;
+  const int b = local % it.batch;
+  const int chunk = local / it.batch;
+  const int M = eff_dim(it.M, it.m_ref, 1, ranks);
+  const int N = eff_dim(it.N, it.n_ref, it.n_mult, ranks);
+  const int batch = eff_dim(it.batch, it.b_ref, it.b_mult, ranks);
+  const int m0 = tm * OZ_M, n0 = tn * OZ_N;
+  if (m0 >= M || n0 >= N || b >= batch) return;  // uniform for the CTA, before any TMEM is held
+  int64_t f0, f1;
+  chunk_range(it, chunk, f0, f1);
+  const int nq = (int)((f1 - f0 + OZ_KC - 1) / OZ_KC);  // stages holding data
+  const int nst = it.oz_stages;
+  constexpr uint32_t OPB = S * OZ_BLK;  // bytes of one operand's stage (all slices)
+  const unsigned char *gA = static_cast<const unsigned char *>(it.oza) +
+                            ((((int64_t)b * it.tc_tiles_m + tm) * it.ksplit + chunk) * nst) * (int64_t)OPB;
+  const unsigned char *gB = static_cast<const unsigned char *>(it.ozb) +
+                            ((((int64_t)b * it.tc_tiles_n + tn) * it.ksplit + chunk) * nst) * (int64_t)OPB;
+  const uint32_t full0 = smem_addr(&bar_full[0]), full1 = smem_addr(&bar_full[1]);
+  const uint32_t empty0 = smem_addr(&bar_empty[0]), empty1 = smem_addr(&bar_empty[1]);
+  const uint32_t accb = smem_addr(&bar_acc);
+
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 128) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(accb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 4) {
+    // ---- producer: one bulk copy per operand and stage ----
+    if (lane == 0) {
+      for (int q = 0; q < nq; ++q) {
+        const int buf = q & 1;
+        if (q >= 2 && !mbar_wait(buf ? empty1 : empty0, (uint32_t)(((q >> 1) - 1) & 1))) {
+          atomicOr(&g_oz_status, 1u);
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        unsigned char *sA = sm + buf * 2 * OPB;
+        unsigned char *sB = sA + OPB;
+        const uint32_t fb = buf ? full1 : full0;
+        asm volatile(
+            "{\n\t.reg .b64 st;\n\t"
+            "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(fb),
+            "r"(2u * OPB)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_addr(sA)),
+            "l"(gA + (int64_t)q * OPB), "r"(OPB), "r"(fb)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_addr(sB)),
+            "l"(gB + (int64_t)q * OPB), "r"(OPB), "r"(fb)
+            : "memory");
+      }
+    }
+  } else if (warp == 5) {
+    // ---- MMA issue: products (i, j), i + j <= S - 1, into accumulator min(i + j, 3) ----
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(OZ_M, OZ_N);
+      bool started[4] = {false, false, false, false};
+      int q = 0;
+      for (; q < nq; ++q) {
+        const int buf = q & 1;
+        if (*(volatile int *)&abort_flag) break;
+        if (!mbar_wait(buf ? full1 : full0, (uint32_t)((q >> 1) & 1))) {
+          atomicOr(&g_oz_status, 1u);
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_addr(sm + buf * 2 * OPB), b0 = a0 + OPB;
+#pragma unroll
+        for (int ks = 0; ks < OZ_KC / 16; ++ks) {
+#pragma unroll
+          for (int s = S - 1; s >= 0; --s) {  // smallest products first
+#pragma unroll
+            for (int i = 0; i <= s; ++i) {
+              const int j = s - i;
+              const int acc = s < 3 ? s : 3;
+              const uint64_t da = smem_desc(a0 + i * OZ_BLK + ks * 256);
+              const uint64_t db = smem_desc(b0 + j * OZ_BLK + ks * 256);
+              const uint32_t en = started[acc] ? 1u : 0u;
+              started[acc] = true;
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\t"
+                  "setp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + (uint32_t)(acc * OZ_N)),
+                  "l"(da), "l"(db), "r"(idesc), "r"(en)
+                  : "memory");
+            }
+          }
+        }
+        // the buffer may be refilled once these MMAs have read it
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         buf ? empty1 : empty0)
+                     : "memory");
+      }
+      // every MMA issued above is complete when this commit arrives (also after an abort)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accb)
+                   : "memory");
+    }
+  } else {
+    // ---- epilogue: warps 0-3, TMEM lanes 32 w .. 32 w + 31 = tile rows ----
+    bool ok_wait = mbar_wait(accb, 0u);
+    if (!ok_wait) {
+      atomicOr(&g_oz_status, 1u);
+      mbar_wait(accb, 0u);  // once more (bounded): no issued MMA may still write the TMEM when it is freed
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // warp-uniform, so that the warp-collective TMEM loads below never diverge
+    const bool valid = __all_sync(0xffffffffu, ok_wait) && !*(volatile int *)&abort_flag;
+    const int row = m0 + warp * 32 + lane;
+    const int64_t Mpad = (int64_t)it.tc_tiles_m * OZ_M, Npad = (int64_t)it.tc_tiles_n * OZ_N;
+    const int ea = it.oea[((int64_t)b * Mpad + row) * it.ksplit + chunk];
+    const double sa = (ea == OZ_EXP_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll)
+                                               : __longlong_as_double((long long)(ea + 1023) << 52);
+    double *Cp = static_cast<double *>(it.C) + (int64_t)b * it.scb;
+    double *Pp = it.ksplit > 1 ? static_cast<double *>(it.part) + ((int64_t)chunk * it.batch + b) * (int64_t)it.M * it.N
+                               : nullptr;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const int n_here = (N - n0 < OZ_N) ? N - n0 : OZ_N;
+    for (int c0 = 0; c0 < n_here; c0 += 16) {
+      uint32_t v[4][16];
+      if (nq > 0 && valid) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (a >= S) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[a][j] = 0u;
+            continue;
+          }
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+              "%14, %15}, [%16];"
+              : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
+                "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]), "=r"(v[a][10]), "=r"(v[a][11]),
+                "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]), "=r"(v[a][15])
+              : "r"(trow + (uint32_t)(a * OZ_N + c0)));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[a][j] = 0u;
+      }
+      if (row >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = n0 + c0 + j;
+        if (col >= N) break;
+        const int eb = it.oeb[((int64_t)b * Npad + col) * it.ksplit + chunk];
+        double val;
+        if (!valid || eb == OZ_EXP_NONFINITE) {
+          val = __longlong_as_double(0x7FF8000000000000ll);
+        } else {
+          const double sum = ((double)__uint_as_float(v[0][j]) + (double)__uint_as_float(v[1][j])) +
+                             ((double)__uint_as_float(v[2][j]) + (double)__uint_as_float(v[3][j]));
+          const double sb = __longlong_as_double((long long)(eb + 1023) << 52);
+          val = (sum * sa) * sb;
+        }
+        if (Pp) {
+          Pp[(int64_t)col * it.M + row] = val;
+        } else {
+          double *c = Cp + (int64_t)row * it.scm + (int64_t)col * it.scn;
+          double o = it.alpha * val;
+          if (it.beta != 0.0) o += it.beta * *c;
+          *c = o;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 5) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+  }
+}
+
+template <int S>
+cudaError_t launch_oz_s(const GemmItem *d_items, int n_items, int split_blocks, int tiles, const int *d_ranks,
+                        cudaStream_t s) {
+  oz_split_kernel<S><<<split_blocks, 256, 0, s>>>(d_items, n_items, d_ranks);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = 2 * 2 * (size_t)S * OZ_BLK + 1024;
+  // at least 116 KB: one CTA per SM, which holds all 512 TMEM columns
+  const size_t smem_req = smem > 116 * 1024 ? smem : 116 * 1024;
+  e = cudaFuncSetAttribute(oz_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
+  if (e != cudaSuccess) return e;
+  oz_gemm_kernel<S><<<tiles, OZ_THREADS, smem_req, s>>>(d_items, n_items, d_ranks);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int oz_tile_m() { return OZ_M; }
+int oz_tile_n() { return OZ_N; }
+int oz_stage_k() { return OZ_KC; }
+int oz_block_bytes() { return (int)OZ_BLK; }
+
+cudaError_t launch_gemm_oz(const GemmItem *d_items, int n_items, int split_blocks, int tiles, const int *d_ranks,
+                           bool any_split, int slices, cudaStream_t s) {
+  if (n_items <= 0 || tiles <= 0) return cudaSuccess;
+  cudaError_t e;
+  switch (slices) {
+    case 2: e = launch_oz_s<2>(d_items, n_items, split_blocks, tiles, d_ranks, s); break;
+    case 3: e = launch_oz_s<3>(d_items, n_items, split_blocks, tiles, d_ranks, s); break;
+    case 4: e = launch_oz_s<4>(d_items, n_items, split_blocks, tiles, d_ranks, s); break;
+    case 5: e = launch_oz_s<5>(d_items, n_items, split_blocks, tiles, d_ranks, s); break;
+    case 6: e = launch_oz_s<6>(d_items, n_items, split_blocks, tiles, d_ranks, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  if (any_split) return launch_gemm_reduce_f64(d_items, n_items, d_ranks, s);
+  return cudaSuccess;
+}
+
+unsigned oz_take_status() {
+  unsigned v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_oz_status, sizeof(v)) != cudaSuccess) return ~0u;
+  if (v) {
+    const unsigned z = 0;
+    if (cudaMemcpyToSymbol(g_oz_status, &z, sizeof(z)) != cudaSuccess) return ~0u;
+  }
+  return v;
+}
+
+}  // namespace htgb

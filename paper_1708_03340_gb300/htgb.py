@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libhtgb.so")
 
 HT_OK, HT_EINVAL, HT_ENOMEM, HT_ECUDA, HT_ETIMEOUT, HT_ENUMERIC, HT_EUNSUPPORTED = range(7)
 HT_F64, HT_F32 = 0, 1
-HT_PREC_FP64, HT_PREC_FP32, HT_PREC_FP32_SQRT = 0, 1, 2
+HT_PREC_FP64, HT_PREC_FP32, HT_PREC_FP32_SQRT, HT_PREC_MIXED = 0, 1, 2, 3
 HT_TRUNC_RANK, HT_TRUNC_EPS = 0, 1
 HT_SCHED_LEVEL, HT_SCHED_NODE = 0, 1
 
