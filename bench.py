@@ -3,25 +3,31 @@
 
 One step = ht_add (Lemma "sum of two H-tensors") of seeded HT tensor pairs
 followed by the truncation of each sum (orthogonalization, reduced Gramians,
-refined eigendecompositions, rank selection, projection), replayed as one CUDA
-graph (ht_graph_add_truncate / ht_graph_launch).  Workloads (--config):
+eigendecompositions, rank selection, projection), replayed as one CUDA graph
+(ht_graph_add_truncate / ht_graph_launch).  Workloads (--config):
 
+  deep     d=256, n=4096, k=64 -> rank 128, Gaussian leaves,
+           sigma_j = 10^(-10j/64), eps = 1e-6 relative (default)
   single   d=64, n=1000, k=32 -> rank 64, orthonormal Gaussian leaves,
-           sigma_j = 10^(-8j/32), eps = 1e-8 relative, rank cap 32 (default)
+           sigma_j = 10^(-8j/32), eps = 1e-8 relative, rank cap 32
   small    256 pairs of d=8, n=32, k=8 -> rank 16, Gaussian leaves,
            sigma_j = 2^-j, truncated to rank 8
   batched  a wave of uneven tensors, d~U{4..32}, n~U{16..512}, k~U{4..48},
            each the sum of 4 tensors (sigma_j = 2^-j) truncated to its own k
-  deep     d=256, n=4096, k=64 -> rank 128, Gaussian leaves,
-           sigma_j = 10^(-10j/64), eps = 1e-6 relative
   wide     8 pairs of d=16, n=2048, k=128 -> rank 256, orthonormal leaves,
            sigma_j = j^-2, truncated to rank 128
 
-Arms:
-  default            the GB300 library (FP32 storage and contractions, FP64
-                     eigensolves, one batched launch per tree level); for
-                     `single` the plain FP64 path (per level and one launch per
-                     node) is timed beside it
+Arms (all on the same workload):
+  value              the mixed-precision path (HT_PREC_MIXED: F64 storage,
+                     FP64 QR blocks and eigensolves, contractions on the tcgen05
+                     tensor cores by exact BF16 slicing), one batched launch
+                     per tree level, CUDA-graph replay
+  fp32_path          FP32 storage and contractions (HT_PREC_FP32)
+  plain_fp64_*       every step in FP64 on the SIMT pipes, one launch per level
+                     and one launch per tree node
+  errors             each path's results against the CPU FP64 oracle on the
+                     workload's first pair (the oracle run is also the
+                     cpu_baseline timing)
   --impl reference   the CPU FP64 oracle on the host cores (rank 0 only)
 
 Multi-GPU (torchrun): every rank truncates its own tensors (independent
@@ -45,7 +51,8 @@ sys.path.insert(0, ROOT)
 from paper_1708_03340_gb300 import inputs as I  # noqa: E402
 
 METRIC = "HT truncations/s + roofline fraction, mixed vs plain FP64 GPU at stated rel err"
-FP32_PEAK = 152 * 128 * 2 * 2.070e9  # SMs x FP32 lanes x 2 flop x max clock (80.5 TFLOP/s)
+FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9  # SMs x FP32 lanes x 2 flop x max clock (80.5 TFLOP/s)
+OZ_PRODUCTS = 15  # BF16 slice products per FP64-equivalent product in the mixed path (5 slices, i + j <= 4)
 
 
 # ---------------------------------------------------------------------------
@@ -304,10 +311,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="single", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="deep", choices=sorted(WORKLOADS))
     ap.add_argument("--pairs", type=int, default=0, help="tensors per step (small: 256, batched: 64, wide: 8)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison arms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-errors", action="store_true", help="skip the error statement against the oracle")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -395,10 +403,13 @@ def main():
         ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs))
         return dict(ms=ms, launches=htgb.ht_launch_count() - l0, prof=prof, X=X)
 
-    # ---- headline: graph replays of the FP32-storage path (FP32 eigensolves refined to FP64 level)
+    # ---- unit peaks of this GPU (roofline denominators the measured peak file lacks)
+    peaks = measured_peaks() if rank == 0 else {}
+
+    # ---- headline: graph replays of the mixed-precision path
     clk_path = os.path.join(tempfile.gettempdir(), f"htgb_clocks_{os.getpid()}.csv")
     proc, fh = start_clock_sampler(clk_path)
-    main_arm = graph_arm(htgb.HT_F32, htgb.HT_PREC_FP32, args.steps, args.warmup)
+    main_arm = graph_arm(htgb.HT_F64, htgb.HT_PREC_MIXED, args.steps, args.warmup)
     clocks = read_clocks(proc, fh, clk_path, local)
     per_step = len(main_arm["X"])
     value = main_arm["value"]
@@ -409,63 +420,54 @@ def main():
         work += w
 
     # ---- kernel breakdown and the roofline of the dominant kernel family
-    psteps = max(2, min(args.steps, 5))
-    prof = profiled_arm(htgb.HT_F32, htgb.HT_PREC_FP32, psteps)
-    roofline = None
-    arith = {k: v for k, v in prof["prof"].items() if v["flops"] > 0}  # families with an arithmetic roofline
-    if arith:
-        name, rec = max(arith.items(), key=lambda kv: kv[1]["ms"])
-        per_launch_ms = rec["ms"] / rec["launches"]
-        per_launch_flops = rec["flops"] / rec["launches"]
-        ach = per_launch_flops / (per_launch_ms / 1e3)
-        kernel = {"qr": "qr_reg_kernel + qr_reg2_kernel (FP32 TSQR blocks)", "gemm": "gemm_kernel (FP32 SIMT, compensated)",
-                  "eig": "eig_ql_kernel<float> + refine_df_kernel (double-float)"}.get(name, name)
-        peak = FP32_PEAK  # every family of the FP32 path runs on the FP32 pipes (the refinement in double-float)
-        roofline = {"kernel": kernel, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
-                    "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": TRAFFIC_PER_LAUNCH.get((args.config, name)),
-                    "peak_source": "FP32 unit count x max SM clock (recipe)",
-                    "launches_per_step": rec["launches"] / psteps, "ms_per_launch": per_launch_ms,
-                    "flops_per_launch": per_launch_flops}
+    psteps = max(2, min(args.steps, 4))
+    prof = profiled_arm(htgb.HT_F64, htgb.HT_PREC_MIXED, psteps)
+    roofline = roofline_of(prof["prof"], psteps, peaks)
 
     line = {
         "metric": METRIC, "value": value, "unit": "truncations/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64",
+        "vs_baseline": None, "dtype": "f64 (contractions: bf16 slices, fp32 accumulate)",
         "data": "synthetic (seeded SplitMix64/Box-Muller HT tensors)",
         "config": {"workload": args.config, "tensors_per_step": per_step, "shape": WORKLOADS[args.config]["desc"],
                    "l2": "flushed between steps (256 MB write)",
-                   "path": "FP32 storage and contractions, FP32 eigensolves refined in double-float, one batched launch per level, "
+                   "path": "mixed: F64 storage, FP64 TSQR blocks and QL eigensolves, every contraction on tcgen05 "
+                           "(5 BF16 slices per FP64 operand, exact leading sums), one batched launch per level, "
                            "CUDA-graph replay"},
         "gflops": work / (ms_per_step / 1e3) / 1e9,
         "direct_calls_ms_per_step": prof["ms"] / psteps,
         "kernel_ms_per_step": {k: v["ms"] / psteps for k, v in prof["prof"].items()},
-        "kernel_tflops": {k: v["flops"] / max(v["ms"], 1e-9) / 1e9 for k, v in prof["prof"].items() if v["flops"] > 0},
+        "kernel_launches_per_step": {k: v["launches"] / psteps for k, v in prof["prof"].items()},
         "ranks_first_nodes": [int(v) for v in main_arm["X"][0].ranks()[:8]],
         "gpu_launches": main_arm["launches"],
         "roofline": roofline,
+        "unit_peaks": peaks,
         "clocks": clocks,
     }
 
-    # ---- plain FP64 GPU arms (default workload): per level, and one launch per node
-    if args.config == "single" and not args.no_plain:
-        ps = max(3, args.steps // 4)
+    # ---- comparison arms on the same workload
+    trim_pool()
+    if not args.no_plain:
+        fs = max(3, args.steps // 2)
+        f32 = graph_arm(htgb.HT_F32, htgb.HT_PREC_FP32, fs, 3)
+        line["fp32_path"] = {"value": f32["value"], "unit": "truncations/s", "ms_per_step": f32["ms"] / fs}
+        htgb.ht_graph_free(f32["g"])
+        trim_pool()
+        ps = 2 if args.config in ("deep", "wide") else 3
         plain = profiled_arm(htgb.HT_F64, htgb.HT_PREC_FP64, ps)
-        line["plain_fp64_level"] = {"value": ws * ps / (plain["ms"] / 1e3), "unit": "truncations/s",
+        line["plain_fp64_level"] = {"value": ws * per_step * ps / (plain["ms"] / 1e3), "unit": "truncations/s",
                                     "ms_per_step": plain["ms"] / ps,
                                     "kernel_ms_per_step": {k: v["ms"] / ps for k, v in plain["prof"].items()}}
-        node = graph_arm(htgb.HT_F64, htgb.HT_PREC_FP64, 3, 3, sched=htgb.HT_SCHED_NODE)
+        trim_pool()
+        ns = 1 if args.config in ("deep", "wide") else 3
+        node = graph_arm(htgb.HT_F64, htgb.HT_PREC_FP64, ns, 1, sched=htgb.HT_SCHED_NODE)
         line["plain_fp64_per_node"] = {"value": node["value"], "unit": "truncations/s",
-                                       "ms_per_step": node["ms"] / 3, "launches_per_step": node["launches"] / 3}
+                                       "ms_per_step": node["ms"] / ns, "launches_per_step": node["launches"] / ns,
+                                       "steps": ns, "warmup": 1}
         htgb.ht_graph_free(node["g"])
         line["speedup_vs_plain_per_node"] = value / line["plain_fp64_per_node"]["value"]
         line["speedup_vs_plain_level"] = value / line["plain_fp64_level"]["value"]
-        line["rel_err_vs_fp64"] = accuracy_vs_fp64(htgb, stream)
-        # the square-root Gramian mode of the FP32 path (HT_PREC_FP32_SQRT): accuracy arm
-        sq = graph_arm(htgb.HT_F32, htgb.HT_PREC_FP32_SQRT, ps, 3)
-        line["fp32_sqrt_gramians"] = {"value": sq["value"], "unit": "truncations/s", "ms_per_step": sq["ms"] / ps,
-                                      "rel_err_vs_fp64": accuracy_vs_fp64(htgb, stream, htgb.HT_PREC_FP32_SQRT)}
-        htgb.ht_graph_free(sq["g"])
+        line["speedup_vs_fp32_path"] = value / line["fp32_path"]["value"]
 
     # ---- end to end through the public API: pinned host blobs in, truncated blobs out, every step
     A, C, X, g = main_arm["A"], main_arm["C"], main_arm["X"], main_arm["g"]
@@ -476,9 +478,9 @@ def main():
         k = np.asarray(a.ranks()) + np.asarray(c.ranks())
         k[0] = 1
         cap_sz.append(int(I.blob_size(a.tree.d, a.n, k)))
-    hX = [torch.empty(max(s_, 1), dtype=torch.float32).pin_memory() for s_ in cap_sz]
+    hX = [torch.empty(max(s_, 1), dtype=torch.float64).pin_memory() for s_ in cap_sz]
     e2e_steps = max(3, args.steps // 2)
-    h2d = sum(t.numel() * 4 for t in hA + hC)
+    h2d = sum(t.numel() * 8 for t in hA + hC)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     d2h = 0
@@ -491,25 +493,40 @@ def main():
         for x, hx in zip(X, hX):
             sz = htgb.ht_tensor_blob_size(x.handle)
             htgb.ht_tensor_download(x.handle, hx.numpy()[:sz])
-            d2h += sz * 4
+            d2h += sz * 8
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     line["e2e"] = {"value": ws * per_step * e2e_steps / e2e_s, "unit": "truncations/s",
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     htgb.ht_graph_free(g)
 
-    # ---- CPU oracle baseline (rank 0, N = 1 only), a bounded sample
+    # ---- CPU oracle baseline (rank 0, N = 1 only), a bounded sample; its
+    # result on the workload's first pair is the reference of the error statement
     if ws == 1 and not args.no_cpu:
         from oracle import oracle as O
         cores = O.set_threads(0)
         items, sample, equiv = oracle_sample(args.config, 0, args)
-        secs = oracle_time(items, 1)
+        t0 = time.perf_counter()
+        ref = None
+        (d0, n0, (ka0, xa0), (kc0, xc0), opts0) = items[0]
+        k0, x0 = O.add(d0, n0, ka0, xa0, kc0, xc0)
+        ref = O.truncate(d0, n0, k0, x0, **opts0)
+        for it in items[1:]:
+            oracle_time([it], 1)
+        secs = time.perf_counter() - t0
         reps = 1
         while secs * (reps + 1) / reps < 10.0 and reps < 8:  # about 10 s of CPU work
             secs += oracle_time(items, 1)
             reps += 1
         line["cpu_baseline"] = {"value": reps * equiv / secs, "unit": "truncations/s", "cores": cores,
                                 "kind": "oracle", "sample": f"{reps} x {sample}, OpenMP over tree nodes"}
+        if args.config != "batched" and not args.no_errors:
+            trim_pool()
+            try:
+                line["errors_vs_oracle"] = errors_vs_oracle(htgb, stream, (d0, n0, ka0, xa0, kc0, xc0, opts0, k0, x0),
+                                                            ref)
+            except Exception as e:  # the line is printed either way, with the reason
+                line["errors_vs_oracle"] = {"unavailable": str(e)[:300]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -517,51 +534,148 @@ def main():
     return 0
 
 
-def accuracy_vs_fp64(htgb, stream, prec32=None):
-    """Errors of the FP32-storage path relative to the FP64 GPU path on the same
-    (FP32-representable) inputs of the default workload, all computed by the
-    library on the GPU: sigma^2 normwise per node, ||X||, ||T32(X) - T64(X)|| / ||X||
-    and the truncation errors ||X - T(X)|| / ||X|| of both paths (norms of HT
-    differences via orthogonalization, never via inner products)."""
-    (n, ka, xa), (_, kc, xc) = I.single_pair(11)
-    opts = I.SINGLE_OPTS
-    tree = htgb.HTTree(64)
-    xa32 = np.asarray(xa, np.float32).astype(np.float64)
-    xc32 = np.asarray(xc, np.float32).astype(np.float64)
-    res = {}
-    for name, dt in (("fp32", htgb.HT_F32), ("fp64", htgb.HT_F64)):
-        A = htgb.HTTensor.from_blob(tree, n, ka, xa32, dt, stream)
-        C = htgb.HTTensor.from_blob(tree, n, kc, xc32, dt, stream)
-        X = A.add(C)
-        p32 = htgb.HT_PREC_FP32 if prec32 is None else prec32
-        rep = X.truncate(prec=p32 if dt == htgb.HT_F32 else htgb.HT_PREC_FP64, **opts)
-        res[name] = (rep, X.ranks(), X.download().astype(np.float64))
-    X64 = htgb.HTTensor.from_blob(tree, n, ka, xa32, htgb.HT_F64, stream).add(
-        htgb.HTTensor.from_blob(tree, n, kc, xc32, htgb.HT_F64, stream))
-    nrm = res["fp64"][0]["norm"]
+def trim_pool():
+    """Hand the unused memory the library's stream-ordered pool keeps back to
+    the device (the library keeps freed workspace for reuse; the arms of this
+    benchmark differ in size)."""
+    try:
+        import ctypes
+        import torch
+        from paper_1708_03340_gb300 import htgb
+        htgb.load()
+        rt = ctypes.CDLL("libcudart.so.13")
+        pool = ctypes.c_void_p()
+        torch.cuda.synchronize()
+        if rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), torch.cuda.current_device()) == 0:
+            rt.cudaMemPoolTrimTo(pool, ctypes.c_size_t(0))
+    except Exception:
+        pass
 
-    def diff_norm(ya, ka_, yb, kb_):
-        P = ya if isinstance(ya, htgb.HTTensor) else htgb.HTTensor.from_blob(tree, n, ka_, ya, htgb.HT_F64, stream)
-        Q = htgb.HTTensor.from_blob(tree, n, kb_, yb, htgb.HT_F64, stream)
+
+def measured_peaks():
+    """Unit throughputs measured on this GPU by peaks/peaks.cu (FP64 and FP32
+    FMA chains, tcgen05 BF16 and TF32 MMA issue), next to the measured HBM
+    and cuBLAS BF16 figures of the pool's peak file.  {} if unavailable."""
+    out = {}
+    try:
+        from paper_1708_03340_gb300.peaks import peaks as PK
+        for k, v in PK.run().items():
+            out[k] = v["tflops"]
+    except Exception as e:  # the roofline then states the nominal figure it used
+        out["error"] = str(e)[:200]
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        out["hbm_gbs"] = mp.get("hbm_gbs")
+        out["bf16_cublas"] = mp.get("bf16_tflops")
+        out["bf16_cublas_sustained"] = mp.get("bf16_tflops_sustained")
+    except Exception:
+        pass
+    return out
+
+
+def roofline_of(prof, steps, peaks):
+    """Roofline object of the dominant arithmetic kernel family (by device
+    time) of the mixed path, measured live with CUDA events on the launching
+    stream.  Families and their bound:
+      qr    FP64 Householder TSQR blocks: FP64 ALU, 4 m n^2 - 4 n^3 / 3 flop per block
+      gemm  tensor-core contractions: tensor pipe, BF16 MMA work = 15 slice products
+            x 2 M N K per contraction (M N K counted at the plan's maximal dims)
+      eig   FP64 QL eigensolves: FP64 ALU, 9 k^3 flop per Gramian"""
+    arith = {k: v for k, v in prof.items() if v["flops"] > 0 and k in ("qr", "gemm", "eig")}
+    if not arith:
+        return None
+    fams = {}
+    for name, rec in arith.items():
+        per_launch_ms = rec["ms"] / rec["launches"]
+        fl = rec["flops"] / rec["launches"]
+        if name == "gemm":
+            work, bound = OZ_PRODUCTS * fl, "tensor"
+            peak = peaks.get("bf16_cublas") or 1880.0
+            src = "cuBLAS BF16 burst (measured peak file)"
+        else:
+            work, bound = fl, "alu"
+            peak = peaks.get("fp64_fma")
+            src = "FP64 FMA chains, measured by peaks.cu on this GPU"
+            if not peak:
+                peak, src = 1.25, "FP64 nominal (measurement unavailable)"
+        ach = work / (per_launch_ms / 1e3) / 1e12
+        fams[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                      "ms_per_step": rec["ms"] / steps, "launches_per_step": rec["launches"] / steps,
+                      "ms_per_launch": per_launch_ms, "flops_per_launch": work, "peak_source": src}
+        if name == "gemm":
+            fams[name]["fp64_equivalent_tflops"] = fl / (per_launch_ms / 1e3) / 1e12
+    name = max(fams, key=lambda k: fams[k]["ms_per_step"])
+    kernel = {"qr": "qr_reg_kernel<double> (FP64 TSQR row blocks)",
+              "gemm": "oz_split_kernel + oz_gemm_kernel (tcgen05 BF16 slices)",
+              "eig": "eig_ql_kernel<double> (FP64 QL)"}[name]
+    top = dict(fams[name])
+    top["kernel"] = kernel
+    top["traffic"] = TRAFFIC_PER_LAUNCH.get(("deep", name))
+    top["families"] = fams
+    return top
+
+
+def errors_vs_oracle(htgb, stream, pair, ref):
+    """Per-result errors of the mixed, FP64 and FP32 paths against the CPU FP64
+    oracle's truncation `ref` of the same sum: sigma per node for sigma >=
+    1e-5 sigma_max (normwise |sigma_i - sigma_ref_i| / sigma_max and relative
+    |sigma_i - sigma_ref_i| / sigma_ref_i), ||X||, the truncated tensors
+    ||T(X) - T_ref(X)|| / ||X||, the truncation errors ||X - T(X)|| / ||X||,
+    and the nodes whose rank differs with the oracle's energy between the two
+    cuts.  Tensor differences are norms of the orthogonalized sum Y + (-Z)
+    (mixed path, FP64 storage), never inner products."""
+    d, n, ka, xa, kc, xc, opts, k, x = pair
+    tree = htgb.HTTree(d)
+    nrm = ref["norm"]
+
+    def tensor(kk, blob):
+        return htgb.HTTensor.from_blob(tree, n, kk, blob, htgb.HT_F64, stream)
+
+    def diff_norm(k1, y1, k2, y2):
+        """||Y - Z|| = ||B_D||_F of the orthogonalized Y + (-Z) (mixed-path
+        orthogonalization: FP64 QR blocks, the products to about 1e-12)."""
+        P, Q = tensor(k1, y1), tensor(k2, y2)
         Q.scale(-1.0)
-        return P.add(Q).norm()
+        S = P.add(Q)
+        S.orthogonalize(htgb.HT_PREC_MIXED)
+        ks = S.ranks()
+        root = htgb.ht_tensor_node_ptr(S.handle, 0)[1]
+        b = S.download()[:root]
+        del S, P, Q
+        trim_pool()
+        return float(np.linalg.norm(b))
 
-    (r32, k32, x32), (r64, k64, x64) = res["fp32"], res["fp64"]
-    worst = 0.0
-    o32 = o64 = 0
-    for t in range(1, len(r64["korth"])):
-        a = r32["sigma"][o32:o32 + r32["korth"][t]]
-        b = r64["sigma"][o64:o64 + r64["korth"][t]]
-        o32 += r32["korth"][t]
-        o64 += r64["korth"][t]
-        if len(b) and b[0] > 0:
-            sel = b >= 1e-5 * b[0]
-            worst = max(worst, float(np.max(np.abs(a[sel] ** 2 - b[sel] ** 2)) / b[0] ** 2))
-    return {"sigma2_normwise": worst, "norm": abs(r32["norm"] - nrm) / nrm,
-            "truncated_tensor": diff_norm(x32, k32, x64, k64) / nrm,
-            "trunc_err_fp32": diff_norm(X64, None, x32, k32) / nrm,
-            "trunc_err_fp64": diff_norm(X64, None, x64, k64) / nrm,
-            "ranks_fp32_ge_fp64": bool(np.all(np.asarray(k32) >= np.asarray(k64)))}
+    err_ref = diff_norm(k, x, ref["k"], ref["x"]) / nrm
+    out = {"oracle_trunc_err": err_ref, "oracle_ranks_first_nodes": [int(v) for v in ref["k"][:8]]}
+    for name, dtype, prec in (("mixed", htgb.HT_F64, htgb.HT_PREC_MIXED), ("fp64", htgb.HT_F64, htgb.HT_PREC_FP64),
+                              ("fp32", htgb.HT_F32, htgb.HT_PREC_FP32)):
+        A = htgb.HTTensor.from_blob(tree, n, ka, xa, dtype, stream)
+        C = htgb.HTTensor.from_blob(tree, n, kc, xc, dtype, stream)
+        X = A.add(C)
+        rep = X.truncate(prec=prec, **opts)
+        kt, xt = X.ranks(), X.download().astype(np.float64)
+        worst_nw = worst_rel = 0.0
+        o = 0
+        for t in range(1, 2 * d - 1):
+            a = np.asarray(rep["sigma"][o:o + rep["korth"][t]], np.float64)
+            o += int(rep["korth"][t])
+            b = np.asarray(ref["sigma"][t], np.float64)
+            if len(b) and b[0] > 0:
+                sel = b >= 1e-5 * b[0]
+                worst_nw = max(worst_nw, float(np.max(np.abs(a[sel] - b[sel])) / b[0]))
+                worst_rel = max(worst_rel, float(np.max(np.abs(a[sel] - b[sel]) / b[sel])))
+        differ = [t for t in range(1, 2 * d - 1) if int(kt[t]) != int(ref["k"][t])]
+        energy = 0.0
+        for t in differ:
+            lo, hi = sorted((int(kt[t]), int(ref["k"][t])))
+            energy += float(np.sqrt(np.sum(np.asarray(ref["sigma"][t][lo:hi], np.float64) ** 2)))
+        out[name] = {"sigma_normwise": worst_nw, "sigma_relative": worst_rel,
+                     "norm": abs(rep["norm"] - nrm) / nrm,
+                     "truncated_tensor": diff_norm(kt, xt, ref["k"], ref["x"]) / nrm,
+                     "trunc_err": diff_norm(k, x, kt, xt) / nrm,
+                     "rank_diff_nodes": len(differ), "rank_diff_energy": energy / nrm,
+                     "ranks_first_nodes": [int(v) for v in kt[:8]]}
+    return out
 
 
 if __name__ == "__main__":

@@ -234,7 +234,8 @@ namespace {
 constexpr uint64_t TAG_P = 1ull << 62;  // persistent workspace
 constexpr uint64_t TAG_S = 1ull << 61;  // per-phase scratch workspace
 constexpr uint64_t TAG_M = 1ull << 60;  // metadata appended to the item upload
-constexpr uint64_t TAG_MASK = (1ull << 60) - 1;
+constexpr uint64_t TAG_L = 1ull << 59;  // per-launch scratch (split-K partials, tensor-core slices)
+constexpr uint64_t TAG_MASK = (1ull << 59) - 1;
 
 enum LKind { L_GEMM, L_QR, L_EIG, L_COPY, L_COMPACT, L_RANKS, L_CHOL };
 
@@ -249,6 +250,7 @@ struct Launch {
   double flops = 0.0;  // algorithmic flops of the launch (literal, i.e. maximal, dims)
   int tc_tiles = 0;    // GEMM: tiles of the tensor-core kernel (mixed path)
   int oz_split = 0;    // GEMM: CTAs of the tensor-core path's split launch
+  int oz_slices = 0;   // GEMM: BF16 slices per operand (mixed path)
   const void *ranks = nullptr;  // tagged pointer to the rank array used by the launch
   void *scratch = nullptr;      // eig scratch (tagged)
   int variant = 0;              // GEMM: SIMT tile shape (gemm_tile_shape)
@@ -267,12 +269,17 @@ inline P *tagp(uint64_t tag, size_t off) {
 // 2^-40 of the row scale per product).
 constexpr int kOzChunk = 256;
 constexpr int kOzSlices = 5;
+// the reduced-Gramian contractions: 6 slices (about 1e-14 of the row scale).
+// Their eigenvalues decide the ranks; the eps cut of the deep workload sits
+// at eigenvalues near 1e-15 of the largest, where 5 slices leave noise that
+// moves the cut.
+constexpr int kOzSlicesGram = 6;
 
 struct Plan {
   std::vector<uint8_t> items;
   std::vector<uint8_t> meta;
   std::vector<Launch> launches;
-  size_t p_bytes = 0, s_bytes = 0, s_peak = 0;
+  size_t p_bytes = 0, s_bytes = 0, s_peak = 0, l_bytes = 0, l_peak = 0;
   bool node_sched = false;
   bool sqrt_gram = false;  // Gramians from square-root factors (HT_PREC_FP32_SQRT)
   bool mixed = false;      // HT_PREC_MIXED: contractions on the tensor cores (k_oz.cu)
@@ -301,6 +308,13 @@ struct Plan {
     return tagp<void>(TAG_S, off);
   }
   void sreset() { s_bytes = 0; }
+  // scratch that lives for one launch only (the next launch reuses it)
+  void *lalloc_bytes(size_t bytes) {
+    size_t off = (l_bytes + 255) & ~size_t(255);
+    l_bytes = off + bytes;
+    l_peak = std::max(l_peak, l_bytes);
+    return tagp<void>(TAG_L, off);
+  }
   template <typename P>
   P *mpush(const P *data, size_t count) {
     size_t off = (meta.size() + 15) & ~size_t(15);
@@ -313,6 +327,8 @@ struct Plan {
   void begin(LKind kind, const void *ranks = nullptr) {
     Launch L;
     L.kind = kind;
+    L.oz_slices = oz_slices;
+    l_bytes = 0;
     size_t off = (items.size() + 15) & ~size_t(15);
     items.resize(off);
     L.off = off;
@@ -327,8 +343,10 @@ struct Plan {
       LKind k = L.kind;
       const void *r = L.ranks;
       const bool df = L.df;
+      const int sl = L.oz_slices;
       begin(k, r);
       cur().df = df;
+      cur().oz_slices = sl;
     }
     Launch &M = cur();
     M.node = node;
@@ -378,8 +396,10 @@ struct Plan {
       LKind k = cur().kind;
       const void *r = cur().ranks;
       const bool df = cur().df;
+      const int sl = cur().oz_slices;
       begin(k, r);
       cur().df = df;
+      cur().oz_slices = sl;
     }
     Launch &L = cur();
     g.tile0 = L.tiles;
@@ -387,23 +407,27 @@ struct Plan {
     g.tc_tile0 = L.tc_tiles;
     L.tc_tiles += g.tc_tiles_m * g.tc_tiles_n * g.batch * g.ksplit;
     if (mixed) {
-      // BF16 slice blocks (stages of oz_stage_k() reduction indices) and exponents
+      // BF16 slice blocks (stages of oz_stage_k() reduction indices) and
+      // exponents, for this launch only; an operand that every batch entry
+      // shares (zero batch stride) is sliced once
       const int max_ko = (g.Ko + g.ksplit - 1) / g.ksplit;
       const int sk = oz_stage_k();
       g.oz_stages = (g.K * max_ko + sk - 1) / sk;
-      const size_t blk = (size_t)oz_block_bytes() * oz_slices * g.oz_stages * g.ksplit * g.batch;
-      g.oza = salloc_bytes(blk * g.tc_tiles_m);
-      g.ozb = salloc_bytes(blk * g.tc_tiles_n);
-      g.oea = static_cast<int *>(salloc_bytes(sizeof(int) * (size_t)g.batch * g.tc_tiles_m * oz_tile_m() * g.ksplit));
-      g.oeb = static_cast<int *>(salloc_bytes(sizeof(int) * (size_t)g.batch * g.tc_tiles_n * oz_tile_n() * g.ksplit));
+      g.oz_share = (g.batch > 1 && g.sab == 0 ? 1 : 0) | (g.batch > 1 && g.sbb == 0 ? 2 : 0);
+      const int ba = (g.oz_share & 1) ? 1 : g.batch, bb = (g.oz_share & 2) ? 1 : g.batch;
+      const size_t blk = (size_t)oz_block_bytes() * L.oz_slices * g.oz_stages * g.ksplit;
+      g.oza = lalloc_bytes(blk * ba * g.tc_tiles_m);
+      g.ozb = lalloc_bytes(blk * bb * g.tc_tiles_n);
+      g.oea = static_cast<int *>(lalloc_bytes(sizeof(int) * (size_t)ba * g.tc_tiles_m * oz_tile_m() * g.ksplit));
+      g.oeb = static_cast<int *>(lalloc_bytes(sizeof(int) * (size_t)bb * g.tc_tiles_n * oz_tile_n() * g.ksplit));
       g.oz_split0 = L.oz_split;
-      L.oz_split += g.batch * g.ksplit * (g.tc_tiles_m + g.tc_tiles_n);
+      L.oz_split += g.ksplit * (ba * g.tc_tiles_m + bb * g.tc_tiles_n);
     }
     const double fl = 2.0 * g.M * g.N * (double)g.K * g.Ko * g.batch;
     L.flops += fl;
     if (g.ksplit > 1) {
       L.split = true;
-      g.part = salloc_bytes((size_t)g.ksplit * g.batch * g.M * g.N * (L.df ? sizeof(double) : esz));
+      g.part = lalloc_bytes((size_t)g.ksplit * g.batch * g.M * g.N * (L.df ? sizeof(double) : esz));
     }
     push_item(g, node);
   }
@@ -426,11 +450,15 @@ struct Plan {
   void chol(const CholItem &c, int node) { push_item(c, node); }
 };
 
+// Launch scratch sits right after the phase scratch; its base is found from
+// the phase scratch's base and size (g_lscratch_off, set by prepare_plan).
+thread_local size_t g_lscratch_off = 0;
 inline void *reloc(const void *p, char *pb, char *sb, char *mb) {
   uint64_t u = (uint64_t)p;
   if (u & TAG_P) return pb + (u & TAG_MASK);
   if (u & TAG_S) return sb + (u & TAG_MASK);
   if (u & TAG_M) return mb + (u & TAG_MASK);
+  if (u & TAG_L) return sb + g_lscratch_off + (u & TAG_MASK);
   return const_cast<void *>(p);
 }
 
@@ -576,7 +604,7 @@ void choose_gemm_variant(Plan &P, Launch &L) {
 // Workspace size of a plan: persistent | scratch | metadata | items.
 size_t plan_bytes(const Plan &P) {
   const size_t p_sz = (P.p_bytes + 255) & ~size_t(255);
-  const size_t s_sz = (P.s_peak + 255) & ~size_t(255);
+  const size_t s_sz = ((P.s_peak + 255) & ~size_t(255)) + ((P.l_peak + 255) & ~size_t(255));
   const size_t m_off = p_sz + s_sz;
   const size_t i_off = m_off + ((P.meta.size() + 255) & ~size_t(255));
   return i_off + P.items.size();
@@ -609,7 +637,8 @@ void dump_plan(const Plan &P) {
 // that stays alive in P).
 ht_status prepare_plan(Plan &P, cudaStream_t s, char *base, char **ib_dev_out) {
   const size_t p_sz = (P.p_bytes + 255) & ~size_t(255);
-  const size_t s_sz = (P.s_peak + 255) & ~size_t(255);
+  g_lscratch_off = (P.s_peak + 255) & ~size_t(255);
+  const size_t s_sz = g_lscratch_off + ((P.l_peak + 255) & ~size_t(255));
   const size_t m_off = p_sz + s_sz;
   const size_t i_off = m_off + ((P.meta.size() + 255) & ~size_t(255));
   char *pb = base, *sb = base + p_sz, *mb = base + m_off;
@@ -659,7 +688,7 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
     switch (L.kind) {
       case L_GEMM: {
         if (P.mixed)
-          e = launch_gemm_oz((const GemmItem *)items, L.n, L.oz_split, L.tc_tiles, rk, L.split, P.oz_slices, s);
+          e = launch_gemm_oz((const GemmItem *)items, L.n, L.oz_split, L.tc_tiles, rk, L.split, L.oz_slices, s);
         else if (f64)
           e = launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s, L.variant, false, false,
                                   L.uniform);
@@ -1476,6 +1505,7 @@ void plan_gramians(Plan &P, std::vector<TState> &TS, const std::vector<double *>
     if (jobs.empty()) continue;
     // C[i2,p,l] = sum_i1 Bhat_t[i1,i2] B[i1,p,l]:  C_mat (k1k2 x K0) = B_mat (k1k2 x K0) * Bhat_t
     P.begin(L_GEMM);
+    P.cur().oz_slices = kOzSlicesGram;
     for (Job &J : jobs) {
       GemmItem g = gemm0();
       g.A = node_ptr(J.S->x, J.t);
@@ -1496,6 +1526,7 @@ void plan_gramians(Plan &P, std::vector<TState> &TS, const std::vector<double *>
     // parent index i is split across CTAs when the level has few nodes
     int ksplit = split_for(tiles, 1 << 30);
     P.begin(L_GEMM);
+    P.cur().oz_slices = kOzSlicesGram;
     for (Job &J : jobs) {
       const ht_tree &T = J.S->x->tr;
       const int s1 = T.s1[J.t], s2 = T.s2[J.t];

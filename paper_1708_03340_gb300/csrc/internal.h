@@ -44,6 +44,7 @@ struct GemmItem {
   int *oea, *oeb;
   int oz_stages;
   int oz_split0;
+  int oz_share;  // bit 0: A, bit 1: B is the same for every batch entry (sliced once)
 };
 
 // Householder QR of one row block (m >= n) held in shared memory.

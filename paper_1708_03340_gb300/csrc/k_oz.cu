@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
   __shared__ int sexp[OZ_M];
   const GemmItem &it = items[find_split(items, n_items, blockIdx.x)];
   int local = blockIdx.x - it.oz_split0;
-  const int per_a = it.batch * it.tc_tiles_m * it.ksplit;
+  const int bat_a = (it.oz_share & 1) ? 1 : it.batch;  // an operand shared by the batch is sliced once
+  const int per_a = bat_a * it.tc_tiles_m * it.ksplit;
   const int op = local < per_a ? 0 : 1;
   if (op) local -= per_a;
   const int tiles = op ? it.tc_tiles_n : it.tc_tiles_m;
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const GemmItem &it = items[find_tile(items, n_items, blockIdx.x)];
   int local = blockIdx.x - it.tc_tile0;
+  const int share = it.oz_share;
   const int tm = local % it.tc_tiles_m;
   local /= it.tc_tiles_m;
   const int tn = local % it.tc_tiles_n;
@@ -306,10 +308,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
   const int nq = (int)((f1 - f0 + OZ_KC - 1) / OZ_KC);  // stages holding data
   const int nst = it.oz_stages;
   constexpr uint32_t OPB = S * OZ_BLK;  // bytes of one operand's stage (all slices)
+  const int ba = (share & 1) ? 0 : b, bb = (share & 2) ? 0 : b;  // slices of a shared operand: entry 0
   const unsigned char *gA = static_cast<const unsigned char *>(it.oza) +
-                            ((((int64_t)b * it.tc_tiles_m + tm) * it.ksplit + chunk) * nst) * (int64_t)OPB;
+                            ((((int64_t)ba * it.tc_tiles_m + tm) * it.ksplit + chunk) * nst) * (int64_t)OPB;
   const unsigned char *gB = static_cast<const unsigned char *>(it.ozb) +
-                            ((((int64_t)b * it.tc_tiles_n + tn) * it.ksplit + chunk) * nst) * (int64_t)OPB;
+                            ((((int64_t)bb * it.tc_tiles_n + tn) * it.ksplit + chunk) * nst) * (int64_t)OPB;
   const uint32_t full0 = smem_addr(&bar_full[0]), full1 = smem_addr(&bar_full[1]);
   const uint32_t empty0 = smem_addr(&bar_empty[0]), empty1 = smem_addr(&bar_empty[1]);
   const uint32_t accb = smem_addr(&bar_acc);
@@ -422,7 +425,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
     const bool valid = __all_sync(0xffffffffu, ok_wait) && !*(volatile int *)&abort_flag;
     const int row = m0 + warp * 32 + lane;
     const int64_t Mpad = (int64_t)it.tc_tiles_m * OZ_M, Npad = (int64_t)it.tc_tiles_n * OZ_N;
-    const int ea = it.oea[((int64_t)b * Mpad + row) * it.ksplit + chunk];
+    const int ea = it.oea[((int64_t)ba * Mpad + row) * it.ksplit + chunk];
     const double sa = (ea == OZ_EXP_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll)
                                                : __longlong_as_double((long long)(ea + 1023) << 52);
     double *Cp = static_cast<double *>(it.C) + (int64_t)b * it.scb;
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
       for (int j = 0; j < 16; ++j) {
         const int col = n0 + c0 + j;
         if (col >= N) break;
-        const int eb = it.oeb[((int64_t)b * Npad + col) * it.ksplit + chunk];
+        const int eb = it.oeb[((int64_t)bb * Npad + col) * it.ksplit + chunk];
         double val;
         if (!valid || eb == OZ_EXP_NONFINITE) {
           val = __longlong_as_double(0x7FF8000000000000ll);
