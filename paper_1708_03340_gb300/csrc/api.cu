@@ -283,6 +283,7 @@ struct Plan {
   bool node_sched = false;
   bool sqrt_gram = false;  // Gramians from square-root factors (HT_PREC_FP32_SQRT)
   bool mixed = false;      // HT_PREC_MIXED: contractions on the tensor cores (k_oz.cu)
+  int panel = 64;          // TSQR panel width (columns factored by the Householder blocks at once)
   int oz_slices = kOzSlices;
   int qr_kernel = 0;       // TSQR block kernel choice (ht_trunc_opts.qr_kernel)
   int dtype = HT_F64;
@@ -405,7 +406,7 @@ struct Plan {
     g.tile0 = L.tiles;
     L.tiles += g.tiles_m * g.tiles_n * g.batch * g.ksplit;
     g.tc_tile0 = L.tc_tiles;
-    L.tc_tiles += g.tc_tiles_m * g.tc_tiles_n * g.batch * g.ksplit;
+    L.tc_tiles += g.tc_tiles_m * ((g.N + oz_gemm_tile_n() - 1) / oz_gemm_tile_n()) * g.batch * g.ksplit;
     if (mixed) {
       // BF16 slice blocks (stages of oz_stage_k() reduction indices) and
       // exponents, for this launch only; an operand that every batch entry
@@ -815,6 +816,10 @@ struct Mat {
 void plan_tsqr_narrow(Plan &P, const std::vector<Mat> &mats);
 
 constexpr int kPanel = 64;  // widest matrix the register-resident QR blocks factor
+// Panel width of the mixed path: narrower panels move QR work from the FP64
+// Householder blocks (4 m w^2 per panel) into the panel projections, which run
+// on the tensor cores.
+constexpr int kPanelMixed = 32;
 
 // Reduced QR of matrices wider than one panel: columns are taken in panels
 // of kPanel; panel p is projected twice against the finished Q columns
@@ -826,7 +831,8 @@ void plan_tsqr_panels(Plan &P, const std::vector<Mat> &mats) {
   const size_t esz = P.esz;
   const bool f64 = (P.dtype == HT_F64);
   int max_panels = 0;
-  for (const Mat &M : mats) max_panels = std::max(max_panels, (M.n + kPanel - 1) / kPanel);
+  const int pw = P.panel;
+  for (const Mat &M : mats) max_panels = std::max(max_panels, (M.n + pw - 1) / pw);
   // R starts as zero below the diagonal blocks
   P.begin(L_COPY);
   for (const Mat &M : mats) {
@@ -849,12 +855,12 @@ void plan_tsqr_panels(Plan &P, const std::vector<Mat> &mats) {
     };
     std::vector<PJ> pj;
     for (const Mat &M : mats) {
-      const int np = (M.n + kPanel - 1) / kPanel;
+      const int np = (M.n + pw - 1) / pw;
       if (p >= np) continue;
       PJ j;
       j.M = &M;
-      j.c0 = p * kPanel;
-      j.w = std::min(kPanel, M.n - j.c0);
+      j.c0 = p * pw;
+      j.w = std::min(pw, M.n - j.c0);
       j.C1 = j.C2 = nullptr;
       if (p > 0) {
         j.C1 = P.salloc_bytes((size_t)j.c0 * j.w * esz);
@@ -968,7 +974,7 @@ void plan_tsqr_panels(Plan &P, const std::vector<Mat> &mats) {
 
 void plan_tsqr(Plan &P, const std::vector<Mat> &mats) {
   std::vector<Mat> narrow, wide;
-  for (const Mat &M : mats) (M.n > kPanel ? wide : narrow).push_back(M);
+  for (const Mat &M : mats) (M.n > P.panel ? wide : narrow).push_back(M);
   if (!narrow.empty()) plan_tsqr_narrow(P, narrow);
   if (!wide.empty()) plan_tsqr_panels(P, wide);
 }
@@ -2415,6 +2421,7 @@ ht_status ht_orthogonalize(ht_tensor *x, int prec) {
   P.dtype = x->dtype;
   P.esz = x->esz;
   P.mixed = (prec == HT_PREC_MIXED);
+  if (P.mixed) P.panel = kPanelMixed;
   std::vector<TState> TS(1);
   TS[0].x = x;
   plan_orthogonalize(P, TS);
@@ -2431,6 +2438,7 @@ ht_status ht_gramians(ht_tensor *x, double *dev_out, int prec) {
   Plan P;
   P.sqrt_gram = (prec == HT_PREC_FP32_SQRT);
   P.mixed = (prec == HT_PREC_MIXED);
+  if (P.mixed) P.panel = kPanelMixed;
   P.dtype = x->dtype;
   P.esz = x->esz;
   std::vector<TState> TS(1);
@@ -2489,6 +2497,7 @@ ht_status ht_gramians_noalloc(ht_tensor *x, double *dev_out, int prec) {
   Plan P;
   P.sqrt_gram = (prec == HT_PREC_FP32_SQRT);
   P.mixed = (prec == HT_PREC_MIXED);
+  if (P.mixed) P.panel = kPanelMixed;
   P.dtype = x->dtype;
   P.esz = x->esz;
   std::vector<TState> TS(1);
@@ -2519,6 +2528,7 @@ static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_o
   P.node_sched = (o->schedule == HT_SCHED_NODE);
   P.sqrt_gram = (o->prec == HT_PREC_FP32_SQRT);
   P.mixed = (o->prec == HT_PREC_MIXED);
+  if (P.mixed) P.panel = kPanelMixed;
   P.qr_kernel = o->qr_kernel;
   std::vector<TState> TS(count);
   int total_nodes = 0;
@@ -2662,6 +2672,7 @@ ht_status ht_graph_add_truncate(const ht_tensor *const *a, const ht_tensor *cons
   P.node_sched = (o->schedule == HT_SCHED_NODE);
   P.sqrt_gram = (o->prec == HT_PREC_FP32_SQRT);
   P.mixed = (o->prec == HT_PREC_MIXED);
+  if (P.mixed) P.panel = kPanelMixed;
   P.qr_kernel = o->qr_kernel;
   std::vector<TState> TS(count);
   int total_nodes = 0;

@@ -29,8 +29,9 @@
 //     normwise error of about 2^-(8S) |A| |B| per product: S = 5 gives about
 //     2^-40 of the row scale, far below what the 1e-6 results of the mixed
 //     path need and well beyond FP32 (2^-24).
-//   * The four accumulators are read from TMEM, summed in FP64, scaled by
-//     2^(E_row + E_col) and written (or written as a split-K partial; the
+//   * The four accumulators are read from TMEM, summed in double-float FP32
+//     arithmetic and assembled into FP64 (scaled by 2^(E_row + E_col)) with
+//     integer operations, then written (or written as a split-K partial; the
 //     chunks of a long reduction are added in FP64 by the reduction kernel of
 //     k_gemm.cu).
 //
@@ -170,6 +171,56 @@ __device__ __forceinline__ uint32_t slice_bf16(int d, int i) {
   return __float_as_uint(f) >> 16;
 }
 
+// Error-free sums in FP32 (Knuth's two-sum, Dekker's fast two-sum for |a| >= |b|).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// The four accumulators D_0 + D_1 + D_2 + D_3 (in grid units) as a
+// double-float (h, l), then h + l scaled by 2^E as an FP64 bit pattern built
+// with integer operations (the FP64 pipe of this GPU runs at 1/64 of the
+// FP32 rate): h's 24-bit significand at bit 52, l's added at its offset
+// (|l| <= ulp(h) / 2, bits below 2^-52 of h's scale cut), renormalised by
+// one place if the sum crossed a power of two.  About 2^-47 relative.
+// Results below the FP64 normal range flush to zero, above it become Inf.
+__device__ __forceinline__ double combine_to_f64(float d0, float d1, float d2, float d3, int E) {
+  float s, e1, e2, h, l;
+  two_sum(d0, d1, s, e1);
+  two_sum(s, d2, s, e2);
+  fast_two_sum(s, __fadd_rn(__fadd_rn(e1, e2), d3), h, l);
+  const uint32_t bh = __float_as_uint(h);
+  const int eh = (int)((bh >> 23) & 0xFFu);
+  if (eh == 0) return 0.0;
+  long long W = (long long)((bh & 0x7FFFFFu) | 0x800000u) << 29;  // [2^52, 2^53)
+  const uint32_t bl = __float_as_uint(l);
+  const int el = (int)((bl >> 23) & 0xFFu);
+  if (el != 0) {
+    const long long ml = (long long)((bl & 0x7FFFFFu) | 0x800000u);
+    const int sh = el - eh + 29;  // <= 5
+    const long long lp = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> (-sh)) : 0ll);
+    W = ((bl ^ bh) >> 31) ? W - lp : W + lp;
+  }
+  int ex = eh - 127 + 1023 + E;
+  if (W >= (1ll << 53)) {
+    W >>= 1;
+    ++ex;
+  } else if (W < (1ll << 52)) {
+    W <<= 1;
+    --ex;
+  }
+  if (ex <= 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)(bh >> 31) << 63;
+  if (ex >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)ex << 52) | ((unsigned long long)W & 0xFFFFFFFFFFFFFull)));
+}
+
 __device__ __forceinline__ int find_split(const GemmItem *items, int n, int blk) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -216,6 +267,57 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
   chunk_range(it, chunk, f0, f1);
   const int K = it.K;
   const int tid = threadIdx.x;
+  const int nst = it.oz_stages;
+  unsigned char *out = static_cast<unsigned char *>(op ? it.ozb : it.oza) +
+                       ((((int64_t)b * tiles + tile) * it.ksplit + chunk) * nst) * S * (int64_t)OZ_BLK;
+  int *Ex = (op ? it.oeb : it.oea) + ((int64_t)b * tiles * OZ_M + (int64_t)tile * OZ_M) * it.ksplit + chunk;
+  if (sk == 1 && f1 - f0 <= 256) {
+    // reduction index contiguous in memory: one warp per row, lane l holds the
+    // 8 indices 8l .. 8l+7 of the chunk (coalesced loads, read once); the row
+    // maximum is a warp reduction and the digits come from the registers
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int r = warp; r < OZ_M; r += 8) {
+      const int grow = tile * OZ_M + r;
+      double v[8];
+      double m = 0.0;
+      bool bad = false;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int64_t f = f0 + lane * 8 + e;
+        v[e] = 0.0;
+        if (grow < rows && f < f1) {
+          const int64_t ko = f / K, k = f - ko * K;
+          v[e] = X[(int64_t)grow * sr + k + ko * sko];
+        }
+        const double a = fabs(v[e]);
+        if (!(a <= 1.7976931348623157e308)) bad = true;
+        m = a > m ? a : m;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      bad = __any_sync(0xffffffffu, bad);
+      const int ex = (int)(((unsigned long long)__double_as_longlong(m) >> 52) & 0x7FF);
+      const int E = bad ? OZ_EXP_NONFINITE : (ex ? ex - 1022 : 0);
+      if (lane == 0) Ex[(int64_t)r * it.ksplit] = E;
+      const int q = lane >> 2, kk0 = (lane & 3) * 8;
+      if (q >= nst) continue;
+      uint32_t w[S][4];
+#pragma unroll
+      for (int i = 0; i < S; ++i) w[i][0] = w[i][1] = w[i][2] = w[i][3] = 0u;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        int d[S];
+        oz_digits<S>(bad ? 0.0 : v[e], E, d);
+#pragma unroll
+        for (int i = 0; i < S; ++i) w[i][e >> 1] |= slice_bf16(d[i], i) << ((e & 1) * 16);
+      }
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+        *reinterpret_cast<uint4 *>(out + ((int64_t)q * S + i) * OZ_BLK + oz_off(r, kk0)) =
+            make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+    }
+    return;
+  }
   const int r = tid & (OZ_M - 1), h = tid >> 7;
   const int grow = tile * OZ_M + r;
   const bool row_in = grow < rows;
@@ -246,15 +348,11 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
       E = ex ? ex - 1022 : 0;  // mx = 1.f 2^(ex-1023) < 2^(ex-1022); zero / subnormal rows: digits 0
     }
     sexp[r] = E;
-    int *Ex = op ? it.oeb : it.oea;
-    Ex[((int64_t)b * tiles * OZ_M + grow) * it.ksplit + chunk] = E;
+    Ex[(int64_t)r * it.ksplit] = E;
   }
   __syncthreads();
   const int E = sexp[r];
   // pass 2: slices, 8 reduction indices of one row per step (16 bytes per slice)
-  const int nst = it.oz_stages;
-  unsigned char *out = static_cast<unsigned char *>(op ? it.ozb : it.oza) +
-                       ((((int64_t)b * tiles + tile) * it.ksplit + chunk) * nst) * S * (int64_t)OZ_BLK;
   for (int g = h; g < nst * (OZ_KC / 8); g += 2) {
     const int q = g / (OZ_KC / 8), kk0 = (g % (OZ_KC / 8)) * 8;
     uint32_t w[S][4];
@@ -278,44 +376,52 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
 }
 
 // ---------------------------------------------------------------------------
-// GEMM: one CTA per (item, 128-row tile, 128-column tile, batch, chunk)
+// GEMM: persistent CTAs (one per SM) walking the launch's tiles of 128 rows x
+// 64 columns (per item: row tiles x column tiles x batch x chunk).
 // ---------------------------------------------------------------------------
-template <int S>
-__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *__restrict__ items, int n_items,
-                                                                const int *__restrict__ ranks) {
-  extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_acc;
-  __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
-  unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const GemmItem &it = items[find_tile(items, n_items, blockIdx.x)];
-  int local = blockIdx.x - it.tc_tile0;
-  const int share = it.oz_share;
-  const int tm = local % it.tc_tiles_m;
+constexpr int OZ_TN = 64;       // columns of a GEMM tile
+constexpr int OZ_STAGES = 3;    // stage buffers of the bulk-copy ring
+constexpr uint32_t OZ_BLK_B = OZ_TN * OZ_KC * 2;  // bytes of a 64-row half of a slice block
+
+struct TileInfo {
+  const GemmItem *it;
+  int tm, tn, b, chunk, nq;
+  bool live;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const GemmItem *items, int n_items, const int *ranks, int t) {
+  TileInfo ti;
+  const GemmItem &it = items[find_tile(items, n_items, t)];
+  ti.it = &it;
+  int local = t - it.tc_tile0;
+  const int tiles_n = (it.N + OZ_TN - 1) / OZ_TN;
+  ti.tm = local % it.tc_tiles_m;
   local /= it.tc_tiles_m;
-  const int tn = local % it.tc_tiles_n;
-  local /= it.tc_tiles_n;
-  const int b = local % it.batch;
-  const int chunk = local / it.batch;
+  ti.tn = local % tiles_n;
+  local /= tiles_n;
+  ti.b = local % it.batch;
+  ti.chunk = local / it.batch;
   const int M = eff_dim(it.M, it.m_ref, 1, ranks);
   const int N = eff_dim(it.N, it.n_ref, it.n_mult, ranks);
   const int batch = eff_dim(it.batch, it.b_ref, it.b_mult, ranks);
-  const int m0 = tm * OZ_M, n0 = tn * OZ_N;
-  if (m0 >= M || n0 >= N || b >= batch) return;  // uniform for the CTA, before any TMEM is held
+  ti.live = ti.tm * OZ_M < M && ti.tn * OZ_TN < N && ti.b < batch;
   int64_t f0, f1;
-  chunk_range(it, chunk, f0, f1);
-  const int nq = (int)((f1 - f0 + OZ_KC - 1) / OZ_KC);  // stages holding data
-  const int nst = it.oz_stages;
-  constexpr uint32_t OPB = S * OZ_BLK;  // bytes of one operand's stage (all slices)
-  const int ba = (share & 1) ? 0 : b, bb = (share & 2) ? 0 : b;  // slices of a shared operand: entry 0
-  const unsigned char *gA = static_cast<const unsigned char *>(it.oza) +
-                            ((((int64_t)ba * it.tc_tiles_m + tm) * it.ksplit + chunk) * nst) * (int64_t)OPB;
-  const unsigned char *gB = static_cast<const unsigned char *>(it.ozb) +
-                            ((((int64_t)bb * it.tc_tiles_n + tn) * it.ksplit + chunk) * nst) * (int64_t)OPB;
-  const uint32_t full0 = smem_addr(&bar_full[0]), full1 = smem_addr(&bar_full[1]);
-  const uint32_t empty0 = smem_addr(&bar_empty[0]), empty1 = smem_addr(&bar_empty[1]);
-  const uint32_t accb = smem_addr(&bar_acc);
+  chunk_range(it, ti.chunk, f0, f1);
+  ti.nq = (int)((f1 - f0 + OZ_KC - 1) / OZ_KC);
+  return ti;
+}
+
+template <int S>
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *__restrict__ items, int n_items,
+                                                                int total_tiles, const int *__restrict__ ranks) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES], bar_acc_full[2], bar_acc_empty[2],
+      bar_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr uint32_t STA = S * OZ_BLK, STB = S * OZ_BLK_B, STG = STA + STB;  // bytes of one stage
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
@@ -324,11 +430,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 128) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full1) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty1) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(accb) : "memory");
+    for (int i = 0; i < OZ_STAGES; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_full[i])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_empty[i])) : "memory");
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_acc_full[i])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_addr(&bar_acc_empty[i])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_done)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_flag = 0;
   }
@@ -338,151 +448,210 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
   const uint32_t tmem = tmem_slot;
 
   if (warp == 4) {
-    // ---- producer: one bulk copy per operand and stage ----
+    // ---- producer: the stages of every live tile, through the ring ----
     if (lane == 0) {
-      for (int q = 0; q < nq; ++q) {
-        const int buf = q & 1;
-        if (q >= 2 && !mbar_wait(buf ? empty1 : empty0, (uint32_t)(((q >> 1) - 1) & 1))) {
-          atomicOr(&g_oz_status, 1u);
-          atomicExch(&abort_flag, 1);
-          break;
+      int g = 0;  // stages issued so far
+      for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const TileInfo ti = tile_info(items, n_items, ranks, t);
+        if (!ti.live) continue;
+        const GemmItem &it = *ti.it;
+        const int share = it.oz_share;
+        const int ba = (share & 1) ? 0 : ti.b, bb = (share & 2) ? 0 : ti.b;
+        const unsigned char *gA = static_cast<const unsigned char *>(it.oza) +
+                                  ((((int64_t)ba * it.tc_tiles_m + ti.tm) * it.ksplit + ti.chunk) * it.oz_stages) * (int64_t)STA;
+        const unsigned char *gB = static_cast<const unsigned char *>(it.ozb) +
+                                  ((((int64_t)bb * it.tc_tiles_n + (ti.tn >> 1)) * it.ksplit + ti.chunk) * it.oz_stages) *
+                                      (int64_t)STA +
+                                  (ti.tn & 1) * OZ_BLK_B;
+        for (int q = 0; q < ti.nq; ++q, ++g) {
+          const int slot = g % OZ_STAGES;
+          if (*(volatile int *)&abort_flag) break;
+          if (g >= OZ_STAGES && !mbar_wait(smem_addr(&bar_empty[slot]), (uint32_t)((g / OZ_STAGES - 1) & 1))) {
+            atomicOr(&g_oz_status, 1u);
+            atomicExch(&abort_flag, 1);
+            break;
+          }
+          unsigned char *sA = sm + slot * STG;
+          const uint32_t fb = smem_addr(&bar_full[slot]);
+          asm volatile(
+              "{\n\t.reg .b64 st;\n\t"
+              "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(fb),
+              "r"(STG)
+              : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_addr(sA)),
+              "l"(gA + (int64_t)q * STA), "r"(STA), "r"(fb)
+              : "memory");
+#pragma unroll
+          for (int i = 0; i < S; ++i)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_addr(sA + STA + i * OZ_BLK_B)),
+                "l"(gB + (int64_t)q * STA + i * OZ_BLK), "r"(OZ_BLK_B), "r"(fb)
+                : "memory");
         }
-        unsigned char *sA = sm + buf * 2 * OPB;
-        unsigned char *sB = sA + OPB;
-        const uint32_t fb = buf ? full1 : full0;
-        asm volatile(
-            "{\n\t.reg .b64 st;\n\t"
-            "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(fb),
-            "r"(2u * OPB)
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_addr(sA)),
-            "l"(gA + (int64_t)q * OPB), "r"(OPB), "r"(fb)
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_addr(sB)),
-            "l"(gB + (int64_t)q * OPB), "r"(OPB), "r"(fb)
-            : "memory");
+        if (*(volatile int *)&abort_flag) break;
       }
     }
   } else if (warp == 5) {
-    // ---- MMA issue: products (i, j), i + j <= S - 1, into accumulator min(i + j, 3) ----
+    // ---- MMA issue: per tile, products (i, j), i + j <= S - 1, into accumulator
+    // min(i + j, 3) of the tile's TMEM buffer (two buffers of 4 x 64 columns) ----
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(OZ_M, OZ_N);
-      bool started[4] = {false, false, false, false};
-      int q = 0;
-      for (; q < nq; ++q) {
-        const int buf = q & 1;
+      constexpr uint32_t idesc = idesc_bf16(OZ_M, OZ_TN);
+      int g = 0, n = 0;  // stages consumed, live tiles
+      for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const TileInfo ti = tile_info(items, n_items, ranks, t);
+        if (!ti.live) continue;
+        const int tb = n & 1;
         if (*(volatile int *)&abort_flag) break;
-        if (!mbar_wait(buf ? full1 : full0, (uint32_t)((q >> 1) & 1))) {
+        if (n >= 2 && !mbar_wait(smem_addr(&bar_acc_empty[tb]), (uint32_t)((n / 2 - 1) & 1))) {
           atomicOr(&g_oz_status, 1u);
           atomicExch(&abort_flag, 1);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_addr(sm + buf * 2 * OPB), b0 = a0 + OPB;
+        const uint32_t dbase = tmem + (uint32_t)(tb * 4 * OZ_TN);
+        bool ok = true;
+        for (int q = 0; q < ti.nq; ++q, ++g) {
+          const int slot = g % OZ_STAGES;
+          if (*(volatile int *)&abort_flag || !mbar_wait(smem_addr(&bar_full[slot]), (uint32_t)((g / OZ_STAGES) & 1))) {
+            atomicOr(&g_oz_status, 1u);
+            atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_addr(sm + slot * STG), b0 = a0 + STA;
 #pragma unroll
-        for (int ks = 0; ks < OZ_KC / 16; ++ks) {
+          for (int ks = 0; ks < OZ_KC / 16; ++ks) {
 #pragma unroll
-          for (int s = S - 1; s >= 0; --s) {  // smallest products first
+            for (int s = S - 1; s >= 0; --s) {  // smallest products first
 #pragma unroll
-            for (int i = 0; i <= s; ++i) {
-              const int j = s - i;
-              const int acc = s < 3 ? s : 3;
-              const uint64_t da = smem_desc(a0 + i * OZ_BLK + ks * 256);
-              const uint64_t db = smem_desc(b0 + j * OZ_BLK + ks * 256);
-              const uint32_t en = started[acc] ? 1u : 0u;
-              started[acc] = true;
-              asm volatile(
-                  "{\n\t.reg .pred p;\n\t"
-                  "setp.ne.b32 p, %4, 0;\n\t"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + (uint32_t)(acc * OZ_N)),
-                  "l"(da), "l"(db), "r"(idesc), "r"(en)
-                  : "memory");
+              for (int i = 0; i <= s; ++i) {
+                const int j = s - i;
+                const int acc = s < 3 ? s : 3;
+                const uint64_t da = smem_desc(a0 + i * OZ_BLK + ks * 256);
+                const uint64_t db = smem_desc(b0 + j * OZ_BLK_B + ks * 256);
+                // the first product into an accumulator of the tile overwrites it
+                const bool first = q == 0 && ks == 0 && i == 0 && (acc < 3 || s == S - 1);
+                const uint32_t en = first ? 0u : 1u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dbase + (uint32_t)(acc * OZ_TN)),
+                    "l"(da), "l"(db), "r"(idesc), "r"(en)
+                    : "memory");
+              }
             }
           }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_addr(&bar_empty[slot]))
+                       : "memory");
         }
-        // the buffer may be refilled once these MMAs have read it
+        if (!ok) break;
+        // the tile's accumulators are complete when this commit arrives
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         buf ? empty1 : empty0)
+                         smem_addr(&bar_acc_full[tb]))
                      : "memory");
+        ++n;
       }
-      // every MMA issued above is complete when this commit arrives (also after an abort)
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(accb)
+      // tracks every MMA issued above (also after an abort): the TMEM may be freed once it arrives
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&bar_done))
                    : "memory");
     }
   } else {
     // ---- epilogue: warps 0-3, TMEM lanes 32 w .. 32 w + 31 = tile rows ----
-    bool ok_wait = mbar_wait(accb, 0u);
-    if (!ok_wait) {
-      atomicOr(&g_oz_status, 1u);
-      mbar_wait(accb, 0u);  // once more (bounded): no issued MMA may still write the TMEM when it is freed
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // warp-uniform, so that the warp-collective TMEM loads below never diverge
-    const bool valid = __all_sync(0xffffffffu, ok_wait) && !*(volatile int *)&abort_flag;
-    const int row = m0 + warp * 32 + lane;
-    const int64_t Mpad = (int64_t)it.tc_tiles_m * OZ_M, Npad = (int64_t)it.tc_tiles_n * OZ_N;
-    const int ea = it.oea[((int64_t)ba * Mpad + row) * it.ksplit + chunk];
-    const double sa = (ea == OZ_EXP_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll)
-                                               : __longlong_as_double((long long)(ea + 1023) << 52);
-    double *Cp = static_cast<double *>(it.C) + (int64_t)b * it.scb;
-    double *Pp = it.ksplit > 1 ? static_cast<double *>(it.part) + ((int64_t)chunk * it.batch + b) * (int64_t)it.M * it.N
-                               : nullptr;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    const int n_here = (N - n0 < OZ_N) ? N - n0 : OZ_N;
-    for (int c0 = 0; c0 < n_here; c0 += 16) {
-      uint32_t v[4][16];
-      if (nq > 0 && valid) {
+    int n = 0;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+      const TileInfo ti = tile_info(items, n_items, ranks, t);
+      if (!ti.live) continue;
+      const GemmItem &it = *ti.it;
+      const int tb = n & 1;
+      bool ok = mbar_wait(smem_addr(&bar_acc_full[tb]), (uint32_t)((n / 2) & 1));
+      if (!ok) {
+        atomicOr(&g_oz_status, 1u);
+        atomicExch(&abort_flag, 1);
+      }
+      const bool valid = __all_sync(0xffffffffu, ok) && !*(volatile int *)&abort_flag;
+      if (!valid) break;  // warp-uniform
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int M = eff_dim(it.M, it.m_ref, 1, ranks);
+      const int N = eff_dim(it.N, it.n_ref, it.n_mult, ranks);
+      const int share = it.oz_share;
+      const int ba = (share & 1) ? 0 : ti.b, bb = (share & 2) ? 0 : ti.b;
+      const int row = ti.tm * OZ_M + warp * 32 + lane;
+      const int n0 = ti.tn * OZ_TN;
+      const int64_t Mpad = (int64_t)it.tc_tiles_m * OZ_M, Npad = (int64_t)it.tc_tiles_n * OZ_N;
+      const int ea = it.oea[((int64_t)ba * Mpad + row) * it.ksplit + ti.chunk];
+      double *Cp = static_cast<double *>(it.C) + (int64_t)ti.b * it.scb;
+      double *Pp = it.ksplit > 1
+                       ? static_cast<double *>(it.part) + ((int64_t)ti.chunk * it.batch + ti.b) * (int64_t)it.M * it.N
+                       : nullptr;
+      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tb * 4 * OZ_TN);
+      const int n_here = (N - n0 < OZ_TN) ? N - n0 : OZ_TN;
+      for (int c0 = 0; c0 < n_here; c0 += 16) {
+        uint32_t v[4][16];
+        if (ti.nq > 0) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          if (a >= S) {
+          for (int a = 0; a < 4; ++a) {
+            if (a >= S) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) v[a][j] = 0u;
+              continue;
+            }
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];"
+                : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
+                  "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]), "=r"(v[a][10]), "=r"(v[a][11]),
+                  "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]), "=r"(v[a][15])
+                : "r"(trow + (uint32_t)(a * OZ_TN + c0)));
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        } else {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[a][j] = 0u;
-            continue;
+        }
+        if (row >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col >= N) break;
+          const int eb = it.oeb[((int64_t)bb * Npad + col) * it.ksplit + ti.chunk];
+          double val;
+          if (eb == OZ_EXP_NONFINITE || ea == OZ_EXP_NONFINITE) {
+            val = __longlong_as_double(0x7FF8000000000000ll);
+          } else {
+            val = combine_to_f64(__uint_as_float(v[0][j]), __uint_as_float(v[1][j]), __uint_as_float(v[2][j]),
+                                 __uint_as_float(v[3][j]), ea + eb);
           }
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-              "%14, %15}, [%16];"
-              : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
-                "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]), "=r"(v[a][10]), "=r"(v[a][11]),
-                "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]), "=r"(v[a][15])
-              : "r"(trow + (uint32_t)(a * OZ_N + c0)));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      } else {
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int j = 0; j < 16; ++j) v[a][j] = 0u;
-      }
-      if (row >= M) continue;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = n0 + c0 + j;
-        if (col >= N) break;
-        const int eb = it.oeb[((int64_t)bb * Npad + col) * it.ksplit + chunk];
-        double val;
-        if (!valid || eb == OZ_EXP_NONFINITE) {
-          val = __longlong_as_double(0x7FF8000000000000ll);
-        } else {
-          const double sum = ((double)__uint_as_float(v[0][j]) + (double)__uint_as_float(v[1][j])) +
-                             ((double)__uint_as_float(v[2][j]) + (double)__uint_as_float(v[3][j]));
-          const double sb = __longlong_as_double((long long)(eb + 1023) << 52);
-          val = (sum * sa) * sb;
-        }
-        if (Pp) {
-          Pp[(int64_t)col * it.M + row] = val;
-        } else {
-          double *c = Cp + (int64_t)row * it.scm + (int64_t)col * it.scn;
-          double o = it.alpha * val;
-          if (it.beta != 0.0) o += it.beta * *c;
-          *c = o;
+          if (Pp) {
+            Pp[(int64_t)col * it.M + row] = val;
+          } else {
+            double *c = Cp + (int64_t)row * it.scm + (int64_t)col * it.scn;
+            // alpha = +-1 and beta = 0 (all but the TSQR panel updates) need no FP64 arithmetic
+            double o = it.alpha == 1.0 ? val : (it.alpha == -1.0 ? -val : it.alpha * val);
+            if (it.beta != 0.0) o += it.beta * *c;
+            *c = o;
+          }
         }
       }
+      // every load of this tile's buffer has completed (wait::ld above): hand it back
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                       smem_addr(&bar_acc_empty[tb]))
+                   : "memory");
+      ++n;
     }
+  }
+  // all MMAs complete (bounded wait) before the TMEM is freed
+  if (warp == 5) {
+    if (lane == 0 && !mbar_wait(smem_addr(&bar_done), 0u)) atomicOr(&g_oz_status, 1u);
+    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -498,12 +667,13 @@ cudaError_t launch_oz_s(const GemmItem *d_items, int n_items, int split_blocks, 
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = 2 * 2 * (size_t)S * OZ_BLK + 1024;
-  // at least 116 KB: one CTA per SM, which holds all 512 TMEM columns
-  const size_t smem_req = smem > 116 * 1024 ? smem : 116 * 1024;
-  e = cudaFuncSetAttribute(oz_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
+  const size_t smem = OZ_STAGES * (size_t)S * (OZ_BLK + OZ_BLK_B) + 1024;
+  e = cudaFuncSetAttribute(oz_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  oz_gemm_kernel<S><<<tiles, OZ_THREADS, smem_req, s>>>(d_items, n_items, d_ranks);
+  int dev = 0, sms = kSmCount;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = tiles < sms ? tiles : sms;  // persistent: one CTA per SM (it holds all 512 TMEM columns)
+  oz_gemm_kernel<S><<<grid, OZ_THREADS, smem, s>>>(d_items, n_items, tiles, d_ranks);
   count_launch();
   return cudaGetLastError();
 }
@@ -512,6 +682,7 @@ cudaError_t launch_oz_s(const GemmItem *d_items, int n_items, int split_blocks, 
 
 int oz_tile_m() { return OZ_M; }
 int oz_tile_n() { return OZ_N; }
+int oz_gemm_tile_n() { return OZ_TN; }
 int oz_stage_k() { return OZ_KC; }
 int oz_block_bytes() { return (int)OZ_BLK; }
 
