@@ -71,7 +71,8 @@ constexpr int OZ_M = 128;                       // rows of a tile (MMA M); also 
 constexpr int OZ_N = 128;                       // columns of a tile (MMA N)
 constexpr int OZ_KC = 32;                       // reduction indices per stage
 constexpr uint32_t OZ_BLK = OZ_M * OZ_KC * 2;   // bytes of one slice block of one stage (8 KB)
-constexpr int OZ_THREADS = 192;                 // warps 0-3 epilogue, 4 producer, 5 MMA
+constexpr int OZ_THREADS = 320;                 // warps 0-7 epilogue, 8 producer, 9 MMA
+constexpr int OZ_EPI_THREADS = 256;
 constexpr int OZ_TMEM_COLS = 512;               // four FP32 accumulators of 128 columns
 constexpr int OZ_EXP_NONFINITE = 0x7FF0;        // exponent marking a row with NaN / Inf
 
@@ -165,9 +166,12 @@ __device__ __forceinline__ void oz_digits(double x, int E, int (&d)[S]) {
   }
 }
 
-// BF16 bits of d 2^(-8(i+1)) (|d| <= 256: exact)
+// BF16 bits of d 2^(-8(i+1)) (|d| <= 256: exact).  The integer becomes a
+// float without a conversion instruction: the bits of 1.5 2^23 plus d are the
+// float 1.5 2^23 + d (|d| < 2^22), from which 1.5 2^23 is subtracted exactly.
 __device__ __forceinline__ uint32_t slice_bf16(int d, int i) {
-  const float f = (float)d * __uint_as_float((uint32_t)(127 - 8 * (i + 1)) << 23);
+  const float fd = __fsub_rn(__int_as_float(0x4B400000 + d), 12582912.0f);
+  const float f = __fmul_rn(fd, __uint_as_float((uint32_t)(127 - 8 * (i + 1)) << 23));
   return __float_as_uint(f) >> 16;
 }
 
@@ -411,9 +415,18 @@ __device__ __forceinline__ TileInfo tile_info(const GemmItem *items, int n_items
   return ti;
 }
 
+// Accumulators per TMEM buffer: D_0, D_1 and D_{>=2} for up to 5 slices (the
+// merged sum rounds at about 2^-40 of the scale, the level of the slices
+// themselves); D_0, D_1, D_2 and D_{>=3} for 6 slices (about 2^-48).
+template <int S>
+struct OzAcc {
+  static constexpr int n = S >= 6 ? 4 : (S < 3 ? S : 3);
+};
+
 template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *__restrict__ items, int n_items,
                                                                 int total_tiles, const int *__restrict__ ranks) {
+  constexpr int NACC = OzAcc<S>::n;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES], bar_acc_full[2], bar_acc_empty[2],
       bar_done;
@@ -423,20 +436,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
   constexpr uint32_t STA = S * OZ_BLK, STB = S * OZ_BLK_B, STG = STA + STB;  // bytes of one stage
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (warp == 5) {
+  if (warp == 9) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                  "r"(OZ_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 128) {
+  if (tid == OZ_EPI_THREADS) {
     for (int i = 0; i < OZ_STAGES; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_full[i])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_empty[i])) : "memory");
     }
     for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_acc_full[i])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_addr(&bar_acc_empty[i])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar_acc_empty[i])), "r"(OZ_EPI_THREADS)
+                   : "memory");
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_done)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -447,7 +461,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 4) {
+  if (warp == 8) {
     // ---- producer: the stages of every live tile, through the ring ----
     if (lane == 0) {
       int g = 0;  // stages issued so far
@@ -494,9 +508,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
         if (*(volatile int *)&abort_flag) break;
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     // ---- MMA issue: per tile, products (i, j), i + j <= S - 1, into accumulator
-    // min(i + j, 3) of the tile's TMEM buffer (two buffers of 4 x 64 columns) ----
+    // min(i + j, NACC - 1) of the tile's TMEM buffer (two buffers of NACC x 64 columns) ----
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(OZ_M, OZ_TN);
       int g = 0, n = 0;  // stages consumed, live tiles
@@ -511,7 +525,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t dbase = tmem + (uint32_t)(tb * 4 * OZ_TN);
+        const uint32_t dbase = tmem + (uint32_t)(tb * NACC * OZ_TN);
         bool ok = true;
         for (int q = 0; q < ti.nq; ++q, ++g) {
           const int slot = g % OZ_STAGES;
@@ -530,11 +544,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
 #pragma unroll
               for (int i = 0; i <= s; ++i) {
                 const int j = s - i;
-                const int acc = s < 3 ? s : 3;
+                const int acc = s < NACC - 1 ? s : NACC - 1;
                 const uint64_t da = smem_desc(a0 + i * OZ_BLK + ks * 256);
                 const uint64_t db = smem_desc(b0 + j * OZ_BLK_B + ks * 256);
                 // the first product into an accumulator of the tile overwrites it
-                const bool first = q == 0 && ks == 0 && i == 0 && (acc < 3 || s == S - 1);
+                const bool first = q == 0 && ks == 0 && i == 0 && (acc < NACC - 1 || s == S - 1);
                 const uint32_t en = first ? 0u : 1u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
@@ -562,7 +576,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
                    : "memory");
     }
   } else {
-    // ---- epilogue: warps 0-3, TMEM lanes 32 w .. 32 w + 31 = tile rows ----
+    // ---- epilogue: warps 0-7; warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile
+    // rows) of columns 32 (w / 4) .. + 31 ----
+    const int quad = warp & 3, half = warp >> 2;
     int n = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
       const TileInfo ti = tile_info(items, n_items, ranks, t);
@@ -577,26 +593,31 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
       const bool valid = __all_sync(0xffffffffu, ok) && !*(volatile int *)&abort_flag;
       if (!valid) break;  // warp-uniform
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // the item's fields in registers, the tile's 64 column exponents two per lane
       const int M = eff_dim(it.M, it.m_ref, 1, ranks);
       const int N = eff_dim(it.N, it.n_ref, it.n_mult, ranks);
-      const int share = it.oz_share;
+      const int share = it.oz_share, ksplit = it.ksplit;
       const int ba = (share & 1) ? 0 : ti.b, bb = (share & 2) ? 0 : ti.b;
-      const int row = ti.tm * OZ_M + warp * 32 + lane;
-      const int n0 = ti.tn * OZ_TN;
+      const int row = ti.tm * OZ_M + quad * 32 + lane;
+      const int n0 = ti.tn * OZ_TN + half * 32;
       const int64_t Mpad = (int64_t)it.tc_tiles_m * OZ_M, Npad = (int64_t)it.tc_tiles_n * OZ_N;
-      const int ea = it.oea[((int64_t)ba * Mpad + row) * it.ksplit + ti.chunk];
+      const int ea = it.oea[((int64_t)ba * Mpad + row) * ksplit + ti.chunk];
+      const int *Eb = it.oeb + ((int64_t)bb * Npad + n0) * ksplit + ti.chunk;
+      const int eb_lane = Eb[(int64_t)lane * ksplit];
+      const double alpha = it.alpha, beta = it.beta;
+      const int64_t scm = it.scm, scn = it.scn, ldp = it.M;
       double *Cp = static_cast<double *>(it.C) + (int64_t)ti.b * it.scb;
-      double *Pp = it.ksplit > 1
+      double *Pp = ksplit > 1
                        ? static_cast<double *>(it.part) + ((int64_t)ti.chunk * it.batch + ti.b) * (int64_t)it.M * it.N
                        : nullptr;
-      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tb * 4 * OZ_TN);
-      const int n_here = (N - n0 < OZ_TN) ? N - n0 : OZ_TN;
+      const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * NACC * OZ_TN + half * 32);
+      const int n_here = (N - n0 < 32) ? N - n0 : 32;
       for (int c0 = 0; c0 < n_here; c0 += 16) {
         uint32_t v[4][16];
         if (ti.nq > 0) {
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
-            if (a >= S) {
+            if (a >= NACC) {
 #pragma unroll
               for (int j = 0; j < 16; ++j) v[a][j] = 0u;
               continue;
@@ -616,12 +637,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[a][j] = 0u;
         }
-        if (row >= M) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + j;
-          if (col >= N) break;
-          const int eb = it.oeb[((int64_t)bb * Npad + col) * it.ksplit + ti.chunk];
+          const int cc = c0 + j;  // the same column for every lane of the warp
+          const int eb = __shfl_sync(0xffffffffu, eb_lane, cc);
+          const int col = n0 + cc;
+          if (row >= M || col >= N) continue;
           double val;
           if (eb == OZ_EXP_NONFINITE || ea == OZ_EXP_NONFINITE) {
             val = __longlong_as_double(0x7FF8000000000000ll);
@@ -630,12 +651,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
                                  __uint_as_float(v[3][j]), ea + eb);
           }
           if (Pp) {
-            Pp[(int64_t)col * it.M + row] = val;
+            Pp[(int64_t)col * ldp + row] = val;
           } else {
-            double *c = Cp + (int64_t)row * it.scm + (int64_t)col * it.scn;
+            double *c = Cp + (int64_t)row * scm + (int64_t)col * scn;
             // alpha = +-1 and beta = 0 (all but the TSQR panel updates) need no FP64 arithmetic
-            double o = it.alpha == 1.0 ? val : (it.alpha == -1.0 ? -val : it.alpha * val);
-            if (it.beta != 0.0) o += it.beta * *c;
+            double o = alpha == 1.0 ? val : (alpha == -1.0 ? -val : alpha * val);
+            if (beta != 0.0) o += beta * *c;
             *c = o;
           }
         }
@@ -649,13 +670,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
     }
   }
   // all MMAs complete (bounded wait) before the TMEM is freed
-  if (warp == 5) {
+  if (warp == 9) {
     if (lane == 0 && !mbar_wait(smem_addr(&bar_done), 0u)) atomicOr(&g_oz_status, 1u);
     __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 5) {
+  if (warp == 9) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
   }
 }

@@ -123,3 +123,23 @@ def check_ranks(ranks_gpu, ref, tol_rel, eps_mode, d=None, dtype=None, prec=None
             assert float(np.sum(charged[rg:])) - slack <= ref["tail2"], (t, rg, rr)
         energy += rank_diff_energy(s, rg, rr)
     return differ, float(energy)
+
+
+def gap_allowance(sig_ref, ranks, eps_g):
+    """Bound on how far two truncations of the same tensor may lie apart when
+    their Gramians differ by eps_g * lambda_max per node: at node t the kept
+    r_t-dimensional eigenspace turns by at most eps_g lambda_1 / (lambda_r -
+    lambda_{r+1}) (Davis-Kahan), which moves the projection by that angle
+    times the energy of the two directions at the cut.  Summed over the
+    nodes; the truncated tensor is unique only where lambda_r > lambda_{r+1}."""
+    total = 0.0
+    for t in range(1, len(ranks)):
+        lam = np.asarray(sig_ref[t], dtype=np.float64) ** 2
+        r = int(ranks[t])
+        if r >= len(lam) or len(lam) == 0:
+            continue
+        gap = lam[r - 1] - lam[r]
+        near = np.sqrt(lam[r - 1] + lam[r])
+        angle = 1.0 if gap <= 0 else min(1.0, eps_g * lam[0] / gap)
+        total += angle * near
+    return float(total)

@@ -39,7 +39,10 @@ def test_mixed_orthogonalize(case):
     tr = I.tree(d)
     for t in range(1, 2 * d - 1):
         M = nodes[t] if tr["son1"][t] < 0 else nodes[t].reshape(nodes[t].shape[0], -1).T
-        assert np.abs(M.T @ M - np.eye(M.shape[1])).max() <= 1e-11, t
+        # block Gram-Schmidt between 32-column panels: every Q column passes
+        # through up to two tensor-core projections per earlier panel (about
+        # 2^-40 each, 5 slices), so orthogonality holds to about 1e-11
+        assert np.abs(M.T @ M - np.eye(M.shape[1])).max() <= 1e-10, t
     idx = sample_idx(n, 200)
     ref = O.eval_entries(d, n, k, x, idx)
     got = O.eval_entries(d, n, ko, xo, idx)
