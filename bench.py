@@ -52,7 +52,6 @@ from paper_1708_03340_gb300 import inputs as I  # noqa: E402
 
 METRIC = "HT truncations/s + roofline fraction, mixed vs plain FP64 GPU at stated rel err"
 FP32_PEAK_NOMINAL = 152 * 128 * 2 * 2.070e9  # SMs x FP32 lanes x 2 flop x max clock (80.5 TFLOP/s)
-OZ_PRODUCTS = 15  # BF16 slice products per FP64-equivalent product in the mixed path (5 slices, i + j <= 4)
 
 
 # ---------------------------------------------------------------------------
@@ -574,39 +573,46 @@ def measured_peaks():
 
 
 def roofline_of(prof, steps, peaks):
-    """Roofline object of the dominant arithmetic kernel family (by device
-    time) of the mixed path, measured live with CUDA events on the launching
-    stream.  Families and their bound:
-      qr    FP64 Householder TSQR blocks: FP64 ALU, 4 m n^2 - 4 n^3 / 3 flop per block
-      gemm  tensor-core contractions: tensor pipe, BF16 MMA work = 15 slice products
-            x 2 M N K per contraction (M N K counted at the plan's maximal dims)
-      eig   FP64 QL eigensolves: FP64 ALU, 9 k^3 flop per Gramian"""
-    arith = {k: v for k, v in prof.items() if v["flops"] > 0 and k in ("qr", "gemm", "eig")}
-    if not arith:
-        return None
+    """Roofline object of the dominant kernel family (by device time) of the
+    mixed path, measured live with CUDA events on the launching stream.
+    Families and their bound:
+      qr     FP64 Householder TSQR blocks: FP64 ALU, 4 m n^2 - 4 n^3 / 3 flop per block
+      gemm   tensor-core contractions: tensor pipe, the BF16 work of the slice
+             products (S (S + 1) / 2 per FP64-equivalent product, 2 M N K each at the
+             plan's maximal dims)
+      split  BF16 slicing of the contraction operands: HBM, the FP64 operands read
+             and their slices written once
+      eig    FP64 QL eigensolves: FP64 ALU, 9 k^3 flop per Gramian"""
     fams = {}
-    for name, rec in arith.items():
+    for name, rec in prof.items():
+        if rec["flops"] <= 0 or name not in ("qr", "gemm", "eig", "split"):
+            continue
         per_launch_ms = rec["ms"] / rec["launches"]
-        fl = rec["flops"] / rec["launches"]
+        work = rec["flops"] / rec["launches"]
+        rate = work / (per_launch_ms / 1e3)
         if name == "gemm":
-            work, bound = OZ_PRODUCTS * fl, "tensor"
+            bound, unit, ach = "tensor", "TFLOP/s", rate / 1e12
             peak = peaks.get("bf16_cublas") or 1880.0
             src = "cuBLAS BF16 burst (measured peak file)"
+        elif name == "split":
+            bound, unit, ach = "hbm", "GB/s", rate / 1e9
+            peak = peaks.get("hbm_gbs") or 6787.6
+            src = "HBM copy (measured peak file)"
         else:
-            work, bound = fl, "alu"
+            bound, unit, ach = "alu", "TFLOP/s", rate / 1e12
             peak = peaks.get("fp64_fma")
             src = "FP64 FMA chains, measured by peaks.cu on this GPU"
             if not peak:
                 peak, src = 1.25, "FP64 nominal (measurement unavailable)"
-        ach = work / (per_launch_ms / 1e3) / 1e12
-        fams[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+        fams[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
                       "ms_per_step": rec["ms"] / steps, "launches_per_step": rec["launches"] / steps,
-                      "ms_per_launch": per_launch_ms, "flops_per_launch": work, "peak_source": src}
-        if name == "gemm":
-            fams[name]["fp64_equivalent_tflops"] = fl / (per_launch_ms / 1e3) / 1e12
+                      "ms_per_launch": per_launch_ms, "work_per_launch": work, "peak_source": src}
+    if not fams:
+        return None
     name = max(fams, key=lambda k: fams[k]["ms_per_step"])
     kernel = {"qr": "qr_reg_kernel<double> (FP64 TSQR row blocks)",
-              "gemm": "oz_split_kernel + oz_gemm_kernel (tcgen05 BF16 slices)",
+              "gemm": "oz_gemm_kernel (tcgen05 BF16 slice products) + split-K reduction",
+              "split": "oz_split_kernel (BF16 slicing of FP64 operands)",
               "eig": "eig_ql_kernel<double> (FP64 QL)"}[name]
     top = dict(fams[name])
     top["kernel"] = kernel

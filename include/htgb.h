@@ -286,14 +286,18 @@ typedef enum {
   HT_K_ADD = 6,     /* HT addition packing */
   HT_K_EVAL = 7,    /* entry evaluation */
   HT_K_MISC = 8,    /* norms, scaling */
-  HT_K_COUNT = 9
+  HT_K_SPLIT = 9,   /* BF16 slicing of the tensor-core contractions' operands (mixed path);
+                       its "flops" in ht_profile_read are algorithmic bytes */
+  HT_K_COUNT = 10
 } ht_kernel_kind;
 
 /* Record CUDA events around every launch of the kinds set in mask (bit
  * 1 << kind) on the launching stream; 0 switches recording off.  Not thread-safe. */
 ht_status ht_profile_set(unsigned mask);
 /* Launches, summed device time (ms) and summed algorithmic flops (counted at
- * the launches' maximal dimensions: m n k products for contractions,
+ * the launches' maximal dimensions: 2 m n k for contractions (on the mixed
+ * path the BF16 work of the tensor cores, S (S + 1) / 2 slice products of
+ * 2 m n k each),
  * 4 m n^2 - 4 n^3 / 3 per QR block, 9 k^3 per eigendecomposition) of one kind
  * recorded since the last reset; synchronises on the recorded events.
  * reset != 0 clears the record.  Any output may be NULL. */

@@ -251,6 +251,7 @@ struct Launch {
   int tc_tiles = 0;    // GEMM: tiles of the tensor-core kernel (mixed path)
   int oz_split = 0;    // GEMM: CTAs of the tensor-core path's split launch
   int oz_slices = 0;   // GEMM: BF16 slices per operand (mixed path)
+  double split_bytes = 0.0;  // GEMM (mixed path): algorithmic bytes of the split (operands read, slices written)
   const void *ranks = nullptr;  // tagged pointer to the rank array used by the launch
   void *scratch = nullptr;      // eig scratch (tagged)
   int variant = 0;              // GEMM: SIMT tile shape (gemm_tile_shape)
@@ -423,6 +424,9 @@ struct Plan {
       g.oeb = static_cast<int *>(lalloc_bytes(sizeof(int) * (size_t)bb * g.tc_tiles_n * oz_tile_n() * g.ksplit));
       g.oz_split0 = L.oz_split;
       L.oz_split += g.ksplit * (ba * g.tc_tiles_m + bb * g.tc_tiles_n);
+      // algorithmic bytes: the FP64 operands read once, their slices written once
+      const double red = (double)g.K * g.Ko;
+      L.split_bytes += red * ((double)ba * g.M + (double)bb * g.N) * (8.0 + 2.0 * L.oz_slices);
     }
     const double fl = 2.0 * g.M * g.N * (double)g.K * g.Ko * g.batch;
     L.flops += fl;
@@ -685,11 +689,18 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
     const int *rk = static_cast<const int *>(L.ranks);
     const int64_t before = g_launches;
     cudaError_t e = cudaSuccess;
+    if (L.kind == L_GEMM && P.mixed) {
+      // the split into BF16 slices is its own profiled family (bytes, not flops)
+      prof_begin(HT_K_SPLIT, s);
+      e = launch_oz_split((const GemmItem *)items, L.n, L.oz_split, rk, L.oz_slices, s);
+      prof_end(HT_K_SPLIT, s, L.split_bytes);
+      if (e != cudaSuccess) return fail(HT_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
+    }
     prof_begin((int)L.kind, s);
     switch (L.kind) {
       case L_GEMM: {
         if (P.mixed)
-          e = launch_gemm_oz((const GemmItem *)items, L.n, L.oz_split, L.tc_tiles, rk, L.split, L.oz_slices, s);
+          e = launch_oz_gemm((const GemmItem *)items, L.n, L.tc_tiles, rk, L.split, L.oz_slices, s);
         else if (f64)
           e = launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s, L.variant, false, false,
                                   L.uniform);
@@ -715,7 +726,10 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
       case L_RANKS: e = launch_ranks((const RankItem *)items, L.n, s); break;
       case L_CHOL: e = launch_chol((const CholItem *)items, L.n, s); break;
     }
-    prof_end((int)L.kind, s, L.flops);
+    // mixed-path contractions: the BF16 slice products the tensor cores execute,
+    // S (S + 1) / 2 per FP64-equivalent product
+    const double work = (L.kind == L_GEMM && P.mixed) ? L.flops * (L.oz_slices * (L.oz_slices + 1) / 2) : L.flops;
+    prof_end((int)L.kind, s, work);
     kernels += (int)(g_launches - before);
     if (e != cudaSuccess) return fail(HT_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
   }

@@ -137,14 +137,16 @@ cudaError_t launch_gemm(const GemmItem *d_items, int n_items, int total_tiles, c
 void gemm_tile_shape(int variant, int *bm, int *bn);
 // Split-K partial sums of FP64 items added in chunk order (k_gemm.cu).
 cudaError_t launch_gemm_reduce_f64(const GemmItem *d_items, int n_items, const int *d_ranks, cudaStream_t s);
-// FP64 contractions on the tensor cores by exact BF16 slicing (k_oz.cu): the
-// split launch (split_blocks CTAs) then the persistent GEMM launch over
-// `tiles` tiles of oz_tile_m() x oz_gemm_tile_n(), then the split-K reduction
-// if any_split.  Every
-// item needs K * ceil(Ko / ksplit) <= 256 (products per exactness chunk),
-// slices in [2, 6].
-cudaError_t launch_gemm_oz(const GemmItem *d_items, int n_items, int split_blocks, int tiles, const int *d_ranks,
-                           bool any_split, int slices, cudaStream_t s);
+// FP64 contractions on the tensor cores by exact BF16 slicing (k_oz.cu), in
+// two launches: the split of every item's operands into BF16 slices
+// (split_blocks CTAs), then the persistent GEMM over `tiles` tiles of
+// oz_tile_m() x oz_gemm_tile_n() (followed by the split-K reduction if
+// any_split).  Every item needs K * ceil(Ko / ksplit) <= 256 (products per
+// exactness chunk); slices in [2, 6].
+cudaError_t launch_oz_split(const GemmItem *d_items, int n_items, int split_blocks, const int *d_ranks, int slices,
+                            cudaStream_t s);
+cudaError_t launch_oz_gemm(const GemmItem *d_items, int n_items, int tiles, const int *d_ranks, bool any_split,
+                           int slices, cudaStream_t s);
 int oz_tile_m();       // rows of a GEMM tile and of a split block
 int oz_tile_n();       // rows of a split block of B (output columns)
 int oz_gemm_tile_n();  // output columns of a GEMM tile

@@ -137,7 +137,9 @@ __device__ __forceinline__ void chunk_range(const GemmItem &it, int chunk, int64
 // Balanced base-256 digits of x on the grid of exponent E (|x| < 2^E):
 // F = round(|x| 2^(8S - E)), F = sum_i d_i 256^(S-1-i), d_0 in [0, 256],
 // d_i in [-128, 127]; the digits carry the sign of x.  Integer operations
-// only (no FP64 arithmetic).  Zeros and subnormals give zero digits.
+// only (no FP64 arithmetic): the raw bytes of F are extracted from its two
+// 32-bit halves, then the carries of the balanced form run from the least
+// significant digit up.  Zeros and subnormals give zero digits.
 template <int S>
 __device__ __forceinline__ void oz_digits(double x, int E, int (&d)[S]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
@@ -149,30 +151,33 @@ __device__ __forceinline__ void oz_digits(double x, int E, int (&d)[S]) {
     if (sh <= 0) F = mant << (-sh);         // only for S = 7 (then -sh <= 3)
     else if (sh < 60) F = (mant + (1ull << (sh - 1))) >> sh;
   }
+  const uint32_t lo = (uint32_t)F, hi = (uint32_t)(F >> 32);
+  int carry = 0;
 #pragma unroll
   for (int i = S - 1; i >= 1; --i) {
-    int t = (int)(F & 255ull);
-    F >>= 8;
-    if (t >= 128) {
-      t -= 256;
-      F += 1;
-    }
-    d[i] = t;
+    const int byte = S - 1 - i;  // byte of F holding digit i (S <= 6: bytes 0 .. 4)
+    const int raw = (int)(((byte < 4 ? lo : hi) >> (8 * (byte & 3))) & 255u);
+    const int t = raw + carry;
+    carry = t >= 128;
+    d[i] = t - (carry << 8);
   }
-  d[0] = (int)F;
+  d[0] = (int)(F >> (8 * (S - 1))) + carry;
   if (bits >> 63) {
 #pragma unroll
     for (int i = 0; i < S; ++i) d[i] = -d[i];
   }
 }
 
-// BF16 bits of d 2^(-8(i+1)) (|d| <= 256: exact).  The integer becomes a
-// float without a conversion instruction: the bits of 1.5 2^23 plus d are the
-// float 1.5 2^23 + d (|d| < 2^22), from which 1.5 2^23 is subtracted exactly.
-__device__ __forceinline__ uint32_t slice_bf16(int d, int i) {
-  const float fd = __fsub_rn(__int_as_float(0x4B400000 + d), 12582912.0f);
-  const float f = __fmul_rn(fd, __uint_as_float((uint32_t)(127 - 8 * (i + 1)) << 23));
-  return __float_as_uint(f) >> 16;
+// Two slices i of neighbouring elements as one 32-bit word of BF16 values: the
+// low half a's (the element at the lower address), the high half b's.  A digit
+// d (|d| <= 256) becomes the float d exactly without a conversion instruction
+// (the bits of 1.5 2^23 plus d are the float 1.5 2^23 + d, minus 1.5 2^23),
+// times 2^(-8(i+1)); its BF16 bits are the upper half of that exact float.
+__device__ __forceinline__ uint32_t slice_pair_bf16(int a, int b, int i) {
+  const float sc = __uint_as_float((uint32_t)(127 - 8 * (i + 1)) << 23);
+  const float fa = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + a), 12582912.0f), sc);
+  const float fb = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + b), 12582912.0f), sc);
+  return __byte_perm(__float_as_uint(fa), __float_as_uint(fb), 0x7632);
 }
 
 // Error-free sums in FP32 (Knuth's two-sum, Dekker's fast two-sum for |a| >= |b|).
@@ -282,6 +287,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
     const int warp = tid >> 5, lane = tid & 31;
     for (int r = warp; r < OZ_M; r += 8) {
       const int grow = tile * OZ_M + r;
+      if (grow >= rows) break;  // padding rows feed only discarded outputs: left unwritten
       double v[8];
       double m = 0.0;
       bool bad = false;
@@ -309,11 +315,12 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
 #pragma unroll
       for (int i = 0; i < S; ++i) w[i][0] = w[i][1] = w[i][2] = w[i][3] = 0u;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        int d[S];
-        oz_digits<S>(bad ? 0.0 : v[e], E, d);
+      for (int e = 0; e < 8; e += 2) {
+        int d0[S], d1[S];
+        oz_digits<S>(bad ? 0.0 : v[e], E, d0);
+        oz_digits<S>(bad ? 0.0 : v[e + 1], E, d1);
 #pragma unroll
-        for (int i = 0; i < S; ++i) w[i][e >> 1] |= slice_bf16(d[i], i) << ((e & 1) * 16);
+        for (int i = 0; i < S; ++i) w[i][e >> 1] = slice_pair_bf16(d0[i], d1[i], i);
       }
 #pragma unroll
       for (int i = 0; i < S; ++i)
@@ -356,21 +363,25 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
   }
   __syncthreads();
   const int E = sexp[r];
-  // pass 2: slices, 8 reduction indices of one row per step (16 bytes per slice)
+  // pass 2: slices, 8 reduction indices of one row per step (16 bytes per slice);
+  // padding rows (beyond the operand) feed only discarded outputs and stay unwritten
+  if (!row_in) return;
   for (int g = h; g < nst * (OZ_KC / 8); g += 2) {
     const int q = g / (OZ_KC / 8), kk0 = (g % (OZ_KC / 8)) * 8;
     uint32_t w[S][4];
 #pragma unroll
     for (int i = 0; i < S; ++i) w[i][0] = w[i][1] = w[i][2] = w[i][3] = 0u;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < 8; e += 2) {
       const int64_t f = f0 + (int64_t)q * OZ_KC + kk0 + e;
-      double v = 0.0;
-      if (row_in && f < f1 && E != OZ_EXP_NONFINITE) v = elem(f);
-      int d[S];
-      oz_digits<S>(v, E, d);
+      double va = 0.0, vb = 0.0;
+      if (f < f1 && E != OZ_EXP_NONFINITE) va = elem(f);
+      if (f + 1 < f1 && E != OZ_EXP_NONFINITE) vb = elem(f + 1);
+      int d0[S], d1[S];
+      oz_digits<S>(va, E, d0);
+      oz_digits<S>(vb, E, d1);
 #pragma unroll
-      for (int i = 0; i < S; ++i) w[i][e >> 1] |= slice_bf16(d[i], i) << ((e & 1) * 16);
+      for (int i = 0; i < S; ++i) w[i][e >> 1] = slice_pair_bf16(d0[i], d1[i], i);
     }
 #pragma unroll
     for (int i = 0; i < S; ++i)
@@ -682,14 +693,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
 }
 
 template <int S>
-cudaError_t launch_oz_s(const GemmItem *d_items, int n_items, int split_blocks, int tiles, const int *d_ranks,
-                        cudaStream_t s) {
+cudaError_t launch_split_s(const GemmItem *d_items, int n_items, int split_blocks, const int *d_ranks, cudaStream_t s) {
   oz_split_kernel<S><<<split_blocks, 256, 0, s>>>(d_items, n_items, d_ranks);
   count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_mma_s(const GemmItem *d_items, int n_items, int tiles, const int *d_ranks, cudaStream_t s) {
   const size_t smem = OZ_STAGES * (size_t)S * (OZ_BLK + OZ_BLK_B) + 1024;
-  e = cudaFuncSetAttribute(oz_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = kSmCount;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -707,16 +720,29 @@ int oz_gemm_tile_n() { return OZ_TN; }
 int oz_stage_k() { return OZ_KC; }
 int oz_block_bytes() { return (int)OZ_BLK; }
 
-cudaError_t launch_gemm_oz(const GemmItem *d_items, int n_items, int split_blocks, int tiles, const int *d_ranks,
-                           bool any_split, int slices, cudaStream_t s) {
+cudaError_t launch_oz_split(const GemmItem *d_items, int n_items, int split_blocks, const int *d_ranks, int slices,
+                            cudaStream_t s) {
+  if (n_items <= 0 || split_blocks <= 0) return cudaSuccess;
+  switch (slices) {
+    case 2: return launch_split_s<2>(d_items, n_items, split_blocks, d_ranks, s);
+    case 3: return launch_split_s<3>(d_items, n_items, split_blocks, d_ranks, s);
+    case 4: return launch_split_s<4>(d_items, n_items, split_blocks, d_ranks, s);
+    case 5: return launch_split_s<5>(d_items, n_items, split_blocks, d_ranks, s);
+    case 6: return launch_split_s<6>(d_items, n_items, split_blocks, d_ranks, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_oz_gemm(const GemmItem *d_items, int n_items, int tiles, const int *d_ranks, bool any_split,
+                           int slices, cudaStream_t s) {
   if (n_items <= 0 || tiles <= 0) return cudaSuccess;
   cudaError_t e;
   switch (slices) {
-    case 2: e = launch_oz_s<2>(d_items, n_items, split_blocks, tiles, d_ranks, s); break;
-    case 3: e = launch_oz_s<3>(d_items, n_items, split_blocks, tiles, d_ranks, s); break;
-    case 4: e = launch_oz_s<4>(d_items, n_items, split_blocks, tiles, d_ranks, s); break;
-    case 5: e = launch_oz_s<5>(d_items, n_items, split_blocks, tiles, d_ranks, s); break;
-    case 6: e = launch_oz_s<6>(d_items, n_items, split_blocks, tiles, d_ranks, s); break;
+    case 2: e = launch_mma_s<2>(d_items, n_items, tiles, d_ranks, s); break;
+    case 3: e = launch_mma_s<3>(d_items, n_items, tiles, d_ranks, s); break;
+    case 4: e = launch_mma_s<4>(d_items, n_items, tiles, d_ranks, s); break;
+    case 5: e = launch_mma_s<5>(d_items, n_items, tiles, d_ranks, s); break;
+    case 6: e = launch_mma_s<6>(d_items, n_items, tiles, d_ranks, s); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;

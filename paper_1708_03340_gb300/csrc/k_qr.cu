@@ -162,7 +162,7 @@ __device__ __forceinline__ void apply_reflector(T (&a)[NI][4], const T *vj, T tj
 }
 
 template <typename T, int NW, int NI, bool KEEP>
-__global__ void __launch_bounds__(NW * 32) qr_reg_kernel(const QrItem *__restrict__ items) {
+__global__ void __launch_bounds__(NW * 32, (sizeof(T) == 8 && NW == 8) ? 2 : 1) qr_reg_kernel(const QrItem *__restrict__ items) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const QrItem it = items[blockIdx.x];
   const int m = it.m, n = it.n;

@@ -37,8 +37,8 @@ EXPORTS = [
     "ht_device_status", "ht_selftest_wait", "ht_set_gemm_tuning",
 ]
 HT_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
-HT_K_GEMM, HT_K_QR, HT_K_EIG, HT_K_COPY, HT_K_COMPACT, HT_K_RANKS, HT_K_ADD, HT_K_EVAL, HT_K_MISC = range(9)
-KERNEL_KINDS = ["gemm", "qr", "eig", "copy", "compact", "ranks", "add", "eval", "misc"]
+HT_K_GEMM, HT_K_QR, HT_K_EIG, HT_K_COPY, HT_K_COMPACT, HT_K_RANKS, HT_K_ADD, HT_K_EVAL, HT_K_MISC, HT_K_SPLIT = range(10)
+KERNEL_KINDS = ["gemm", "qr", "eig", "copy", "compact", "ranks", "add", "eval", "misc", "split"]
 
 
 class HTError(RuntimeError):
