@@ -315,10 +315,16 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison arms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-errors", action="store_true", help="skip the error statement against the oracle")
+    ap.add_argument("--ncu-step", default=None, choices=["mixed", "fp64", "fp32"],
+                    help="for ncu --profile-from-start off: one warm truncation of the workload's first pair, then "
+                         "one between cudaProfilerStart and cudaProfilerStop, and exit")
+    ap.add_argument("--modes", type=int, default=0, help="deep workload only: number of modes d (default 256)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.ncu_step:
+        return ncu_step(args)
 
     import torch
     from paper_1708_03340_gb300 import htgb
@@ -530,6 +536,42 @@ def main():
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def ncu_step(args):
+    """One warm truncation of the workload's first pair, then one bracketed by
+    cudaProfilerStart / cudaProfilerStop (direct calls, no graph), so that
+    `ncu --profile-from-start off` sees exactly one truncation's launches."""
+    import torch
+    from paper_1708_03340_gb300 import htgb
+    prec = {"mixed": htgb.HT_PREC_MIXED, "fp64": htgb.HT_PREC_FP64, "fp32": htgb.HT_PREC_FP32}[args.ncu_step]
+    dtype = htgb.HT_F32 if args.ncu_step == "fp32" else htgb.HT_F64
+    if args.config == "deep" and args.modes:
+        (n, ka, xa), (_, kc, xc) = I.deep_pair(21, d=args.modes)
+        d = args.modes
+        opts = I.DEEP_OPTS
+    else:
+        (d, n, (ka, xa), (kc, xc), _) = WORKLOADS[args.config]["pairs"](0, argparse.Namespace(pairs=1))[0]
+        opts = WORKLOADS[args.config]["opts"]
+    tree = htgb.HTTree(d)
+    A = htgb.HTTensor.from_blob(tree, n, ka, xa, dtype)
+    C = htgb.HTTensor.from_blob(tree, n, kc, xc, dtype)
+    k = np.asarray(A.ranks()) + np.asarray(C.ranks())
+    k[0] = 1
+    X = htgb.HTTensor.create(tree, n, k, dtype)
+    o = htgb.make_opts(prec=prec, **opts)
+    X.add_into(A, C)
+    htgb.ht_truncate(X.handle, o)
+    X.add_into(A, C)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    t0 = time.perf_counter()
+    htgb.ht_truncate(X.handle, o)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    htgb.ht_device_status()
+    print(json.dumps({"ncu_step": args.ncu_step, "config": args.config, "d": d, "seconds": time.perf_counter() - t0}))
     return 0
 
 

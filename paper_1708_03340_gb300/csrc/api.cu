@@ -252,6 +252,8 @@ struct Launch {
   int oz_split = 0;    // GEMM: CTAs of the tensor-core path's split launch
   int oz_slices = 0;   // GEMM: BF16 slices per operand (mixed path)
   double split_bytes = 0.0;  // GEMM (mixed path): algorithmic bytes of the split (operands read, slices written)
+  std::vector<int> tile_item;  // GEMM (mixed path): the launch's item of every tensor-core tile
+  const int *tile_tab = nullptr;  // the same, uploaded with the metadata (tagged pointer)
   const void *ranks = nullptr;  // tagged pointer to the rank array used by the launch
   void *scratch = nullptr;      // eig scratch (tagged)
   int variant = 0;              // GEMM: SIMT tile shape (gemm_tile_shape)
@@ -424,6 +426,8 @@ struct Plan {
       g.oeb = static_cast<int *>(lalloc_bytes(sizeof(int) * (size_t)bb * g.tc_tiles_n * oz_tile_n() * g.ksplit));
       g.oz_split0 = L.oz_split;
       L.oz_split += g.ksplit * (ba * g.tc_tiles_m + bb * g.tc_tiles_n);
+      const int tiles_here = g.tc_tiles_m * ((g.N + oz_gemm_tile_n() - 1) / oz_gemm_tile_n()) * g.batch * g.ksplit;
+      L.tile_item.insert(L.tile_item.end(), (size_t)tiles_here, L.n);
       // algorithmic bytes: the FP64 operands read once, their slices written once
       const double red = (double)g.K * g.Ko;
       L.split_bytes += red * ((double)ba * g.M + (double)bb * g.N) * (8.0 + 2.0 * L.oz_slices);
@@ -606,6 +610,15 @@ void choose_gemm_variant(Plan &P, Launch &L) {
   if (L.uniform < 0) L.uniform = 0;
 }
 
+// Tile -> item tables of the tensor-core launches, appended to the metadata
+// (once, before the plan's sizes are taken).
+void finalize_tables(Plan &P) {
+  for (Launch &L : P.launches) {
+    if (L.kind != L_GEMM || L.tile_item.empty() || L.tile_tab) continue;
+    L.tile_tab = P.mpush(L.tile_item.data(), L.tile_item.size());
+  }
+}
+
 // Workspace size of a plan: persistent | scratch | metadata | items.
 size_t plan_bytes(const Plan &P) {
   const size_t p_sz = (P.p_bytes + 255) & ~size_t(255);
@@ -663,6 +676,7 @@ ht_status prepare_plan(Plan &P, cudaStream_t s, char *base, char **ib_dev_out) {
     }
     L.ranks = reloc(L.ranks, pb, sb, mb);
     L.scratch = reloc(L.scratch, pb, sb, mb);
+    L.tile_tab = static_cast<const int *>(reloc(L.tile_tab, pb, sb, mb));
   }
   cudaError_t e;
   if (!P.meta.empty()) {
@@ -700,7 +714,7 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
     switch (L.kind) {
       case L_GEMM: {
         if (P.mixed)
-          e = launch_oz_gemm((const GemmItem *)items, L.n, L.tc_tiles, rk, L.split, L.oz_slices, s);
+          e = launch_oz_gemm((const GemmItem *)items, L.tile_tab, L.n, L.tc_tiles, rk, L.split, L.oz_slices, s);
         else if (f64)
           e = launch_gemm<double>((const GemmItem *)items, L.n, L.tiles, rk, L.split, 0, s, L.variant, false, false,
                                   L.uniform);
@@ -746,6 +760,7 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
 // keep_base must be null).
 ht_status run_plan(Plan &P, cudaStream_t s, char **keep_base, char *ext_base = nullptr, size_t ext_cap = 0) {
   if (!P.err.empty()) return fail(HT_EUNSUPPORTED, P.err);
+  finalize_tables(P);
   const size_t total = plan_bytes(P);
   char *base = nullptr;
   if (ext_base) {
@@ -2702,6 +2717,7 @@ ht_status ht_graph_add_truncate(const ht_tensor *const *a, const ht_tensor *cons
   plan_eig_ranks(P, TS, *o, rank_array);
   plan_project(P, TS, rank_array);
   if (!P.err.empty()) return fail(HT_EUNSUPPORTED, P.err);
+  finalize_tables(P);
   // one device buffer: plan workspace | per tensor: addition descriptor, sum ranks
   const size_t plan_sz = (plan_bytes(P) + 255) & ~size_t(255);
   std::vector<size_t> desc_off(count), rk_off(count);

@@ -145,8 +145,9 @@ cudaError_t launch_gemm_reduce_f64(const GemmItem *d_items, int n_items, const i
 // exactness chunk); slices in [2, 6].
 cudaError_t launch_oz_split(const GemmItem *d_items, int n_items, int split_blocks, const int *d_ranks, int slices,
                             cudaStream_t s);
-cudaError_t launch_oz_gemm(const GemmItem *d_items, int n_items, int tiles, const int *d_ranks, bool any_split,
-                           int slices, cudaStream_t s);
+// tile_item: the item of every tile (device array of `tiles` ints).
+cudaError_t launch_oz_gemm(const GemmItem *d_items, const int *tile_item, int n_items, int tiles, const int *d_ranks,
+                           bool any_split, int slices, cudaStream_t s);
 int oz_tile_m();       // rows of a GEMM tile and of a split block
 int oz_tile_n();       // rows of a split block of B (output columns)
 int oz_gemm_tile_n();  // output columns of a GEMM tile

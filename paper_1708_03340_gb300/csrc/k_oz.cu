@@ -239,14 +239,6 @@ __device__ __forceinline__ int find_split(const GemmItem *items, int n, int blk)
   return lo;
 }
 
-__device__ __forceinline__ int find_tile(const GemmItem *items, int n, int tile) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (items[mid].tc_tile0 <= tile) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 // ---------------------------------------------------------------------------
 // split: one CTA (256 threads) per (item, operand, batch, 128-row tile, chunk)
@@ -404,9 +396,9 @@ struct TileInfo {
   bool live;
 };
 
-__device__ __forceinline__ TileInfo tile_info(const GemmItem *items, int n_items, const int *ranks, int t) {
+__device__ __forceinline__ TileInfo tile_info(const GemmItem *items, const int *tile_item, const int *ranks, int t) {
   TileInfo ti;
-  const GemmItem &it = items[find_tile(items, n_items, t)];
+  const GemmItem &it = items[tile_item[t]];
   ti.it = &it;
   int local = t - it.tc_tile0;
   const int tiles_n = (it.N + OZ_TN - 1) / OZ_TN;
@@ -435,8 +427,9 @@ struct OzAcc {
 };
 
 template <int S>
-__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *__restrict__ items, int n_items,
-                                                                int total_tiles, const int *__restrict__ ranks) {
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *__restrict__ items,
+                                                                const int *__restrict__ tile_item, int total_tiles,
+                                                                const int *__restrict__ ranks) {
   constexpr int NACC = OzAcc<S>::n;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[OZ_STAGES], bar_empty[OZ_STAGES], bar_acc_full[2], bar_acc_empty[2],
@@ -477,7 +470,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
     if (lane == 0) {
       int g = 0;  // stages issued so far
       for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-        const TileInfo ti = tile_info(items, n_items, ranks, t);
+        const TileInfo ti = tile_info(items, tile_item, ranks, t);
         if (!ti.live) continue;
         const GemmItem &it = *ti.it;
         const int share = it.oz_share;
@@ -526,7 +519,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
       constexpr uint32_t idesc = idesc_bf16(OZ_M, OZ_TN);
       int g = 0, n = 0;  // stages consumed, live tiles
       for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-        const TileInfo ti = tile_info(items, n_items, ranks, t);
+        const TileInfo ti = tile_info(items, tile_item, ranks, t);
         if (!ti.live) continue;
         const int tb = n & 1;
         if (*(volatile int *)&abort_flag) break;
@@ -592,7 +585,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
     const int quad = warp & 3, half = warp >> 2;
     int n = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-      const TileInfo ti = tile_info(items, n_items, ranks, t);
+      const TileInfo ti = tile_info(items, tile_item, ranks, t);
       if (!ti.live) continue;
       const GemmItem &it = *ti.it;
       const int tb = n & 1;
@@ -700,14 +693,14 @@ cudaError_t launch_split_s(const GemmItem *d_items, int n_items, int split_block
 }
 
 template <int S>
-cudaError_t launch_mma_s(const GemmItem *d_items, int n_items, int tiles, const int *d_ranks, cudaStream_t s) {
+cudaError_t launch_mma_s(const GemmItem *d_items, const int *tile_item, int tiles, const int *d_ranks, cudaStream_t s) {
   const size_t smem = OZ_STAGES * (size_t)S * (OZ_BLK + OZ_BLK_B) + 1024;
   cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = kSmCount;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = tiles < sms ? tiles : sms;  // persistent: one CTA per SM (it holds all 512 TMEM columns)
-  oz_gemm_kernel<S><<<grid, OZ_THREADS, smem, s>>>(d_items, n_items, tiles, d_ranks);
+  oz_gemm_kernel<S><<<grid, OZ_THREADS, smem, s>>>(d_items, tile_item, tiles, d_ranks);
   count_launch();
   return cudaGetLastError();
 }
@@ -733,16 +726,17 @@ cudaError_t launch_oz_split(const GemmItem *d_items, int n_items, int split_bloc
   }
 }
 
-cudaError_t launch_oz_gemm(const GemmItem *d_items, int n_items, int tiles, const int *d_ranks, bool any_split,
-                           int slices, cudaStream_t s) {
+cudaError_t launch_oz_gemm(const GemmItem *d_items, const int *tile_item, int n_items, int tiles, const int *d_ranks,
+                           bool any_split, int slices, cudaStream_t s) {
   if (n_items <= 0 || tiles <= 0) return cudaSuccess;
+  if (!tile_item) return cudaErrorInvalidValue;
   cudaError_t e;
   switch (slices) {
-    case 2: e = launch_mma_s<2>(d_items, n_items, tiles, d_ranks, s); break;
-    case 3: e = launch_mma_s<3>(d_items, n_items, tiles, d_ranks, s); break;
-    case 4: e = launch_mma_s<4>(d_items, n_items, tiles, d_ranks, s); break;
-    case 5: e = launch_mma_s<5>(d_items, n_items, tiles, d_ranks, s); break;
-    case 6: e = launch_mma_s<6>(d_items, n_items, tiles, d_ranks, s); break;
+    case 2: e = launch_mma_s<2>(d_items, tile_item, tiles, d_ranks, s); break;
+    case 3: e = launch_mma_s<3>(d_items, tile_item, tiles, d_ranks, s); break;
+    case 4: e = launch_mma_s<4>(d_items, tile_item, tiles, d_ranks, s); break;
+    case 5: e = launch_mma_s<5>(d_items, tile_item, tiles, d_ranks, s); break;
+    case 6: e = launch_mma_s<6>(d_items, tile_item, tiles, d_ranks, s); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
