@@ -198,14 +198,15 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
 // (|l| <= ulp(h) / 2, bits below 2^-52 of h's scale cut), renormalised by
 // one place if the sum crossed a power of two.  About 2^-47 relative.
 // Results below the FP64 normal range flush to zero, above it become Inf.
-__device__ __forceinline__ double combine_to_f64(float d0, float d1, float d2, float d3, int E) {
+// Returns the FP64 bit pattern.
+__device__ __forceinline__ unsigned long long combine_to_f64(float d0, float d1, float d2, float d3, int E) {
   float s, e1, e2, h, l;
   two_sum(d0, d1, s, e1);
   two_sum(s, d2, s, e2);
   fast_two_sum(s, __fadd_rn(__fadd_rn(e1, e2), d3), h, l);
   const uint32_t bh = __float_as_uint(h);
   const int eh = (int)((bh >> 23) & 0xFFu);
-  if (eh == 0) return 0.0;
+  if (eh == 0) return 0ull;
   long long W = (long long)((bh & 0x7FFFFFu) | 0x800000u) << 29;  // [2^52, 2^53)
   const uint32_t bl = __float_as_uint(l);
   const int el = (int)((bl >> 23) & 0xFFu);
@@ -223,11 +224,28 @@ __device__ __forceinline__ double combine_to_f64(float d0, float d1, float d2, f
     W <<= 1;
     --ex;
   }
-  if (ex <= 0) return 0.0;
+  if (ex <= 0) return 0ull;
   const unsigned long long sign = (unsigned long long)(bh >> 31) << 63;
-  if (ex >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
-  return __longlong_as_double(
-      (long long)(sign | ((unsigned long long)ex << 52) | ((unsigned long long)W & 0xFFFFFFFFFFFFFull)));
+  if (ex >= 2047) return sign | 0x7FF0000000000000ull;
+  return sign | ((unsigned long long)ex << 52) | ((unsigned long long)W & 0xFFFFFFFFFFFFFull);
+}
+
+// High 32 bits of |x| (sign cleared).  For non-negative doubles the order of
+// these words is the order of the exponents, so the largest word of a row
+// carries the row's largest exponent; a word >= kHiNonFinite is Inf or NaN.
+// Integer operations only: compares and maxima of FP64 values would run on the
+// FP64 pipe (1/64 of the FP32 rate on this GPU).
+constexpr uint32_t kHiNonFinite = 0x7FF00000u;
+__device__ __forceinline__ uint32_t abs_hi(double x) {
+  return (uint32_t)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7FFFFFFFu;
+}
+// Exponent E of a row with largest high word mh: every |x| of the row is
+// below 2^E (|x| = 1.f 2^(ex-1023) < 2^(ex-1022)); zero and subnormal rows
+// get E = 0 (their digits are zero), rows with Inf / NaN the marker.
+__device__ __forceinline__ int row_exponent(uint32_t mh) {
+  if (mh >= kHiNonFinite) return OZ_EXP_NONFINITE;
+  const int ex = (int)(mh >> 20);
+  return ex ? ex - 1022 : 0;
 }
 
 __device__ __forceinline__ int find_split(const GemmItem *items, int n, int blk) {
@@ -246,7 +264,7 @@ __device__ __forceinline__ int find_split(const GemmItem *items, int n, int blk)
 template <int S>
 __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restrict__ items, int n_items,
                                                        const int *__restrict__ ranks) {
-  __shared__ double red[2][OZ_M];
+  __shared__ uint32_t red[2][OZ_M];
   __shared__ int sexp[OZ_M];
   const GemmItem &it = items[find_split(items, n_items, blockIdx.x)];
   int local = blockIdx.x - it.oz_split0;
@@ -281,8 +299,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
       const int grow = tile * OZ_M + r;
       if (grow >= rows) break;  // padding rows feed only discarded outputs: left unwritten
       double v[8];
-      double m = 0.0;
-      bool bad = false;
+      uint32_t mh = 0u;  // largest high word of |x|: its exponent field is the row's largest exponent
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int64_t f = f0 + lane * 8 + e;
@@ -291,15 +308,12 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
           const int64_t ko = f / K, k = f - ko * K;
           v[e] = X[(int64_t)grow * sr + k + ko * sko];
         }
-        const double a = fabs(v[e]);
-        if (!(a <= 1.7976931348623157e308)) bad = true;
-        m = a > m ? a : m;
+        mh = max(mh, abs_hi(v[e]));
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      bad = __any_sync(0xffffffffu, bad);
-      const int ex = (int)(((unsigned long long)__double_as_longlong(m) >> 52) & 0x7FF);
-      const int E = bad ? OZ_EXP_NONFINITE : (ex ? ex - 1022 : 0);
+      for (int o = 16; o > 0; o >>= 1) mh = max(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+      const bool bad = mh >= kHiNonFinite;
+      const int E = row_exponent(mh);
       if (lane == 0) Ex[(int64_t)r * it.ksplit] = E;
       const int q = lane >> 2, kk0 = (lane & 3) * 8;
       if (q >= nst) continue;
@@ -328,28 +342,15 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
     const int64_t ko = f / K, k = f - ko * K;
     return X[(int64_t)grow * sr + k * sk + ko * sko];
   };
-  // pass 1: largest magnitude of the row over the chunk (NaN / Inf flagged)
-  double m = 0.0;
-  bool bad = false;
+  // pass 1: largest high word of |x| over the row's chunk (NaN / Inf: exponent field all ones)
+  uint32_t mh = 0u;
   if (row_in) {
-    for (int64_t f = f0 + h; f < f1; f += 2) {
-      const double v = fabs(elem(f));
-      if (!(v <= 1.7976931348623157e308)) bad = true;
-      m = v > m ? v : m;
-    }
+    for (int64_t f = f0 + h; f < f1; f += 2) mh = max(mh, abs_hi(elem(f)));
   }
-  red[h][r] = bad ? -1.0 : m;
+  red[h][r] = mh;
   __syncthreads();
   if (h == 0) {
-    const double a = red[0][r], c = red[1][r];
-    int E = 0;
-    if (a < 0.0 || c < 0.0) {
-      E = OZ_EXP_NONFINITE;
-    } else {
-      const double mx = a > c ? a : c;
-      const int ex = (int)(((unsigned long long)__double_as_longlong(mx) >> 52) & 0x7FF);
-      E = ex ? ex - 1022 : 0;  // mx = 1.f 2^(ex-1023) < 2^(ex-1022); zero / subnormal rows: digits 0
-    }
+    const int E = row_exponent(max(red[0][r], red[1][r]));
     sexp[r] = E;
     Ex[(int64_t)r * it.ksplit] = E;
   }
@@ -581,7 +582,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
     }
   } else {
     // ---- epilogue: warps 0-7; warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile
-    // rows) of columns 32 (w / 4) .. + 31 ----
+    // rows); the tile's 16-column chunks alternate between warps 0-3 and 4-7,
+    // so that a tile with 32 live columns keeps all eight warps busy ----
     const int quad = warp & 3, half = warp >> 2;
     int n = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
@@ -597,26 +599,38 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
       const bool valid = __all_sync(0xffffffffu, ok) && !*(volatile int *)&abort_flag;
       if (!valid) break;  // warp-uniform
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // the item's fields in registers, the tile's 64 column exponents two per lane
+      // the item's fields in registers
       const int M = eff_dim(it.M, it.m_ref, 1, ranks);
       const int N = eff_dim(it.N, it.n_ref, it.n_mult, ranks);
       const int share = it.oz_share, ksplit = it.ksplit;
       const int ba = (share & 1) ? 0 : ti.b, bb = (share & 2) ? 0 : ti.b;
       const int row = ti.tm * OZ_M + quad * 32 + lane;
-      const int n0 = ti.tn * OZ_TN + half * 32;
+      const int n0 = ti.tn * OZ_TN;
+      const int ncols = (N - n0 < OZ_TN) ? N - n0 : OZ_TN;  // live columns of the tile
       const int64_t Mpad = (int64_t)it.tc_tiles_m * OZ_M, Npad = (int64_t)it.tc_tiles_n * OZ_N;
       const int ea = it.oea[((int64_t)ba * Mpad + row) * ksplit + ti.chunk];
+      // column exponents: lane l holds those of columns n0 + l and n0 + 32 + l
+      // (padding columns, below the padded width, hold unused values)
       const int *Eb = it.oeb + ((int64_t)bb * Npad + n0) * ksplit + ti.chunk;
-      const int eb_lane = Eb[(int64_t)lane * ksplit];
+      const int eb_lo = Eb[(int64_t)lane * ksplit], eb_hi = Eb[(int64_t)(lane + 32) * ksplit];
       const double alpha = it.alpha, beta = it.beta;
       const int64_t scm = it.scm, scn = it.scn, ldp = it.M;
       double *Cp = static_cast<double *>(it.C) + (int64_t)ti.b * it.scb;
       double *Pp = ksplit > 1
                        ? static_cast<double *>(it.part) + ((int64_t)ti.chunk * it.batch + ti.b) * (int64_t)it.M * it.N
                        : nullptr;
-      const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * NACC * OZ_TN + half * 32);
-      const int n_here = (N - n0 < 32) ? N - n0 : 32;
-      for (int c0 = 0; c0 < n_here; c0 += 16) {
+      const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * NACC * OZ_TN);
+      // how the results are stored, decided once per tile so that no FP64
+      // instruction runs per element where none is needed: 0 split-K partial
+      // (alpha and beta are applied by the reduction), 1 C = +-AB (the sign as
+      // a bit flip), 2 C = +-AB + beta C (one FP64 FMA), 3 any other alpha
+      const bool unit = alpha == 1.0 || alpha == -1.0;
+      const int smode = Pp ? 0 : (unit ? (beta == 0.0 ? 1 : 2) : 3);
+      const unsigned long long flip = (!Pp && alpha == -1.0) ? 0x8000000000000000ull : 0ull;
+      const bool row_ok = row < M;
+      double *prow = Pp ? Pp + row : Cp + (int64_t)row * scm;
+      const int64_t cstride = Pp ? ldp : scn;
+      for (int c0 = half * 16; c0 < ncols; c0 += 32) {
         uint32_t v[4][16];
         if (ti.nq > 0) {
 #pragma unroll
@@ -641,27 +655,40 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[a][j] = 0u;
         }
+        const int eb_src = c0 < 32 ? eb_lo : eb_hi;
+        unsigned long long w[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int cc = c0 + j;  // the same column for every lane of the warp
-          const int eb = __shfl_sync(0xffffffffu, eb_lane, cc);
-          const int col = n0 + cc;
-          if (row >= M || col >= N) continue;
-          double val;
-          if (eb == OZ_EXP_NONFINITE || ea == OZ_EXP_NONFINITE) {
-            val = __longlong_as_double(0x7FF8000000000000ll);
+          const int eb = __shfl_sync(0xffffffffu, eb_src, (c0 & 31) + j);  // the same column for every lane
+          w[j] = (eb == OZ_EXP_NONFINITE || ea == OZ_EXP_NONFINITE)
+                     ? 0x7FF8000000000000ull
+                     : combine_to_f64(__uint_as_float(v[0][j]), __uint_as_float(v[1][j]),
+                                      __uint_as_float(v[2][j]), __uint_as_float(v[3][j]), ea + eb);
+        }
+        if (!row_ok) continue;
+        const int jn = ncols - c0 < 16 ? ncols - c0 : 16;
+        double *pc = prow + (int64_t)(n0 + c0) * cstride;
+        if (smode <= 1) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (j < jn) pc[(int64_t)j * cstride] = __longlong_as_double((long long)(w[j] ^ flip));
+        } else {
+          // all loads of C before the first store (the stores could alias them
+          // for all the compiler knows, which would serialise the loads)
+          double cv[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) cv[j] = j < jn ? pc[(int64_t)j * cstride] : 0.0;
+          if (smode == 2) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (j < jn) pc[(int64_t)j * cstride] = fma(beta, cv[j], __longlong_as_double((long long)(w[j] ^ flip)));
           } else {
-            val = combine_to_f64(__uint_as_float(v[0][j]), __uint_as_float(v[1][j]), __uint_as_float(v[2][j]),
-                                 __uint_as_float(v[3][j]), ea + eb);
-          }
-          if (Pp) {
-            Pp[(int64_t)col * ldp + row] = val;
-          } else {
-            double *c = Cp + (int64_t)row * scm + (int64_t)col * scn;
-            // alpha = +-1 and beta = 0 (all but the TSQR panel updates) need no FP64 arithmetic
-            double o = alpha == 1.0 ? val : (alpha == -1.0 ? -val : alpha * val);
-            if (beta != 0.0) o += beta * *c;
-            *c = o;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (j >= jn) continue;
+              const double o = alpha * __longlong_as_double((long long)w[j]);
+              pc[(int64_t)j * cstride] = beta != 0.0 ? fma(beta, cv[j], o) : o;
+            }
           }
         }
       }
