@@ -265,6 +265,7 @@ template <int S>
 __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restrict__ items, int n_items,
                                                        const int *__restrict__ ranks) {
   __shared__ uint32_t red[2][OZ_M];
+  __shared__ int64_t offt[256];
   __shared__ int sexp[OZ_M];
   const GemmItem &it = items[find_split(items, n_items, blockIdx.x)];
   int local = blockIdx.x - it.oz_split0;
@@ -284,42 +285,54 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
   const int64_t sr = op ? it.sbn : it.sam, sk = op ? it.sbk : it.sak, sko = op ? it.sbko : it.sako;
   int64_t f0, f1;
   chunk_range(it, chunk, f0, f1);
-  const int K = it.K;
+  const int K = it.K > 0 ? it.K : 1;  // K = 0 leaves an empty chunk
   const int tid = threadIdx.x;
   const int nst = it.oz_stages;
   unsigned char *out = static_cast<unsigned char *>(op ? it.ozb : it.oza) +
                        ((((int64_t)b * tiles + tile) * it.ksplit + chunk) * nst) * S * (int64_t)OZ_BLK;
   int *Ex = (op ? it.oeb : it.oea) + ((int64_t)b * tiles * OZ_M + (int64_t)tile * OZ_M) * it.ksplit + chunk;
-  if (sk == 1 && f1 - f0 <= 256) {
-    // reduction index contiguous in memory: one warp per row, lane l holds the
-    // 8 indices 8l .. 8l+7 of the chunk (coalesced loads, read once); the row
-    // maximum is a warp reduction and the digits come from the registers
+  // chunks hold at most 256 reduction indices, and a chunk starts at a
+  // multiple of K: local index l of the chunk is (ko0 + l / K, l % K)
+  const int len = (int)(f1 - f0);
+  const int64_t ko0 = f0 / K;
+  if (sk == 1) {
+    // reduction index contiguous in memory: a group of lpr lanes per row
+    // (lpr * 8 >= chunk length), lane i of a group holding the 8 indices
+    // 8i .. 8i+7 of the chunk (coalesced loads, read once); the row maximum is
+    // a reduction over the group and the digits come from the registers
+    int lpr = 4;
+    while (lpr * 8 < len) lpr <<= 1;
+    const int rpw = 32 / lpr;  // rows a warp takes at a time
     const int warp = tid >> 5, lane = tid & 31;
-    for (int r = warp; r < OZ_M; r += 8) {
+    const int sub = lane / lpr, li = lane % lpr;
+    int64_t off[8];  // element offsets of this lane's indices within a row
+    bool in[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int l = li * 8 + e;
+      const int qk = l / K;
+      in[e] = l < len;
+      off[e] = (int64_t)(l - qk * K) + (ko0 + qk) * sko;
+    }
+    const int q = li >> 2, kk0 = (li & 3) * 8;
+    for (int r0 = warp * rpw; r0 < OZ_M; r0 += 8 * rpw) {
+      const int r = r0 + sub;
       const int grow = tile * OZ_M + r;
-      if (grow >= rows) break;  // padding rows feed only discarded outputs: left unwritten
+      const bool live = grow < rows;  // padding rows feed only discarded outputs: left unwritten
       double v[8];
       uint32_t mh = 0u;  // largest high word of |x|: its exponent field is the row's largest exponent
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const int64_t f = f0 + lane * 8 + e;
-        v[e] = 0.0;
-        if (grow < rows && f < f1) {
-          const int64_t ko = f / K, k = f - ko * K;
-          v[e] = X[(int64_t)grow * sr + k + ko * sko];
-        }
+        v[e] = (live && in[e]) ? X[(int64_t)grow * sr + off[e]] : 0.0;
         mh = max(mh, abs_hi(v[e]));
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mh = max(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+      for (int o = lpr >> 1; o > 0; o >>= 1) mh = max(mh, __shfl_xor_sync(0xffffffffu, mh, o));
       const bool bad = mh >= kHiNonFinite;
       const int E = row_exponent(mh);
-      if (lane == 0) Ex[(int64_t)r * it.ksplit] = E;
-      const int q = lane >> 2, kk0 = (lane & 3) * 8;
+      if (!live) continue;
+      if (li == 0) Ex[(int64_t)r * it.ksplit] = E;
       if (q >= nst) continue;
       uint32_t w[S][4];
-#pragma unroll
-      for (int i = 0; i < S; ++i) w[i][0] = w[i][1] = w[i][2] = w[i][3] = 0u;
 #pragma unroll
       for (int e = 0; e < 8; e += 2) {
         int d0[S], d1[S];
@@ -335,17 +348,17 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
     }
     return;
   }
+  // element offsets of the chunk's indices within a row, once per block
+  offt[tid] = (int64_t)(tid % K) * sk + (ko0 + tid / K) * sko;
+  __syncthreads();
   const int r = tid & (OZ_M - 1), h = tid >> 7;
   const int grow = tile * OZ_M + r;
   const bool row_in = grow < rows;
-  auto elem = [&](int64_t f) -> double {
-    const int64_t ko = f / K, k = f - ko * K;
-    return X[(int64_t)grow * sr + k * sk + ko * sko];
-  };
+  const double *Xr = X + (int64_t)grow * sr;
   // pass 1: largest high word of |x| over the row's chunk (NaN / Inf: exponent field all ones)
   uint32_t mh = 0u;
   if (row_in) {
-    for (int64_t f = f0 + h; f < f1; f += 2) mh = max(mh, abs_hi(elem(f)));
+    for (int l = h; l < len; l += 2) mh = max(mh, abs_hi(Xr[offt[l]]));
   }
   red[h][r] = mh;
   __syncthreads();
@@ -366,10 +379,10 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
     for (int i = 0; i < S; ++i) w[i][0] = w[i][1] = w[i][2] = w[i][3] = 0u;
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
-      const int64_t f = f0 + (int64_t)q * OZ_KC + kk0 + e;
+      const int l = q * OZ_KC + kk0 + e;
       double va = 0.0, vb = 0.0;
-      if (f < f1 && E != OZ_EXP_NONFINITE) va = elem(f);
-      if (f + 1 < f1 && E != OZ_EXP_NONFINITE) vb = elem(f + 1);
+      if (l < len && E != OZ_EXP_NONFINITE) va = Xr[offt[l]];
+      if (l + 1 < len && E != OZ_EXP_NONFINITE) vb = Xr[offt[l + 1]];
       int d0[S], d1[S];
       oz_digits<S>(va, E, d0);
       oz_digits<S>(vb, E, d1);
