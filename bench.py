@@ -614,11 +614,20 @@ def measured_peaks():
     return out
 
 
+# FP32 instructions per FP64-equivalent flop in the double-float QR blocks:
+# per entry and reflector a dot-product term (4 for the product, 6 for the
+# two-sum, 2 for the low-order sum) and an update (4 + 6 + 2 + 3 for the
+# renormalisation), 27 instructions for 2 multiply-adds = 4 flop
+DF_FP32_OPS_PER_FLOP = 27.0 / 4.0
+
+
 def roofline_of(prof, steps, peaks):
     """Roofline object of the dominant kernel family (by device time) of the
     mixed path, measured live with CUDA events on the launching stream.
     Families and their bound:
-      qr     FP64 Householder TSQR blocks: FP64 ALU, 4 m n^2 - 4 n^3 / 3 flop per block
+      qr     TSQR blocks in double-float arithmetic on the FP32 pipe: ALU,
+             4 m n^2 - 4 n^3 / 3 FP64-equivalent flop per block against the FP32
+             FMA rate over DF_FP32_OPS_PER_FLOP instructions per such flop
       gemm   tensor-core contractions: tensor pipe, the BF16 work of the slice
              products (S (S + 1) / 2 per FP64-equivalent product, 2 M N K each at the
              plan's maximal dims)
@@ -640,6 +649,16 @@ def roofline_of(prof, steps, peaks):
             bound, unit, ach = "hbm", "GB/s", rate / 1e9
             peak = peaks.get("hbm_gbs") or 6787.6
             src = "HBM copy (measured peak file)"
+        elif name == "qr":
+            # FP32 lane instructions per second (the FMA rate in flop/s / 2) over the
+            # instructions one FP64-equivalent flop costs in the inner loops
+            bound, unit, ach = "alu", "TFLOP/s", rate / 1e12
+            f32 = peaks.get("fp32_fma")
+            src = (f"FP32 FMA chains measured by peaks.cu / 2 / {DF_FP32_OPS_PER_FLOP} FP32 instructions "
+                   "per FP64-equivalent flop (double-float dot and update loops)")
+            if not f32:
+                f32, src = 80.0, "FP32 nominal / 2 / 6.75 (measurement unavailable)"
+            peak = f32 / 2.0 / DF_FP32_OPS_PER_FLOP
         else:
             bound, unit, ach = "alu", "TFLOP/s", rate / 1e12
             peak = peaks.get("fp64_fma")
@@ -652,7 +671,7 @@ def roofline_of(prof, steps, peaks):
     if not fams:
         return None
     name = max(fams, key=lambda k: fams[k]["ms_per_step"])
-    kernel = {"qr": "qr_reg_kernel<double> (FP64 TSQR row blocks)",
+    kernel = {"qr": "qr_df_kernel (double-float TSQR row blocks)",
               "gemm": "oz_gemm_kernel (tcgen05 BF16 slice products) + split-K reduction",
               "split": "oz_split_kernel (BF16 slicing of FP64 operands)",
               "eig": "eig_ql_kernel<double> (FP64 QL)"}[name]

@@ -110,9 +110,12 @@ typedef struct {
   int prec;
   int schedule;
   const int *tensor_caps; /* host, one per tensor of a batch call, or NULL */
-  int qr_kernel;          /* TSQR row-block kernel: 0 by shape and launch size (default),
-                             1 the one-column kernel, 2 the two-column kernel (F32
-                             blocks of 64 columns; smaller blocks keep their kernel) */
+  int qr_kernel;          /* TSQR row-block kernel: 0 by shape and launch size (default;
+                             HT_PREC_MIXED: double-float blocks, about 2^-47 relative,
+                             on the FP32 pipe), 1 the one-column kernel, 2 the
+                             two-column kernel (F32 blocks of 64 columns; smaller
+                             blocks keep their kernel), 3 HT_PREC_MIXED with FP64
+                             Householder blocks */
 } ht_trunc_opts;
 
 /* Optional report (pass NULL to skip; synchronises when given).  With a

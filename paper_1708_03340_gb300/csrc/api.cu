@@ -724,8 +724,11 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
         break;
       }
       case L_QR:
-        e = f64 ? launch_qr<double>((const QrItem *)items, L.n, L.max_m, L.max_n, s, P.qr_kernel)
-                : launch_qr<float>((const QrItem *)items, L.n, L.max_m, L.max_n, s, P.qr_kernel);
+        if (P.mixed && P.qr_kernel != 3)  // mixed path: double-float blocks on the FP32 pipe
+          e = launch_qr_df((const QrItem *)items, L.n, L.max_m, L.max_n, s);
+        else
+          e = f64 ? launch_qr<double>((const QrItem *)items, L.n, L.max_m, L.max_n, s, P.qr_kernel)
+                  : launch_qr<float>((const QrItem *)items, L.n, L.max_m, L.max_n, s, P.qr_kernel);
         break;
       case L_EIG:
         // square-root Gramians carry eigenvalues far below the FP32 solve's resolution,
@@ -2541,7 +2544,7 @@ static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_o
   if (!xs || count < 1 || !o) return fail(HT_EINVAL, "null argument");
   if (o->mode != HT_TRUNC_RANK && o->mode != HT_TRUNC_EPS) return fail(HT_EINVAL, "bad mode");
   if (o->mode == HT_TRUNC_EPS && !(o->eps >= 0.0)) return fail(HT_EINVAL, "eps must be >= 0");
-  if (o->qr_kernel < 0 || o->qr_kernel > 2) return fail(HT_EINVAL, "qr_kernel must be 0, 1 or 2");
+  if (o->qr_kernel < 0 || o->qr_kernel > 3) return fail(HT_EINVAL, "qr_kernel must be 0, 1, 2 or 3");
   const int dtype = xs[0]->dtype;
   cudaStream_t s = xs[0]->stream;
   for (int i = 0; i < count; ++i) {
@@ -2668,7 +2671,7 @@ ht_status ht_graph_add_truncate(const ht_tensor *const *a, const ht_tensor *cons
   if (o->mode != HT_TRUNC_RANK && o->mode != HT_TRUNC_EPS) return fail(HT_EINVAL, "bad mode");
   if (o->mode == HT_TRUNC_EPS && !(o->eps >= 0.0)) return fail(HT_EINVAL, "eps must be >= 0");
   if (count > 1 && o->ranks) return fail(HT_EINVAL, "per-node target ranks are only accepted for a single tensor");
-  if (o->qr_kernel < 0 || o->qr_kernel > 2) return fail(HT_EINVAL, "qr_kernel must be 0, 1 or 2");
+  if (o->qr_kernel < 0 || o->qr_kernel > 3) return fail(HT_EINVAL, "qr_kernel must be 0, 1, 2 or 3");
   cudaStream_t s = out[0] ? out[0]->stream : nullptr;
   for (int i = 0; i < count; ++i) {
     HT_TRY(add_check(a[i], c[i]));

@@ -158,6 +158,9 @@ unsigned oz_take_status();  // bit 0: a bounded wait of the tensor-core kernel g
 // one-column kernel, 2 the two-column kernel (FP32, 64-column blocks).
 template <typename T>
 cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s, int qr_kernel = 0);
+// The same row blocks (FP64 in and out) factored in double-float arithmetic
+// on the FP32 pipe, about 2^-47 relative (k_qr_df.cu); max_n <= 32, max_m <= 256.
+cudaError_t launch_qr_df(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s);
 // mode 0: FP64 QL; mode 1: FP32 QL followed by one double-float refinement step.
 // scratch: 4 * max_k^2 doubles per item when max_k exceeds the shared-memory sizes (eig_scratch_needed).
 cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s, int mode);

@@ -58,6 +58,7 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "dfloat.cuh"
 #include "wait.cuh"
 
 namespace htgb {
@@ -180,54 +181,15 @@ __device__ __forceinline__ uint32_t slice_pair_bf16(int a, int b, int i) {
   return __byte_perm(__float_as_uint(fa), __float_as_uint(fb), 0x7632);
 }
 
-// Error-free sums in FP32 (Knuth's two-sum, Dekker's fast two-sum for |a| >= |b|).
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
 // The four accumulators D_0 + D_1 + D_2 + D_3 (in grid units) as a
 // double-float (h, l), then h + l scaled by 2^E as an FP64 bit pattern built
-// with integer operations (the FP64 pipe of this GPU runs at 1/64 of the
-// FP32 rate): h's 24-bit significand at bit 52, l's added at its offset
-// (|l| <= ulp(h) / 2, bits below 2^-52 of h's scale cut), renormalised by
-// one place if the sum crossed a power of two.  About 2^-47 relative.
-// Results below the FP64 normal range flush to zero, above it become Inf.
-// Returns the FP64 bit pattern.
+// with integer operations (df_to_f64_bits).  About 2^-47 relative.
 __device__ __forceinline__ unsigned long long combine_to_f64(float d0, float d1, float d2, float d3, int E) {
   float s, e1, e2, h, l;
   two_sum(d0, d1, s, e1);
   two_sum(s, d2, s, e2);
   fast_two_sum(s, __fadd_rn(__fadd_rn(e1, e2), d3), h, l);
-  const uint32_t bh = __float_as_uint(h);
-  const int eh = (int)((bh >> 23) & 0xFFu);
-  if (eh == 0) return 0ull;
-  long long W = (long long)((bh & 0x7FFFFFu) | 0x800000u) << 29;  // [2^52, 2^53)
-  const uint32_t bl = __float_as_uint(l);
-  const int el = (int)((bl >> 23) & 0xFFu);
-  if (el != 0) {
-    const long long ml = (long long)((bl & 0x7FFFFFu) | 0x800000u);
-    const int sh = el - eh + 29;  // <= 5
-    const long long lp = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> (-sh)) : 0ll);
-    W = ((bl ^ bh) >> 31) ? W - lp : W + lp;
-  }
-  int ex = eh - 127 + 1023 + E;
-  if (W >= (1ll << 53)) {
-    W >>= 1;
-    ++ex;
-  } else if (W < (1ll << 52)) {
-    W <<= 1;
-    --ex;
-  }
-  if (ex <= 0) return 0ull;
-  const unsigned long long sign = (unsigned long long)(bh >> 31) << 63;
-  if (ex >= 2047) return sign | 0x7FF0000000000000ull;
-  return sign | ((unsigned long long)ex << 52) | ((unsigned long long)W & 0xFFFFFFFFFFFFFull);
+  return df_to_f64_bits(h, l, E);
 }
 
 // High 32 bits of |x| (sign cleared).  For non-negative doubles the order of

@@ -1,6 +1,7 @@
-"""The mixed-precision path (HT_PREC_MIXED: F64 storage, FP64 QR and
-eigensolves, every contraction on the tcgen05 tensor cores by exact BF16
-slicing) against the CPU FP64 oracle, through the C-ABI.
+"""The mixed-precision path (HT_PREC_MIXED: F64 storage, QR blocks in
+double-float arithmetic on the FP32 pipe (FP64 Householder blocks with
+qr_kernel 3), FP64 eigensolves, every contraction on the tcgen05 tensor cores
+by exact BF16 slicing) against the CPU FP64 oracle, through the C-ABI.
 
 Tolerance: 1e-9, normwise on sigma^2 per node and relative to ||X|| on
 entries and norms.  The slicing carries about 2^-40 of |a| |b| per product
@@ -119,3 +120,35 @@ def test_mixed_rejects_f32_tensor():
     with pytest.raises(htgb.HTError) as e:
         A.truncate(mode="rank", rank_cap=4, prec=MIXED)
     assert e.value.status == htgb.HT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("case", ["small", "big_rank", "rank128"])
+def test_mixed_fp64_qr_blocks(case):
+    """qr_kernel 3: the mixed path with FP64 Householder blocks in place of the
+    double-float ones, against the oracle at the same tolerance."""
+    d, n, a, c = _case(case)
+    r = {"small": 8, "big_rank": 30, "rank128": 64}[case]
+    _trunc_compare(d, n, a, c, F64, dict(mode="rank", rank_cap=r), prec=MIXED, tol=TOL, qr_kernel=3)
+
+
+@pytest.mark.parametrize("case", ["uneven", "rank200"])
+def test_double_float_qr_blocks_match_fp64_blocks(case):
+    """The same mixed truncation with double-float QR blocks (default) and with
+    FP64 blocks: both carry the contractions' 2^-40 per product, the blocks
+    themselves 2^-47 and 2^-53, so every node's singular values agree to
+    1e-10 of the largest and the truncated tensors to 1e-9 of ||X||."""
+    d, n, a, c = _case(case)
+    r = {"uneven": 3, "rank200": 100}[case]
+    out = []
+    for qk in (0, 3):
+        _, _, _, X = gpu_sum(d, n, a, c, F64)
+        rep = X.truncate(prec=MIXED, mode="rank", rank_cap=r, qr_kernel=qk)
+        out.append((rep, X))
+    (r0, X0), (r3, X3) = out
+    assert list(r0["korth"]) == list(r3["korth"]) and list(r0["ranks"]) == list(r3["ranks"])
+    s0 = np.concatenate([np.ravel(v) for v in split_sigma(r0["korth"], r0["sigma"])])
+    s3 = np.concatenate([np.ravel(v) for v in split_sigma(r3["korth"], r3["sigma"])])
+    assert np.abs(s0 - s3).max() <= 1e-10 * np.abs(s0).max()
+    assert abs(r0["norm"] - r3["norm"]) <= 1e-12 * r3["norm"]
+    idx = sample_idx(n, 300, 11)
+    assert np.abs(X0.eval(idx) - X3.eval(idx)).max() <= 1e-9 * r3["norm"]
