@@ -295,8 +295,9 @@ def build_pairs(htgb, config, rank, args, dtype, stream):
     return trees, A, C, X, caps, shapes
 
 
-def make_opts(htgb, config, prec, caps, sched=None):
+def make_opts(htgb, config, prec, caps, sched=None, extra=None):
     kw = dict(WORKLOADS[config]["opts"])
+    kw.update(extra or {})
     if config == "batched":
         kw["tensor_caps"] = caps
     if sched is not None:
@@ -350,10 +351,10 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def graph_arm(dtype, prec, steps, warmup, sched=None):
+    def graph_arm(dtype, prec, steps, warmup, sched=None, extra=None):
         """Timed graph replays: per step, L2 flush then one replay between CUDA events."""
         trees, A, C, X, caps, shapes = build_pairs(htgb, args.config, rank, args, dtype, stream)
-        opts = make_opts(htgb, args.config, prec, caps, sched)
+        opts = make_opts(htgb, args.config, prec, caps, sched, extra)
         g = htgb.ht_graph_add_truncate([a.handle for a in A], [c.handle for c in C], [x.handle for x in X], opts)
         for _ in range(warmup):
             htgb.ht_graph_launch(g)
@@ -436,8 +437,9 @@ def main():
         "data": "synthetic (seeded SplitMix64/Box-Muller HT tensors)",
         "config": {"workload": args.config, "tensors_per_step": per_step, "shape": WORKLOADS[args.config]["desc"],
                    "l2": "flushed between steps (256 MB write)",
-                   "path": "mixed: F64 storage, FP64 TSQR blocks and QL eigensolves, every contraction on tcgen05 "
-                           "(5 BF16 slices per FP64 operand, exact leading sums), one batched launch per level, "
+                   "path": "mixed: F64 storage, double-float TSQR blocks (FP32 pipe, 2^-47), FP64 QL eigensolves, "
+                           "every contraction on tcgen05 (5 BF16 slices per FP64 operand, exact leading sums), "
+                           "one batched launch per level, "
                            "CUDA-graph replay"},
         "gflops": work / (ms_per_step / 1e3) / 1e9,
         "direct_calls_ms_per_step": prof["ms"] / psteps,
@@ -458,6 +460,12 @@ def main():
         line["fp32_path"] = {"value": f32["value"], "unit": "truncations/s", "ms_per_step": f32["ms"] / fs}
         htgb.ht_graph_free(f32["g"])
         trim_pool()
+        # the mixed path with FP64 Householder QR blocks instead of the double-float ones
+        mq = graph_arm(htgb.HT_F64, htgb.HT_PREC_MIXED, fs, 3, extra={"qr_kernel": 3})
+        line["mixed_fp64_qr"] = {"value": mq["value"], "unit": "truncations/s", "ms_per_step": mq["ms"] / fs,
+                                 "note": "HT_PREC_MIXED with qr_kernel 3: TSQR blocks in FP64 Householder"}
+        htgb.ht_graph_free(mq["g"])
+        trim_pool()
         ps = 2 if args.config in ("deep", "wide") else 3
         plain = profiled_arm(htgb.HT_F64, htgb.HT_PREC_FP64, ps)
         line["plain_fp64_level"] = {"value": ws * per_step * ps / (plain["ms"] / 1e3), "unit": "truncations/s",
@@ -473,6 +481,7 @@ def main():
         line["speedup_vs_plain_per_node"] = value / line["plain_fp64_per_node"]["value"]
         line["speedup_vs_plain_level"] = value / line["plain_fp64_level"]["value"]
         line["speedup_vs_fp32_path"] = value / line["fp32_path"]["value"]
+        line["speedup_vs_mixed_fp64_qr"] = value / line["mixed_fp64_qr"]["value"]
 
     # ---- end to end through the public API: pinned host blobs in, truncated blobs out, every step
     A, C, X, g = main_arm["A"], main_arm["C"], main_arm["X"], main_arm["g"]

@@ -1657,7 +1657,7 @@ void plan_eig_ranks(Plan &P, std::vector<TState> &TS, const ht_trunc_opts &o, in
       n_eig++;
     }
   }
-  if (eig_scratch_needed(max_k, (P.dtype == HT_F64 || P.sqrt_gram) ? 0 : 1)) {
+  if (eig_scratch_needed(max_k, (P.dtype == HT_F64 || P.sqrt_gram) ? 0 : 1, P.node_sched ? 1 : (int)n_eig)) {
     // one scratch slab per item of a launch (node schedule: one item per launch)
     size_t per = 4 * (size_t)max_k * max_k;
     size_t cnt = P.node_sched ? 1 : n_eig;

@@ -206,6 +206,11 @@ void prof_end(int kind, cudaStream_t s, double flops);
 int qr_max_rows(int n, int elem_bytes);
 // largest k whose eigenproblem is solved in shared memory (larger k use a global scratch slab)
 int eig_smem_k();
-inline bool eig_scratch_needed(int max_k, int mode) { return mode == 0 ? max_k > 128 : max_k > 64; }
+// FP64 eigensolves of more matrices than SMs keep their eigenvectors in the
+// scratch slab instead of shared memory, so that several CTAs share an SM
+inline bool eig_z_global(int max_k, int n_items) { return max_k <= 128 && n_items > kSmCount; }
+inline bool eig_scratch_needed(int max_k, int mode, int n_items) {
+  return mode == 0 ? (max_k > 128 || eig_z_global(max_k, n_items)) : max_k > 64;
+}
 
 }  // namespace htgb

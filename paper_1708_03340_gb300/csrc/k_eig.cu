@@ -413,12 +413,20 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
     const int cnt = sh.count, i0 = sh.lo;
     for (int row = tid; row < k; row += nt) {
       T zi1 = Z[(int64_t)(i0 + 1) * ld + row];
-      for (int q = 0; q < cnt; ++q) {
-        const int i = i0 - q;
-        T *zp = Z + (int64_t)i * ld + row;
-        const T zi = *zp;
-        Z[(int64_t)(i + 1) * ld + row] = rs[q] * zi + rc[q] * zi1;
-        zi1 = rc[q] * zi - rs[q] * zi1;
+      // the sweep's columns in groups of 8: the loads of a group are issued
+      // together (Z may live in global memory), then its 8 rotations
+      for (int q0 = 0; q0 < cnt; q0 += 8) {
+        T zb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) zb[u] = (q0 + u < cnt) ? Z[(int64_t)(i0 - q0 - u) * ld + row] : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int q = q0 + u;
+          if (q < cnt) {
+            Z[(int64_t)(i0 - q + 1) * ld + row] = rs[q] * zb[u] + rc[q] * zi1;
+            zi1 = rc[q] * zb[u] - rs[q] * zi1;
+          }
+        }
       }
       Z[(int64_t)(i0 + 1 - cnt) * ld + row] = zi1;
     }
@@ -595,8 +603,12 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_df_kernel(const EigItem
 }
 
 template <typename T>
+size_t ql_tail_smem(int max_k) {  // everything but the eigenvector array
+  return 32 * sizeof(double) + (size_t)(8 * max_k + 32) * sizeof(T) + (size_t)max_k * sizeof(int);
+}
+template <typename T>
 size_t ql_smem(int max_k) {
-  size_t tail = 32 * sizeof(double) + (size_t)(8 * max_k + 32) * sizeof(T) + (size_t)max_k * sizeof(int);
+  const size_t tail = ql_tail_smem<T>(max_k);
   return (max_k <= kEigSmemK) ? (size_t)max_k * ql_ld(max_k) * sizeof(T) + tail : tail;
 }
 
@@ -658,11 +670,15 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
   if (n_items <= 0) return cudaSuccess;
   cudaError_t e;
   if (mode == 0) {  // FP64 QL
-    const size_t smem = ql_smem<double>(max_k);
+    // eigenvectors in shared memory allow one CTA per SM at k = 128; with more
+    // matrices than SMs they go to the scratch slab (L2-resident) instead, so
+    // that four CTAs share an SM and overlap their one-thread QL recurrences
+    const bool z_smem = max_k <= kEigSmemK && !(scratch && eig_z_global(max_k, n_items));
+    const size_t smem = z_smem ? ql_smem<double>(max_k) : ql_tail_smem<double>(max_k);
     e = cudaFuncSetAttribute(eig_ql_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     eig_ql_kernel<double><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * ql_ld(max_k),
-                                                             max_k <= kEigSmemK ? 1 : 0);
+                                                             z_smem ? 1 : 0);
     count_launch();
     return cudaGetLastError();
   }
