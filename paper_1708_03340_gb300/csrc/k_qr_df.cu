@@ -158,48 +158,23 @@ __device__ __forceinline__ void st4(float2 *p, const float (&xh)[4], const float
   reinterpret_cast<float4 *>(p)[1] = make_float4(xh[2], xl[2], xh[3], xl[3]);
 }
 
-// Row j (< 32) of the lane's column, broadcast to its group.
-__device__ __forceinline__ void df_row_value(const float (&ah)[kDfNI][4], const float (&al)[kDfNI][4], int j, int lane,
-                                             float &h, float &l) {
-  const int e = j & 3;
-  const float yh0 = (e & 1) ? ah[0][1] : ah[0][0], yh1 = (e & 1) ? ah[0][3] : ah[0][2];
-  const float yl0 = (e & 1) ? al[0][1] : al[0][0], yl1 = (e & 1) ? al[0][3] : al[0][2];
-  const int src = (lane & ~7) | (j >> 2);
-  h = __shfl_sync(0xffffffffu, (e & 2) ? yh1 : yh0, src);
-  l = __shfl_sync(0xffffffffu, (e & 2) ? yl1 : yl0, src);
-}
-
-// Column j's reflector (j < 32), formed by the warp that owns column j (each
-// group for its own column; group `me` holds column j and stores):
-// alpha the diagonal entry, w the part below it, beta = R(j, j) = -sign(alpha)
-// sqrt(alpha^2 + ||w||^2), u = alpha - beta, y = [0; u; w], kappa = -1 / (beta u).
-// A column below 4 x the smallest normal FP32 number in alpha^2 + ||w||^2 (after
-// its column scaling) keeps the identity reflector.
-__device__ __forceinline__ void df_form_reflector(float (&ah)[kDfNI][4], float (&al)[kDfNI][4], float2 *yj,
-                                                  float2 *kappa_j, int j, int lane, bool me) {
-  const int s = lane & 7;
-  float qh[4] = {0.f, 0.f, 0.f, 0.f}, ql[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int i = 0; i < kDfNI; ++i) {
-    float xh[4], xl[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const bool below = 32 * i + 4 * s + e > j;
-      xh[e] = below ? ah[i][e] : 0.0f;
-      xl[e] = below ? al[i][e] : 0.0f;
-      df_dot_acc(qh[e], ql[e], xh[e], xl[e], xh[e], xl[e]);
-    }
-    if (me) st4(yj + 32 * i + 4 * s, xh, xl);
-  }
-  float s2h, s2l;
-  df_sum4(qh, ql, s2h, s2l);
-  df_group_sum(s2h, s2l);
-  float alh, all;
-  df_row_value(ah, al, j, lane, alh, all);
+// The scalars of a column's reflector from alpha (its diagonal entry) and s2
+// (the squared norm below it): beta = R(j, j) = -sign(alpha) sqrt(alpha^2 + s2),
+// u = alpha - beta (the reflector's entry at the diagonal; the part below is
+// the column itself) and kappa = -1 / (beta u), so that H = I - kappa y y^T
+// with kappa ||y||^2 = 2.  A column below 4 x the smallest normal FP32 number
+// in alpha^2 + s2 (after its column scaling) keeps the identity reflector.
+__device__ __forceinline__ void df_reflector_scalars(float alh, float all, float s2h, float s2l, float &kh, float &kl,
+                                                     float &bh, float &bl, float &uh, float &ul) {
   float x2h, x2l, t0h, t0l;
   df_mul(alh, all, alh, all, t0h, t0l);
   df_add(t0h, t0l, s2h, s2l, x2h, x2l);
-  float kh = 0.0f, kl = 0.0f, bh = alh, bl = all, uh = 0.0f, ul = 0.0f;
+  kh = 0.0f;
+  kl = 0.0f;
+  bh = alh;
+  bl = all;
+  uh = 0.0f;
+  ul = 0.0f;
   if (s2h != 0.0f && x2h >= 4.0f * 1.17549435e-38f) {
     float nh, nl;
     df_sqrt(x2h, x2l, nh, nl);
@@ -217,17 +192,77 @@ __device__ __forceinline__ void df_form_reflector(float (&ah)[kDfNI][4], float (
     kh = -rh;
     kl = -rl;
   }
-  if (!me) return;
-  if ((j >> 2) == s) {  // row j of chunk 0 lies in this lane
+}
+
+// Sum of a pair over the whole warp.
+__device__ __forceinline__ void df_warp_sum(float &h, float &l) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if (e == (j & 3)) {
-        yj[j] = make_float2(uh, ul);
-        ah[0][e] = bh;
-        al[0][e] = bl;
-      }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add(h, l, oh, ol, h, l);
   }
-  if (s == 0) *kappa_j = make_float2(kh, kl);
+}
+
+// One step of the look-ahead warp (lane l holds rows 32 i + l of one column):
+// the column c (j + 1) as its owner left it in `stage` (H_0 .. H_{j-1} applied)
+// takes H_j (y_j, kappa_j) unless `apply` is false (c = 0), and its reflector
+// y_c, kappa_c and R(c, c) = beta_c are written (c < 32).
+__device__ __forceinline__ void df_lookahead_step(const float2 *stage, const float2 *yj, float2 tj, bool apply,
+                                                  float2 *yc, float2 *kappa_c, float2 *rdiag_c, int c, int lane) {
+  float xh[kDfNI], xl[kDfNI];
+#pragma unroll
+  for (int i = 0; i < kDfNI; ++i) {
+    const float2 v = stage[32 * i + lane];
+    xh[i] = v.x;
+    xl[i] = v.y;
+  }
+  if (apply) {
+    float d0h = 0.f, d0l = 0.f, d1h = 0.f, d1l = 0.f;
+#pragma unroll
+    for (int i = 0; i < kDfNI; i += 2) {
+      const float2 y0 = yj[32 * i + lane], y1 = yj[32 * (i + 1) + lane];
+      df_dot_acc(d0h, d0l, y0.x, y0.y, xh[i], xl[i]);
+      df_dot_acc(d1h, d1l, y1.x, y1.y, xh[i + 1], xl[i + 1]);
+    }
+    df_norm(d0h, d0l);
+    df_norm(d1h, d1l);
+    float dh, dl;
+    df_add(d0h, d0l, d1h, d1l, dh, dl);
+    df_warp_sum(dh, dl);
+    float ch, cl;
+    df_mul(tj.x, tj.y, dh, dl, ch, cl);
+#pragma unroll
+    for (int i = 0; i < kDfNI; ++i) {
+      const float2 y = yj[32 * i + lane];
+      df_axpy_neg(xh[i], xl[i], ch, cl, y.x, y.y);
+    }
+  }
+  float q0h = 0.f, q0l = 0.f, q1h = 0.f, q1l = 0.f;
+#pragma unroll
+  for (int i = 0; i < kDfNI; i += 2) {
+    const bool b0 = 32 * i + lane > c, b1 = 32 * (i + 1) + lane > c;
+    const float h0 = b0 ? xh[i] : 0.f, l0 = b0 ? xl[i] : 0.f;
+    const float h1 = b1 ? xh[i + 1] : 0.f, l1 = b1 ? xl[i + 1] : 0.f;
+    df_dot_acc(q0h, q0l, h0, l0, h0, l0);
+    df_dot_acc(q1h, q1l, h1, l1, h1, l1);
+  }
+  df_norm(q0h, q0l);
+  df_norm(q1h, q1l);
+  float s2h, s2l;
+  df_add(q0h, q0l, q1h, q1l, s2h, s2l);
+  df_warp_sum(s2h, s2l);
+  const float alh = __shfl_sync(0xffffffffu, xh[0], c), all = __shfl_sync(0xffffffffu, xl[0], c);
+  float kh, kl, bh, bl, uh, ul;
+  df_reflector_scalars(alh, all, s2h, s2l, kh, kl, bh, bl, uh, ul);
+#pragma unroll
+  for (int i = 0; i < kDfNI; ++i) {
+    const int r = 32 * i + lane;
+    yc[r] = r > c ? make_float2(xh[i], xl[i]) : (r == c ? make_float2(uh, ul) : make_float2(0.f, 0.f));
+  }
+  if (lane == 0) {
+    *kappa_c = make_float2(kh, kl);
+    *rdiag_c = make_float2(bh, bl);
+  }
 }
 
 // a <- a - kappa (y^T a) y for the lane's column; upd = false leaves a
@@ -260,55 +295,80 @@ __device__ __forceinline__ void df_apply_reflector(float (&ah)[kDfNI][4], float 
   }
 }
 
+// NW warps hold the block's columns (four each); warp NW is the look-ahead
+// warp: while the others apply H_j to their columns it brings column j + 1 up
+// to date and forms its reflector, so that the barrier of step j + 1 waits
+// for the longest update rather than for an update followed by a reflector.
+// The owner of column j + 2 leaves it in a staging buffer (two, alternating)
+// after applying H_j.  R's diagonal comes from the look-ahead warp.
 template <int NW>
-__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 4) qr_df_kernel(const QrItem *__restrict__ items) {
+__global__ void __launch_bounds__((NW + 1) * 32, 1) qr_df_kernel(const QrItem *__restrict__ items) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const QrItem it = items[blockIdx.x];
   const int m = it.m, n = it.n;
+  // 16-byte vector accesses go to V and stage only; both start at multiples of
+  // 2 KB (kDfRows pairs), tau and rdiag (8-byte accesses) come after them
   float2 *V = reinterpret_cast<float2 *>(smem_raw);  // kDfRows x n: y_j in column j
-  float2 *tau = V + (int64_t)kDfRows * n;            // n: kappa_j
+  float2 *stage = V + (int64_t)kDfRows * n;          // 2 x kDfRows: the next column, alternating
+  float2 *tau = stage + 2 * kDfRows;                 // n: kappa_j
+  float2 *rdiag = tau + n;                           // n: R(j, j)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool look = warp == NW;
   const int g = lane >> 3, s = lane & 7;
-  const int c = 4 * warp + g;  // this lane's column
-  const double *A = static_cast<const double *>(it.A) + (int64_t)c * it.lda;
-  // the column's largest exponent in the block (integer compares of the high words)
-  uint32_t mh = 0u;
-#pragma unroll
-  for (int i = 0; i < kDfNI; ++i)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int r = 32 * i + 4 * s + e;
-      if (c < n && r < m) mh = max(mh, abs_hi32(A[r]));
-    }
-#pragma unroll
-  for (int o = 1; o < 8; o <<= 1) mh = max(mh, __shfl_xor_sync(0xffffffffu, mh, o));
-  const bool bad = mh >= 0x7FF00000u;  // Inf or NaN in the column: NaN throughout
-  const int Ec = (mh >> 20) ? (int)(mh >> 20) - 1022 : 0;
+  const int c = 4 * warp + g;  // this lane's column (regular warps)
   float ah[kDfNI][4], al[kDfNI][4];
+  int Ec = 0;
+  if (!look) {
+    const double *A = static_cast<const double *>(it.A) + (int64_t)c * it.lda;
+    // the column's largest exponent in the block (integer compares of the high words)
+    uint32_t mh = 0u;
 #pragma unroll
-  for (int i = 0; i < kDfNI; ++i)
+    for (int i = 0; i < kDfNI; ++i)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int r = 32 * i + 4 * s + e;
-      df_from_f64((c < n && r < m) ? A[r] : 0.0, Ec, ah[i][e], al[i][e]);
-      if (bad) ah[i][e] = __uint_as_float(0x7FC00000u);
-    }
-  if (warp == 0) df_form_reflector(ah, al, V, tau, 0, lane, g == 0);
-  for (int j = 0; j + 1 < n; ++j) {
-    __syncthreads();                  // y_j and kappa_j are in shared memory
-    if (4 * warp + 3 <= j) continue;  // no column of this warp lies right of j
-    df_apply_reflector(ah, al, V + (int64_t)j * kDfRows, tau[j], c > j, s);
-    if (warp == ((j + 1) >> 2))       // the owner of column j+1 forms its reflector
-      df_form_reflector(ah, al, V + (int64_t)(j + 1) * kDfRows, tau + j + 1, j + 1, lane, g == ((j + 1) & 3));
+      for (int e = 0; e < 4; ++e) {
+        const int r = 32 * i + 4 * s + e;
+        if (c < n && r < m) mh = max(mh, abs_hi32(A[r]));
+      }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) mh = max(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+    const bool bad = mh >= 0x7FF00000u;  // Inf or NaN in the column: NaN throughout
+    Ec = (mh >> 20) ? (int)(mh >> 20) - 1022 : 0;
+#pragma unroll
+    for (int i = 0; i < kDfNI; ++i)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 32 * i + 4 * s + e;
+        df_from_f64((c < n && r < m) ? A[r] : 0.0, Ec, ah[i][e], al[i][e]);
+        if (bad) ah[i][e] = __uint_as_float(0x7FC00000u);
+      }
+    if (c < 2 && c < n)  // columns 0 and 1 for the look-ahead warp
+#pragma unroll
+      for (int i = 0; i < kDfNI; ++i) st4(stage + c * kDfRows + 32 * i + 4 * s, ah[i], al[i]);
   }
   __syncthreads();
+  if (look) df_lookahead_step(stage, V, make_float2(0.f, 0.f), false, V, tau, rdiag, 0, lane);
+  for (int j = 0; j + 1 < n; ++j) {
+    __syncthreads();  // y_j and kappa_j are in shared memory, column j + 1 is staged
+    if (look) {
+      df_lookahead_step(stage + ((j + 1) & 1) * kDfRows, V + (int64_t)j * kDfRows, tau[j], true,
+                        V + (int64_t)(j + 1) * kDfRows, tau + j + 1, rdiag + j + 1, j + 1, lane);
+    } else if (4 * warp + 3 > j) {  // some column of this warp lies right of j
+      df_apply_reflector(ah, al, V + (int64_t)j * kDfRows, tau[j], c > j, s);
+      if (j + 2 < n && c == j + 2)  // the owner of column j + 2 stages it
+#pragma unroll
+        for (int i = 0; i < kDfNI; ++i) st4(stage + ((j + 2) & 1) * kDfRows + 32 * i + 4 * s, ah[i], al[i]);
+    }
+  }
+  __syncthreads();
+  if (look) return;  // no barrier follows
   // R (n x n upper triangular), column c scaled back by 2^Ec; n <= 32 rows: chunk 0
   double *R = static_cast<double *>(it.R) + (int64_t)c * it.ldr;
   if (c < n) {
+    const float2 dgc = rdiag[c];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int r = 4 * s + e;
-      if (r < n) R[r] = (r <= c) ? df_to_f64(ah[0][e], al[0][e], Ec) : 0.0;
+      if (r < n) R[r] = (r < c) ? df_to_f64(ah[0][e], al[0][e], Ec) : (r == c ? df_to_f64(dgc.x, dgc.y, Ec) : 0.0);
     }
   }
   // Q = H_0 H_1 ... H_{n-1} [I; 0], accumulated backwards on the columns of
@@ -336,10 +396,10 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 4) qr_df_kernel(const Q
 
 template <int NW>
 cudaError_t launch_qr_df_nw(const QrItem *d_items, int n_items, int max_n, cudaStream_t s) {
-  const size_t smem = ((size_t)kDfRows * max_n + max_n) * sizeof(float2);
+  const size_t smem = ((size_t)kDfRows * max_n + max_n + 2 * kDfRows + max_n) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(qr_df_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  qr_df_kernel<NW><<<n_items, NW * 32, smem, s>>>(d_items);
+  qr_df_kernel<NW><<<n_items, (NW + 1) * 32, smem, s>>>(d_items);
   count_launch();
   return cudaGetLastError();
 }
