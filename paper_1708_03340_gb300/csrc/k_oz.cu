@@ -36,25 +36,26 @@
 //     k_gemm.cu).
 //
 // Kernels:
-//   oz_split_kernel  one CTA per (item, operand, batch, 128-row tile, chunk):
-//                    pass 1 finds every row's exponent, pass 2 writes the S
-//                    BF16 slices straight into the tensor core's canonical
+//   oz_split_kernel  one CTA per (item, operand, batch, 128-row block, chunk):
+//                    every row's exponent over the chunk, then the S BF16
+//                    slices written straight into the tensor core's canonical
 //                    no-swizzle K-major shared-memory layout (core matrices of
 //                    8 rows x 16 bytes), one 8 KB block per slice and 32-wide
-//                    reduction stage, so that the GEMM fetches a stage of all
-//                    slices with one bulk copy per operand.
-//   oz_gemm_kernel   one CTA per 128 x 128 output tile and chunk, 192 threads:
-//                    warp 4 issues the bulk copies (cp.async.bulk, mbarrier
-//                    transaction counts) into two stage buffers, one thread of
-//                    warp 5 issues the MMAs (tcgen05.mma kind::f16, BF16 x
-//                    BF16 -> FP32, M = N = 128, K = 16) into four accumulators
-//                    of 128 TMEM columns each and commits each stage's MMAs to
-//                    that buffer's "empty" barrier, and warps 0-3 (TMEM lanes
-//                    0-127) read the accumulators with tcgen05.ld once all
-//                    MMAs have committed.  Every mbarrier wait is bounded by
-//                    time (wait.cuh); one that gives up sets g_oz_status, lets
-//                    the issued MMAs finish (bounded) before the TMEM is freed,
-//                    writes NaN in place of its results and returns.
+//                    reduction stage, so that the GEMM fetches a stage with a
+//                    few bulk copies.  Rows contiguous along the reduction are
+//                    read once by lane groups (the exponent a group maximum);
+//                    rows adjacent in memory are read in two passes.
+//   oz_gemm_kernel   persistent, one CTA per SM walking the launch's tiles of
+//                    128 rows x 64 columns, 320 threads: warp 8 issues the
+//                    bulk copies (cp.async.bulk, mbarrier transaction counts)
+//                    into a three-stage ring, one thread of warp 9 issues the
+//                    MMAs (tcgen05.mma kind::f16, BF16 x BF16 -> FP32, M = 128,
+//                    N = 64, K = 16) into three or four accumulators of one of
+//                    two TMEM buffers, and warps 0-7 read a finished tile's
+//                    accumulators with tcgen05.ld while the next tile's MMAs
+//                    run.  Every mbarrier wait is bounded by time (wait.cuh);
+//                    one that gives up sets g_oz_status, lets the issued MMAs
+//                    finish (bounded) before the TMEM is freed, and returns.
 #include <stdint.h>
 
 #include "internal.h"
@@ -109,16 +110,20 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// Waits for the phase of the given parity; false when kWaitLimitNs passed first.
+// Each try_wait may suspend the thread for up to kSuspendHintNs (it resumes
+// as soon as the phase completes), so waiting warps take few issue slots.
+constexpr uint32_t kSuspendHintNs = 1000000;
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   const uint64_t t0 = globaltimer_ns();
   for (;;) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.b32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     if (done) return true;
     if ((int64_t)(globaltimer_ns() - t0) > kWaitLimitNs) return false;
@@ -135,14 +140,19 @@ __device__ __forceinline__ void chunk_range(const GemmItem &it, int chunk, int64
   if (f1 < f0) f1 = f0;
 }
 
-// Balanced base-256 digits of x on the grid of exponent E (|x| < 2^E):
-// F = round(|x| 2^(8S - E)), F = sum_i d_i 256^(S-1-i), d_0 in [0, 256],
-// d_i in [-128, 127]; the digits carry the sign of x.  Integer operations
-// only (no FP64 arithmetic): the raw bytes of F are extracted from its two
-// 32-bit halves, then the carries of the balanced form run from the least
-// significant digit up.  Zeros and subnormals give zero digits.
+// The S slices of x on the grid of exponent E (|x| < 2^E) as FP32 values
+// (each exactly a BF16 value): F = round(|x| 2^(8S - E)) written in balanced
+// base-256 digits, F = sum_i d_i 256^(S-1-i) with d_0 in [0, 256] and d_i in
+// [-128, 127] for i > 0, slice i = sign(x) d_i 2^(-8(i+1)).  Integer
+// operations only, no carry chain: adding 128 to every digit position below
+// the top (one 64-bit add of 0x80..80) makes byte i of the sum d_i + 128 for
+// i > 0 and leaves d_0 above them.  The float of a digit comes from the bits
+// of m_i = 1.5 2^(23 - 8(i+1)), whose unit in the last place is 2^(-8(i+1)):
+// bits(m_i) + k is the float m_i + k 2^(-8(i+1)), minus m_i exactly; the
+// -128 and the sign fold into that integer add.  Zeros and subnormals give
+// zero slices.
 template <int S>
-__device__ __forceinline__ void oz_digits(double x, int E, int (&d)[S]) {
+__device__ __forceinline__ void oz_slice_values(double x, int E, float (&f)[S]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
   const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
@@ -152,33 +162,30 @@ __device__ __forceinline__ void oz_digits(double x, int E, int (&d)[S]) {
     if (sh <= 0) F = mant << (-sh);         // only for S = 7 (then -sh <= 3)
     else if (sh < 60) F = (mant + (1ull << (sh - 1))) >> sh;
   }
-  const uint32_t lo = (uint32_t)F, hi = (uint32_t)(F >> 32);
-  int carry = 0;
+  unsigned long long bias = 0;
 #pragma unroll
-  for (int i = S - 1; i >= 1; --i) {
-    const int byte = S - 1 - i;  // byte of F holding digit i (S <= 6: bytes 0 .. 4)
-    const int raw = (int)(((byte < 4 ? lo : hi) >> (8 * (byte & 3))) & 255u);
-    const int t = raw + carry;
-    carry = t >= 128;
-    d[i] = t - (carry << 8);
-  }
-  d[0] = (int)(F >> (8 * (S - 1))) + carry;
-  if (bits >> 63) {
+  for (int j = 0; j < S - 1; ++j) bias |= 128ull << (8 * j);
+  const unsigned long long G = F + bias;
+  const uint32_t lo = (uint32_t)G, hi = (uint32_t)(G >> 32);
+  const bool neg = (bits >> 63) != 0;
 #pragma unroll
-    for (int i = 0; i < S; ++i) d[i] = -d[i];
+  for (int i = 1; i < S; ++i) {
+    const int byte = S - 1 - i;  // byte of G holding digit i + 128 (S <= 6: bytes 0 .. 4)
+    const uint32_t raw = ((byte < 4 ? lo : hi) >> (8 * (byte & 3))) & 255u;
+    const uint32_t mb = ((uint32_t)(127 + 23 - 8 * (i + 1)) << 23) | 0x400000u;
+    f[i] = __fsub_rn(__uint_as_float(neg ? mb + 128u - raw : mb - 128u + raw), __uint_as_float(mb));
   }
+  const uint32_t d0 = (uint32_t)(G >> (8 * (S - 1)));  // [0, 256]
+  constexpr uint32_t mb0 = ((uint32_t)(127 + 23 - 8) << 23) | 0x400000u;
+  f[0] = __fsub_rn(__uint_as_float(neg ? mb0 - d0 : mb0 + d0), __uint_as_float(mb0));
 }
 
-// Two slices i of neighbouring elements as one 32-bit word of BF16 values: the
-// low half a's (the element at the lower address), the high half b's.  A digit
-// d (|d| <= 256) becomes the float d exactly without a conversion instruction
-// (the bits of 1.5 2^23 plus d are the float 1.5 2^23 + d, minus 1.5 2^23),
-// times 2^(-8(i+1)); its BF16 bits are the upper half of that exact float.
-__device__ __forceinline__ uint32_t slice_pair_bf16(int a, int b, int i) {
-  const float sc = __uint_as_float((uint32_t)(127 - 8 * (i + 1)) << 23);
-  const float fa = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + a), 12582912.0f), sc);
-  const float fb = __fmul_rn(__fsub_rn(__int_as_float(0x4B400000 + b), 12582912.0f), sc);
-  return __byte_perm(__float_as_uint(fa), __float_as_uint(fb), 0x7632);
+// Slices i of neighbouring elements as one 32-bit word of BF16 values: the
+// low half a's (the element at the lower address), the high half b's; a
+// slice value has at most 9 significant bits, so its BF16 bits are the upper
+// half of its FP32 bits.
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
+  return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
 }
 
 // The four accumulators D_0 + D_1 + D_2 + D_3 (in grid units) as a
@@ -277,17 +284,26 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
       off[e] = (int64_t)(l - qk * K) + (ko0 + qk) * sko;
     }
     const int q = li >> 2, kk0 = (li & 3) * 8;
+    // rows beyond the operand (padding) feed only discarded outputs: not read, left unwritten
+    auto load_row = [&](int r0, double (&dst)[8]) {
+      const int grow = tile * OZ_M + r0 + sub;
+      const bool live = r0 < OZ_M && grow < rows;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) dst[e] = (live && in[e]) ? X[(int64_t)grow * sr + off[e]] : 0.0;
+    };
+    double vn[8];  // the next row's values, loaded while the current row is sliced
+    load_row(warp * rpw, vn);
     for (int r0 = warp * rpw; r0 < OZ_M; r0 += 8 * rpw) {
       const int r = r0 + sub;
       const int grow = tile * OZ_M + r;
-      const bool live = grow < rows;  // padding rows feed only discarded outputs: left unwritten
+      const bool live = grow < rows;
       double v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = vn[e];
+      load_row(r0 + 8 * rpw, vn);
       uint32_t mh = 0u;  // largest high word of |x|: its exponent field is the row's largest exponent
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        v[e] = (live && in[e]) ? X[(int64_t)grow * sr + off[e]] : 0.0;
-        mh = max(mh, abs_hi(v[e]));
-      }
+      for (int e = 0; e < 8; ++e) mh = max(mh, abs_hi(v[e]));
       for (int o = lpr >> 1; o > 0; o >>= 1) mh = max(mh, __shfl_xor_sync(0xffffffffu, mh, o));
       const bool bad = mh >= kHiNonFinite;
       const int E = row_exponent(mh);
@@ -297,11 +313,11 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
       uint32_t w[S][4];
 #pragma unroll
       for (int e = 0; e < 8; e += 2) {
-        int d0[S], d1[S];
-        oz_digits<S>(bad ? 0.0 : v[e], E, d0);
-        oz_digits<S>(bad ? 0.0 : v[e + 1], E, d1);
+        float fa[S], fb[S];
+        oz_slice_values<S>(bad ? 0.0 : v[e], E, fa);
+        oz_slice_values<S>(bad ? 0.0 : v[e + 1], E, fb);
 #pragma unroll
-        for (int i = 0; i < S; ++i) w[i][e >> 1] = slice_pair_bf16(d0[i], d1[i], i);
+        for (int i = 0; i < S; ++i) w[i][e >> 1] = bf16_pair(fa[i], fb[i]);
       }
 #pragma unroll
       for (int i = 0; i < S; ++i)
@@ -334,22 +350,31 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
   // pass 2: slices, 8 reduction indices of one row per step (16 bytes per slice);
   // padding rows (beyond the operand) feed only discarded outputs and stay unwritten
   if (!row_in) return;
+  // the next step's 8 values are loaded while the current step is sliced
+  auto load8 = [&](int g, double (&dst)[8]) {
+    const int l0 = (g / (OZ_KC / 8)) * OZ_KC + (g % (OZ_KC / 8)) * 8;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      dst[e] = (g < nst * (OZ_KC / 8) && l0 + e < len && E != OZ_EXP_NONFINITE) ? Xr[offt[l0 + e]] : 0.0;
+  };
+  double vn[8];
+  load8(h, vn);
   for (int g = h; g < nst * (OZ_KC / 8); g += 2) {
     const int q = g / (OZ_KC / 8), kk0 = (g % (OZ_KC / 8)) * 8;
+    double v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = vn[e];
+    load8(g + 2, vn);
     uint32_t w[S][4];
 #pragma unroll
     for (int i = 0; i < S; ++i) w[i][0] = w[i][1] = w[i][2] = w[i][3] = 0u;
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
-      const int l = q * OZ_KC + kk0 + e;
-      double va = 0.0, vb = 0.0;
-      if (l < len && E != OZ_EXP_NONFINITE) va = Xr[offt[l]];
-      if (l + 1 < len && E != OZ_EXP_NONFINITE) vb = Xr[offt[l + 1]];
-      int d0[S], d1[S];
-      oz_digits<S>(va, E, d0);
-      oz_digits<S>(vb, E, d1);
+      float fa[S], fb[S];
+      oz_slice_values<S>(v[e], E, fa);
+      oz_slice_values<S>(v[e + 1], E, fb);
 #pragma unroll
-      for (int i = 0; i < S; ++i) w[i][e >> 1] = slice_pair_bf16(d0[i], d1[i], i);
+      for (int i = 0; i < S; ++i) w[i][e >> 1] = bf16_pair(fa[i], fb[i]);
     }
 #pragma unroll
     for (int i = 0; i < S; ++i)
