@@ -406,10 +406,12 @@ struct Plan {
       cur().oz_slices = sl;
     }
     Launch &L = cur();
+    const bool slice_only = mixed && (g.oz_pre & 2);  // operand A's slices only: no tiles, no output
     g.tile0 = L.tiles;
     L.tiles += g.tiles_m * g.tiles_n * g.batch * g.ksplit;
     g.tc_tile0 = L.tc_tiles;
-    L.tc_tiles += g.tc_tiles_m * ((g.N + oz_gemm_tile_n() - 1) / oz_gemm_tile_n()) * g.batch * g.ksplit;
+    if (!slice_only)
+      L.tc_tiles += g.tc_tiles_m * ((g.N + oz_gemm_tile_n() - 1) / oz_gemm_tile_n()) * g.batch * g.ksplit;
     if (mixed) {
       // BF16 slice blocks (stages of oz_stage_k() reduction indices) and
       // exponents, for this launch only; an operand that every batch entry
@@ -420,17 +422,32 @@ struct Plan {
       g.oz_share = (g.batch > 1 && g.sab == 0 ? 1 : 0) | (g.batch > 1 && g.sbb == 0 ? 2 : 0);
       const int ba = (g.oz_share & 1) ? 1 : g.batch, bb = (g.oz_share & 2) ? 1 : g.batch;
       const size_t blk = (size_t)oz_block_bytes() * L.oz_slices * g.oz_stages * g.ksplit;
-      g.oza = lalloc_bytes(blk * ba * g.tc_tiles_m);
-      g.ozb = lalloc_bytes(blk * bb * g.tc_tiles_n);
-      g.oea = static_cast<int *>(lalloc_bytes(sizeof(int) * (size_t)ba * g.tc_tiles_m * oz_tile_m() * g.ksplit));
-      g.oeb = static_cast<int *>(lalloc_bytes(sizeof(int) * (size_t)bb * g.tc_tiles_n * oz_tile_n() * g.ksplit));
+      // given slices (oz_pre bit 0, made by an earlier slicing-only launch of the
+      // same chunk layout) are used as they are; a slicing-only item has no B
+      // and writes A's slices to the buffers it brings
+      const bool make_a = !(g.oz_pre & 1), make_b = !(g.oz_pre & 2);
+      if (make_a && !slice_only) {
+        g.oza = lalloc_bytes(blk * ba * g.tc_tiles_m);
+        g.oea = static_cast<int *>(lalloc_bytes(sizeof(int) * (size_t)ba * g.tc_tiles_m * oz_tile_m() * g.ksplit));
+      }
+      if (make_b) {
+        g.ozb = lalloc_bytes(blk * bb * g.tc_tiles_n);
+        g.oeb = static_cast<int *>(lalloc_bytes(sizeof(int) * (size_t)bb * g.tc_tiles_n * oz_tile_n() * g.ksplit));
+      }
       g.oz_split0 = L.oz_split;
-      L.oz_split += g.ksplit * (ba * g.tc_tiles_m + bb * g.tc_tiles_n);
-      const int tiles_here = g.tc_tiles_m * ((g.N + oz_gemm_tile_n() - 1) / oz_gemm_tile_n()) * g.batch * g.ksplit;
-      L.tile_item.insert(L.tile_item.end(), (size_t)tiles_here, L.n);
+      L.oz_split += g.ksplit * ((make_a ? ba * g.tc_tiles_m : 0) + (make_b ? bb * g.tc_tiles_n : 0));
+      if (!slice_only) {
+        const int tiles_here = g.tc_tiles_m * ((g.N + oz_gemm_tile_n() - 1) / oz_gemm_tile_n()) * g.batch * g.ksplit;
+        L.tile_item.insert(L.tile_item.end(), (size_t)tiles_here, L.n);
+      }
       // algorithmic bytes: the FP64 operands read once, their slices written once
       const double red = (double)g.K * g.Ko;
-      L.split_bytes += red * ((double)ba * g.M + (double)bb * g.N) * (8.0 + 2.0 * L.oz_slices);
+      L.split_bytes += red * ((make_a ? (double)ba * g.M : 0.0) + (make_b ? (double)bb * g.N : 0.0)) *
+                       (8.0 + 2.0 * L.oz_slices);
+    }
+    if (slice_only) {
+      push_item(g, node);
+      return;
     }
     const double fl = 2.0 * g.M * g.N * (double)g.K * g.Ko * g.batch;
     L.flops += fl;
@@ -710,6 +727,10 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
       prof_end(HT_K_SPLIT, s, L.split_bytes);
       if (e != cudaSuccess) return fail(HT_ECUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
     }
+    if (L.kind == L_GEMM && P.mixed && L.tc_tiles == 0) {  // slicing-only launch
+      kernels += (int)(g_launches - before);
+      continue;
+    }
     prof_begin((int)L.kind, s);
     switch (L.kind) {
       case L_GEMM: {
@@ -847,15 +868,15 @@ struct Mat {
 
 void plan_tsqr_narrow(Plan &P, const std::vector<Mat> &mats);
 
-constexpr int kPanel = 64;  // widest matrix the register-resident QR blocks factor
 // Panel width of the mixed path: narrower panels move QR work from the FP64
 // Householder blocks (4 m w^2 per panel) into the panel projections, which run
 // on the tensor cores.
 constexpr int kPanelMixed = 32;
 
 // Reduced QR of matrices wider than one panel: columns are taken in panels
-// of kPanel; panel p is projected twice against the finished Q columns
-// (block Gram-Schmidt, "twice is enough": R[<p, p] = C1 + C2 with
+// of P.panel (64, or 32 on the mixed path); panel p is projected twice
+// against the finished Q columns (block Gram-Schmidt, "twice is enough":
+// R[<p, p] = C1 + C2 with
 // C = Q_<p^T A_p, A_p -= Q_<p C) and then factored by the TSQR of
 // plan_tsqr_narrow.  A (the matrix, overwritten by the projections) and Q
 // (the output) may be the same buffer.
@@ -879,6 +900,32 @@ void plan_tsqr_panels(Plan &P, const std::vector<Mat> &mats) {
     P.copy(z, M.node);
   }
   constexpr int kChunk = 256;  // rows per chunk of the long reductions Q^T A
+  // Mixed path: the projections C = Q_<p^T A_p take Q's columns as operand A,
+  // with one exponent per (column, 256-row chunk), so the slices of a finished
+  // panel do not change with the panels after it.  Each panel is sliced once,
+  // right after its TSQR, into a per-matrix buffer of the same chunk layout
+  // (one block row per 128 columns), and both passes of every later panel use
+  // it instead of slicing Q_<p again.
+  struct QSlices {
+    void *oza = nullptr;
+    int *oea = nullptr;
+    int ko = 0;
+    size_t tile_bytes = 0;
+  };
+  std::vector<QSlices> qs(mats.size());
+  const bool cache_q = P.mixed && max_panels > 1 && oz_tile_m() % pw == 0;
+  if (cache_q) {
+    for (size_t mi = 0; mi < mats.size(); ++mi) {
+      const Mat &M = mats[mi];
+      if (M.n <= pw) continue;  // a single panel: nothing to project
+      QSlices &c = qs[mi];
+      c.ko = (M.m + kChunk - 1) / kChunk;
+      const int tm = (M.n + oz_tile_m() - 1) / oz_tile_m();
+      c.tile_bytes = (size_t)oz_block_bytes() * P.oz_slices * (kChunk / oz_stage_k()) * c.ko;
+      c.oza = P.salloc_bytes(c.tile_bytes * tm);
+      c.oea = static_cast<int *>(P.salloc_bytes(sizeof(int) * (size_t)tm * oz_tile_m() * c.ko));
+    }
+  }
   for (int p = 0; p < max_panels; ++p) {
     struct PJ {
       const Mat *M;
@@ -927,6 +974,13 @@ void plan_tsqr_panels(Plan &P, const std::vector<Mat> &mats) {
           g.Ko = ko;
           g.k_total = M.m;
           g.ksplit = split_for(tiles, ko);
+          const QSlices &c = qs[&M - mats.data()];
+          if (c.oza) {  // Q_<p's slices from the panels' slicing launches
+            g.oz_pre = 1;
+            g.oza = c.oza;
+            g.oea = c.oea;
+            g.ksplit = ko;  // the slicing launches' chunk layout: one chunk per 256 rows
+          }
           P.gemm(g, M.node);
         }
         // A_p -= Q_<p C
@@ -1001,6 +1055,35 @@ void plan_tsqr_panels(Plan &P, const std::vector<Mat> &mats) {
       panel.push_back(q);
     }
     plan_tsqr_narrow(P, panel);
+    if (!cache_q) continue;
+    // slices of this panel's Q columns for the later panels' projections
+    P.begin(L_GEMM);
+    for (PJ &j : pj) {
+      const Mat &M = *j.M;
+      const QSlices &c = qs[&M - mats.data()];
+      if (!c.oza || j.c0 + j.w >= M.n) continue;  // no later panel of this matrix
+      GemmItem g = gemm0();
+      g.A = static_cast<const char *>(M.Q) + (int64_t)j.c0 * M.ldq * esz;
+      g.sam = M.ldq;
+      g.sak = 1;
+      g.sako = kChunk;
+      g.B = g.A;
+      g.sbk = 1;
+      g.sbn = 1;
+      g.M = j.w;
+      g.N = 1;
+      g.K = kChunk;
+      g.Ko = c.ko;
+      g.k_total = M.m;
+      g.ksplit = c.ko;
+      g.oz_pre = 2;
+      // the panel's columns sit at rows c0 % 128 .. of block row c0 / 128 (panels
+      // are at most 32 wide and start at multiples of 32: never across a block row)
+      g.oz_row0 = j.c0 % oz_tile_m();
+      g.oza = static_cast<char *>(c.oza) + (size_t)(j.c0 / oz_tile_m()) * c.tile_bytes;
+      g.oea = c.oea + (size_t)(j.c0 / oz_tile_m()) * oz_tile_m() * c.ko;
+      P.gemm(g, M.node);
+    }
   }
 }
 
@@ -1455,7 +1538,6 @@ void plan_gramians_sqrt(Plan &P, std::vector<TState> &TS, const std::vector<doub
     }
     // factors of the inner sons for the next level
     P.begin(L_CHOL);
-    bool any = false;
     for (Job &J : jobs) {
       const ht_tree &T = J.S->x->tr;
       for (int s : {T.s1[J.t], T.s2[J.t]}) {
@@ -1467,10 +1549,8 @@ void plan_gramians_sqrt(Plan &P, std::vector<TState> &TS, const std::vector<doub
         c.S = static_cast<float *>(J.S->Sf[s]);
         c.k = ks;
         P.chol(c, J.S->node_base + s);
-        any = true;
       }
     }
-    (void)any;
   }
 }
 

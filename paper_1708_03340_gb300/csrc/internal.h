@@ -45,6 +45,11 @@ struct GemmItem {
   int oz_stages;
   int oz_split0;
   int oz_share;  // bit 0: A, bit 1: B is the same for every batch entry (sliced once)
+  // bit 0: A's slices and exponents are given in oza / oea (made by an earlier
+  // launch), not by this launch's split; bit 1: a slicing-only item (operand A
+  // only, no B, no tiles, no output)
+  int oz_pre;
+  int oz_row0;  // slicing-only items: first row of A's slices within its 128-row block
 };
 
 // Householder QR of one row block (m >= n) held in shared memory.

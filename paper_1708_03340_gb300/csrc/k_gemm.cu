@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) != 4 ? 1
 template <typename T>
 __global__ void gemm_reduce_kernel(const GemmItem *__restrict__ items, const int *__restrict__ ranks) {
   const GemmItem &it = items[blockIdx.y];
-  if (it.ksplit <= 1) return;
+  if (it.ksplit <= 1 || (it.oz_pre & 2)) return;  // slicing-only items have no partial sums
   const int M = eff_dim(it.M, it.m_ref, 1, ranks);
   const int N = eff_dim(it.N, it.n_ref, it.n_mult, ranks);
   const int batch = eff_dim(it.batch, it.b_ref, it.b_mult, ranks);

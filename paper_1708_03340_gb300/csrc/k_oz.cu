@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
   const GemmItem &it = items[find_split(items, n_items, blockIdx.x)];
   int local = blockIdx.x - it.oz_split0;
   const int bat_a = (it.oz_share & 1) ? 1 : it.batch;  // an operand shared by the batch is sliced once
-  const int per_a = bat_a * it.tc_tiles_m * it.ksplit;
+  const int per_a = (it.oz_pre & 1) ? 0 : bat_a * it.tc_tiles_m * it.ksplit;  // A given: B only
   const int op = local < per_a ? 0 : 1;
   if (op) local -= per_a;
   const int tiles = op ? it.tc_tiles_n : it.tc_tiles_m;
@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
   unsigned char *out = static_cast<unsigned char *>(op ? it.ozb : it.oza) +
                        ((((int64_t)b * tiles + tile) * it.ksplit + chunk) * nst) * S * (int64_t)OZ_BLK;
   int *Ex = (op ? it.oeb : it.oea) + ((int64_t)b * tiles * OZ_M + (int64_t)tile * OZ_M) * it.ksplit + chunk;
+  const int row0 = op ? 0 : it.oz_row0;  // slicing-only items write their rows at an offset of the block
   // chunks hold at most 256 reduction indices, and a chunk starts at a
   // multiple of K: local index l of the chunk is (ko0 + l / K, l % K)
   const int len = (int)(f1 - f0);
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
       const bool bad = mh >= kHiNonFinite;
       const int E = row_exponent(mh);
       if (!live) continue;
-      if (li == 0) Ex[(int64_t)r * it.ksplit] = E;
+      if (li == 0) Ex[(int64_t)(r + row0) * it.ksplit] = E;
       if (q >= nst) continue;
       uint32_t w[S][4];
 #pragma unroll
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
       }
 #pragma unroll
       for (int i = 0; i < S; ++i)
-        *reinterpret_cast<uint4 *>(out + ((int64_t)q * S + i) * OZ_BLK + oz_off(r, kk0)) =
+        *reinterpret_cast<uint4 *>(out + ((int64_t)q * S + i) * OZ_BLK + oz_off(r + row0, kk0)) =
             make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
     }
     return;
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
   if (h == 0) {
     const int E = row_exponent(max(red[0][r], red[1][r]));
     sexp[r] = E;
-    Ex[(int64_t)r * it.ksplit] = E;
+    if (row_in) Ex[(int64_t)(r + row0) * it.ksplit] = E;
   }
   __syncthreads();
   const int E = sexp[r];
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const GemmItem *__restric
     }
 #pragma unroll
     for (int i = 0; i < S; ++i)
-      *reinterpret_cast<uint4 *>(out + ((int64_t)q * S + i) * OZ_BLK + oz_off(r, kk0)) =
+      *reinterpret_cast<uint4 *>(out + ((int64_t)q * S + i) * OZ_BLK + oz_off(r + row0, kk0)) =
           make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
   }
 }
