@@ -754,7 +754,10 @@ ht_status enqueue_plan(const Plan &P, cudaStream_t s, const char *ib_dev, int *n
       case L_EIG:
         // square-root Gramians carry eigenvalues far below the FP32 solve's resolution,
         // which one refinement step cannot separate (it treats them as one cluster): FP64 QL
-        e = launch_eig((const EigItem *)items, L.n, L.max_n, (double *)L.scratch, s, (f64 || P.sqrt_gram) ? 0 : 1);
+        // the mixed path accumulates the eigenvectors in double-float (mode 2); the
+        // eigenvalues come from the FP64 QL recurrence in every FP64 mode
+        e = launch_eig((const EigItem *)items, L.n, L.max_n, (double *)L.scratch, s,
+                       P.mixed ? 2 : ((f64 || P.sqrt_gram) ? 0 : 1));
         break;
       case L_COPY: e = launch_copy((const CopyItem *)items, L.n, rk, 0, s); break;
       case L_COMPACT:

@@ -53,5 +53,54 @@ __device__ __forceinline__ unsigned long long df_to_f64_bits(float h, float l, i
   return sign | ((unsigned long long)ex << 52) | ((unsigned long long)W & 0xFFFFFFFFFFFFFull);
 }
 
+// (p, e) with p + e = (ah + al)(bh + bl) up to the al bl term and the
+// rounding of e (both below 2^-48 of the product).
+__device__ __forceinline__ void df_prod(float ah, float al, float bh, float bl, float &p, float &e) {
+  p = __fmul_rn(ah, bh);
+  e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+}
+
+// (h, l) = a + b for canonical pairs.
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float &h, float &l) {
+  float s, t;
+  two_sum(ah, bh, s, t);
+  t = __fadd_rn(t, __fadd_rn(al, bl));
+  fast_two_sum(s, t, h, l);
+}
+
+// (h, l) = a b.
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &h, float &l) {
+  float p, e;
+  df_prod(ah, al, bh, bl, p, e);
+  fast_two_sum(p, e, h, l);
+}
+
+// x 2^-E as a pair (|x| < 2^E): h = x's sign, scaled exponent and top 23
+// fraction bits; l = the next 23 fraction bits at their place.  Zero, FP64
+// subnormals and results below 2^-126 give zero (l alone below 2^-126 is
+// dropped).
+__device__ __forceinline__ void df_from_f64(double x, int E, float &h, float &l) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const int fe = ex - 1023 - E + 127;  // biased FP32 exponent of x 2^-E
+  h = 0.0f;
+  l = 0.0f;
+  if (ex == 0 || fe < 1) return;
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  h = __uint_as_float(sign | ((uint32_t)fe << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
+  const uint32_t k = (uint32_t)(b >> 6) & 0x7FFFFFu;  // fraction bits 28 .. 6
+  if (k != 0u && fe > 46) {
+    // k exactly as a float (1.5 2^23 trick without the half), times 2^(fe - 127 - 46)
+    const float kf = __fsub_rn(__uint_as_float(0x4B000000u | k), 8388608.0f);
+    l = __uint_as_float(__float_as_uint(__fmul_rn(kf, __uint_as_float((uint32_t)(fe - 46) << 23))) | sign);
+  }
+}
+
+__device__ __forceinline__ double df_to_f64(float h, float l, int E) {
+  return __longlong_as_double((long long)df_to_f64_bits(h, l, E));
+}
+
 }  // namespace
 }  // namespace htgb

@@ -166,7 +166,9 @@ cudaError_t launch_qr(const QrItem *d_items, int n_items, int max_m, int max_n, 
 // The same row blocks (FP64 in and out) factored in double-float arithmetic
 // on the FP32 pipe, about 2^-47 relative (k_qr_df.cu); max_n <= 32, max_m <= 256.
 cudaError_t launch_qr_df(const QrItem *d_items, int n_items, int max_m, int max_n, cudaStream_t s);
-// mode 0: FP64 QL; mode 1: FP32 QL followed by one double-float refinement step.
+// mode 0: FP64 QL; mode 1: FP32 QL followed by one double-float refinement step;
+// mode 2: FP64 QL recurrence (the eigenvalues) with the eigenvector rotations
+// applied in double-float on the FP32 pipe (about 2^-47 per rotation).
 // scratch: 4 * max_k^2 doubles per item when max_k exceeds the shared-memory sizes (eig_scratch_needed).
 cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s, int mode);
 cudaError_t launch_copy(const CopyItem *d_items, int n_items, const int *d_ranks, int f64_any, cudaStream_t s);

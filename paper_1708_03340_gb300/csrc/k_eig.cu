@@ -21,6 +21,7 @@
 // X <- X (I + E).  Used after an FP32 QL solve, with its dense products in
 // double-float on the FP32 pipes (see the kernel).
 #include "internal.h"
+#include "dfloat.cuh"
 
 namespace htgb {
 
@@ -147,8 +148,8 @@ __device__ __forceinline__ void quad_colvec(const T *Z, int ld, int o, int L, co
 }
 
 template <typename T>
-__global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__restrict__ items, void *scratch,
-                                                             int64_t scratch_stride, int z_in_smem) {
+__global__ void __launch_bounds__(EIG_THREADS, 4) eig_ql_kernel(const EigItem *__restrict__ items, void *scratch,
+                                                             int64_t scratch_stride, int z_in_smem, int df_rot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EigItem it = items[blockIdx.x];
   const int k = it.k, tid = threadIdx.x, nt = blockDim.x;
@@ -176,7 +177,11 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
   T *pv = vv2 + k;   // p of the current step
   T *rc = pv + k;
   T *rs = rc + k;
-  T *red = rs + k;
+  // df_rot: the sweep's rotations as double-float pairs (8-byte aligned: the
+  // tail starts after 32 doubles and holds only 8-byte elements for T = double)
+  float2 *rcf = reinterpret_cast<float2 *>(rs + k);
+  float2 *rsf = rcf + k;
+  T *red = reinterpret_cast<T *>(rsf + k);
   int *perm = reinterpret_cast<int *>(red + 32);
   __shared__ EigShared sh;
   // scale to max |G| = 1 and symmetrise: coalesced copy, then the
@@ -333,6 +338,19 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
     const T eps = (sizeof(T) == 8) ? T(2.220446049250313e-16) : T(1.1920929e-7);
     tol = eps * tn;
   }
+  // df_rot (mixed path): the eigenvectors are accumulated in double-float on
+  // the FP32 pipe (about 2^-47 per rotation); the QL recurrence, which alone
+  // decides the eigenvalues, stays in FP64.  Entries are at most 1 in
+  // magnitude, so no scaling is needed; each is converted in place.
+  if (df_rot) {
+    float2 *Zf = reinterpret_cast<float2 *>(Z);
+    for (int e = tid; e < k * k; e += nt) {
+      const int c = e / k, r = e - c * k;
+      float h, l;
+      df_from_f64((double)Z[(int64_t)c * ld + r], 0, h, l);
+      Zf[(int64_t)c * ld + r] = make_float2(h, l);
+    }
+  }
   for (;;) {
     // warp 0 finds the next unreduced block (a ballot over 32 off-diagonals
     // at a time); lane 0 runs the sweep's rotation recurrence
@@ -411,6 +429,48 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
     __syncthreads();
     if (sh.done) break;
     const int cnt = sh.count, i0 = sh.lo;
+    if (df_rot) {
+      for (int q = tid; q < cnt; q += nt) {
+        float h, l;
+        df_from_f64((double)rc[q], 0, h, l);
+        rcf[q] = make_float2(h, l);
+        df_from_f64((double)rs[q], 0, h, l);
+        rsf[q] = make_float2(h, l);
+      }
+      __syncthreads();
+      float2 *Zf = reinterpret_cast<float2 *>(Z);
+      for (int row = tid; row < k; row += nt) {
+        float2 z1 = Zf[(int64_t)(i0 + 1) * ld + row];
+        for (int q0 = 0; q0 < cnt; q0 += 8) {
+          float2 zb[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            zb[u] = (q0 + u < cnt) ? Zf[(int64_t)(i0 - q0 - u) * ld + row] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u;
+            if (q < cnt) {
+              const float2 c = rcf[q], sn = rsf[q];
+              float p1, e1, p2, e2, t, ah, al, bh, bl;
+              // a = s zb + c z1, b = c zb - s z1, each renormalised
+              df_prod(sn.x, sn.y, zb[u].x, zb[u].y, p1, e1);
+              df_prod(c.x, c.y, z1.x, z1.y, p2, e2);
+              two_sum(p1, p2, ah, t);
+              fast_two_sum(ah, __fadd_rn(t, __fadd_rn(e1, e2)), ah, al);
+              df_prod(c.x, c.y, zb[u].x, zb[u].y, p1, e1);
+              df_prod(sn.x, sn.y, z1.x, z1.y, p2, e2);
+              two_sum(p1, -p2, bh, t);
+              fast_two_sum(bh, __fadd_rn(t, __fsub_rn(e1, e2)), bh, bl);
+              Zf[(int64_t)(i0 - q + 1) * ld + row] = make_float2(ah, al);
+              z1 = make_float2(bh, bl);
+            }
+          }
+        }
+        Zf[(int64_t)(i0 + 1 - cnt) * ld + row] = z1;
+      }
+      __syncthreads();
+      continue;
+    }
     for (int row = tid; row < k; row += nt) {
       T zi1 = Z[(int64_t)(i0 + 1) * ld + row];
       // the sweep's columns in groups of 8: the loads of a group are issued
@@ -429,6 +489,15 @@ __global__ void __launch_bounds__(EIG_THREADS) eig_ql_kernel(const EigItem *__re
         }
       }
       Z[(int64_t)(i0 + 1 - cnt) * ld + row] = zi1;
+    }
+    __syncthreads();
+  }
+  if (df_rot) {  // eigenvectors back to FP64, in place
+    const float2 *Zf = reinterpret_cast<const float2 *>(Z);
+    for (int e = tid; e < k * k; e += nt) {
+      const int c = e / k, r = e - c * k;
+      const float2 v = Zf[(int64_t)c * ld + r];
+      Z[(int64_t)c * ld + r] = T(df_to_f64(v.x, v.y, 0));
     }
     __syncthreads();
   }
@@ -604,7 +673,8 @@ __global__ void __launch_bounds__(REFINE_THREADS) refine_df_kernel(const EigItem
 
 template <typename T>
 size_t ql_tail_smem(int max_k) {  // everything but the eigenvector array
-  return 32 * sizeof(double) + (size_t)(8 * max_k + 32) * sizeof(T) + (size_t)max_k * sizeof(int);
+  return 32 * sizeof(double) + (size_t)(8 * max_k + 32) * sizeof(T) + 2 * (size_t)max_k * sizeof(float2) +
+         (size_t)max_k * sizeof(int);
 }
 template <typename T>
 size_t ql_smem(int max_k) {
@@ -669,7 +739,7 @@ cudaError_t launch_chol(const CholItem *d_items, int n_items, cudaStream_t s) {
 cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *scratch, cudaStream_t s, int mode) {
   if (n_items <= 0) return cudaSuccess;
   cudaError_t e;
-  if (mode == 0) {  // FP64 QL
+  if (mode == 0 || mode == 2) {  // FP64 QL (mode 2: eigenvector rotations in double-float)
     // eigenvectors in shared memory allow one CTA per SM at k = 128; with more
     // matrices than SMs they go to the scratch slab (L2-resident) instead, so
     // that four CTAs share an SM and overlap their one-thread QL recurrences
@@ -678,7 +748,7 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
     e = cudaFuncSetAttribute(eig_ql_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     eig_ql_kernel<double><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * ql_ld(max_k),
-                                                             z_smem ? 1 : 0);
+                                                             z_smem ? 1 : 0, mode == 2 ? 1 : 0);
     count_launch();
     return cudaGetLastError();
   }
@@ -687,7 +757,7 @@ cudaError_t launch_eig(const EigItem *d_items, int n_items, int max_k, double *s
   e = cudaFuncSetAttribute(eig_ql_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   eig_ql_kernel<float><<<n_items, EIG_THREADS, smem, s>>>(d_items, scratch, (int64_t)max_k * ql_ld(max_k),
-                                                            max_k <= kEigSmemK ? 1 : 0);
+                                                            max_k <= kEigSmemK ? 1 : 0, 0);
   count_launch();
   const bool in_smem = max_k <= kDfMaxK;  // else the arrays use the scratch slab (4 max_k^2 doubles per item)
   if (!in_smem && !scratch) return cudaErrorInvalidValue;
