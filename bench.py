@@ -437,7 +437,8 @@ def main():
         "data": "synthetic (seeded SplitMix64/Box-Muller HT tensors)",
         "config": {"workload": args.config, "tensors_per_step": per_step, "shape": WORKLOADS[args.config]["desc"],
                    "l2": "flushed between steps (256 MB write)",
-                   "path": "mixed: F64 storage, double-float TSQR blocks (FP32 pipe, 2^-47), FP64 QL eigensolves, "
+                   "path": "mixed: F64 storage, double-float TSQR blocks (FP32 pipe, 2^-47), FP64 QL eigensolves "
+                           "(eigenvectors in double-float), "
                            "every contraction on tcgen05 (5 BF16 slices per FP64 operand, exact leading sums), "
                            "one batched launch per level, "
                            "CUDA-graph replay"},
@@ -642,7 +643,8 @@ def roofline_of(prof, steps, peaks):
              plan's maximal dims)
       split  BF16 slicing of the contraction operands: HBM, the FP64 operands read
              and their slices written once
-      eig    FP64 QL eigensolves: FP64 ALU, 9 k^3 flop per Gramian"""
+      eig    FP64 QL eigensolves (on the mixed path the eigenvector rotations in
+             double-float): FP64 ALU, 9 k^3 flop per Gramian"""
     fams = {}
     for name, rec in prof.items():
         if rec["flops"] <= 0 or name not in ("qr", "gemm", "eig", "split"):
@@ -683,7 +685,7 @@ def roofline_of(prof, steps, peaks):
     kernel = {"qr": "qr_df_kernel (double-float TSQR row blocks)",
               "gemm": "oz_gemm_kernel (tcgen05 BF16 slice products) + split-K reduction",
               "split": "oz_split_kernel (BF16 slicing of FP64 operands)",
-              "eig": "eig_ql_kernel<double> (FP64 QL)"}[name]
+              "eig": "eig_ql_kernel<double> (FP64 QL, eigenvectors in double-float)"}[name]
     top = dict(fams[name])
     top["kernel"] = kernel
     top["traffic"] = TRAFFIC_PER_LAUNCH.get(("deep", name))
