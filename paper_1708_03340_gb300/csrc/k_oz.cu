@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
     }
   } else {
     // ---- epilogue: warps 0-7; warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile
-    // rows); the tile's 16-column chunks alternate between warps 0-3 and 4-7,
+    // rows); the tile's 8-column chunks alternate between warps 0-3 and 4-7,
     // so that a tile with 32 live columns keeps all eight warps busy ----
     const int quad = warp & 3, half = warp >> 2;
     int n = 0;
@@ -631,35 +631,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
       const bool row_ok = row < M;
       double *prow = Pp ? Pp + row : Cp + (int64_t)row * scm;
       const int64_t cstride = Pp ? ldp : scn;
-      for (int c0 = half * 16; c0 < ncols; c0 += 32) {
-        uint32_t v[4][16];
+      // chunks of 8 columns (a smaller unrolled body), alternating between the halves
+      constexpr int EC = 8;
+      for (int c0 = half * EC; c0 < ncols; c0 += 2 * EC) {
+        uint32_t v[4][EC];
         if (ti.nq > 0) {
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
             if (a >= NACC) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) v[a][j] = 0u;
+              for (int j = 0; j < EC; ++j) v[a][j] = 0u;
               continue;
             }
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15}, [%16];"
-                : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
-                  "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]), "=r"(v[a][10]), "=r"(v[a][11]),
-                  "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]), "=r"(v[a][15])
-                : "r"(trow + (uint32_t)(a * OZ_TN + c0)));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
+                           "=r"(v[a][6]), "=r"(v[a][7])
+                         : "r"(trow + (uint32_t)(a * OZ_TN + c0)));
           }
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         } else {
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[a][j] = 0u;
+            for (int j = 0; j < EC; ++j) v[a][j] = 0u;
         }
         const int eb_src = c0 < 32 ? eb_lo : eb_hi;
-        unsigned long long w[16];
+        unsigned long long w[EC];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < EC; ++j) {
           const int eb = __shfl_sync(0xffffffffu, eb_src, (c0 & 31) + j);  // the same column for every lane
           w[j] = (eb == OZ_EXP_NONFINITE || ea == OZ_EXP_NONFINITE)
                      ? 0x7FF8000000000000ull
@@ -667,25 +666,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
                                       __uint_as_float(v[2][j]), __uint_as_float(v[3][j]), ea + eb);
         }
         if (!row_ok) continue;
-        const int jn = ncols - c0 < 16 ? ncols - c0 : 16;
+        const int jn = ncols - c0 < EC ? ncols - c0 : EC;
         double *pc = prow + (int64_t)(n0 + c0) * cstride;
         if (smode <= 1) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
+          for (int j = 0; j < EC; ++j)
             if (j < jn) pc[(int64_t)j * cstride] = __longlong_as_double((long long)(w[j] ^ flip));
         } else {
           // all loads of C before the first store (the stores could alias them
           // for all the compiler knows, which would serialise the loads)
-          double cv[16];
+          double cv[EC];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) cv[j] = j < jn ? pc[(int64_t)j * cstride] : 0.0;
+          for (int j = 0; j < EC; ++j) cv[j] = j < jn ? pc[(int64_t)j * cstride] : 0.0;
           if (smode == 2) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
+            for (int j = 0; j < EC; ++j)
               if (j < jn) pc[(int64_t)j * cstride] = fma(beta, cv[j], __longlong_as_double((long long)(w[j] ^ flip)));
           } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < EC; ++j) {
               if (j >= jn) continue;
               const double o = alpha * __longlong_as_double((long long)w[j]);
               pc[(int64_t)j * cstride] = beta != 0.0 ? fma(beta, cv[j], o) : o;
