@@ -46,12 +46,12 @@
 //                    read once by lane groups (the exponent a group maximum);
 //                    rows adjacent in memory are read in two passes.
 //   oz_gemm_kernel   persistent, one CTA per SM walking the launch's tiles of
-//                    128 rows x 64 columns, 320 threads: warp 8 issues the
+//                    128 rows x 64 columns, 576 threads: warp 16 issues the
 //                    bulk copies (cp.async.bulk, mbarrier transaction counts)
-//                    into a three-stage ring, one thread of warp 9 issues the
+//                    into a three-stage ring, one thread of warp 17 issues the
 //                    MMAs (tcgen05.mma kind::f16, BF16 x BF16 -> FP32, M = 128,
 //                    N = 64, K = 16) into three or four accumulators of one of
-//                    two TMEM buffers, and warps 0-7 read a finished tile's
+//                    two TMEM buffers, and warps 0-15 read a finished tile's
 //                    accumulators with tcgen05.ld while the next tile's MMAs
 //                    run.  Every mbarrier wait is bounded by time (wait.cuh);
 //                    one that gives up sets g_oz_status, lets the issued MMAs
@@ -73,8 +73,9 @@ constexpr int OZ_M = 128;                       // rows of a tile (MMA M); also 
 constexpr int OZ_N = 128;                       // columns of a tile (MMA N)
 constexpr int OZ_KC = 32;                       // reduction indices per stage
 constexpr uint32_t OZ_BLK = OZ_M * OZ_KC * 2;   // bytes of one slice block of one stage (8 KB)
-constexpr int OZ_THREADS = 320;                 // warps 0-7 epilogue, 8 producer, 9 MMA
-constexpr int OZ_EPI_THREADS = 256;
+constexpr int OZ_THREADS = 576;                 // warps 0-15 epilogue, 16 producer, 17 MMA
+constexpr int OZ_EPI_THREADS = 512;
+constexpr int OZ_PROD_WARP = 16, OZ_MMA_WARP = 17;
 constexpr int OZ_TMEM_COLS = 512;               // four FP32 accumulators of 128 columns
 constexpr int OZ_EXP_NONFINITE = 0x7FF0;        // exponent marking a row with NaN / Inf
 
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
   constexpr uint32_t STA = S * OZ_BLK, STB = S * OZ_BLK_B, STG = STA + STB;  // bytes of one stage
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (warp == 9) {
+  if (warp == OZ_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                  "r"(OZ_TMEM_COLS)
                  : "memory");
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 8) {
+  if (warp == OZ_PROD_WARP) {
     // ---- producer: the stages of every live tile, through the ring ----
     if (lane == 0) {
       int g = 0;  // stages issued so far
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
         if (*(volatile int *)&abort_flag) break;
       }
     }
-  } else if (warp == 9) {
+  } else if (warp == OZ_MMA_WARP) {
     // ---- MMA issue: per tile, products (i, j), i + j <= S - 1, into accumulator
     // min(i + j, NACC - 1) of the tile's TMEM buffer (two buffers of NACC x 64 columns) ----
     if (lane == 0) {
@@ -582,10 +583,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
                    : "memory");
     }
   } else {
-    // ---- epilogue: warps 0-7; warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile
-    // rows); the tile's 8-column chunks alternate between warps 0-3 and 4-7,
-    // so that a tile with 32 live columns keeps all eight warps busy ----
-    const int quad = warp & 3, half = warp >> 2;
+    // ---- epilogue: warps 0-15; warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile
+    // rows); the tile's 8-column chunks go to the four warps of a lane quarter
+    // in turn, so that a tile with 32 live columns keeps all sixteen busy ----
+    const int quad = warp & 3, part = warp >> 2;
     int n = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
       const TileInfo ti = tile_info(items, tile_item, ranks, t);
@@ -631,9 +632,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
       const bool row_ok = row < M;
       double *prow = Pp ? Pp + row : Cp + (int64_t)row * scm;
       const int64_t cstride = Pp ? ldp : scn;
-      // chunks of 8 columns (a smaller unrolled body), alternating between the halves
+      // chunks of 8 columns (a smaller unrolled body), dealt to the four warps of
+      // each TMEM lane quarter in turn
       constexpr int EC = 8;
-      for (int c0 = half * EC; c0 < ncols; c0 += 2 * EC) {
+      for (int c0 = part * EC; c0 < ncols; c0 += 4 * EC) {
         uint32_t v[4][EC];
         if (ti.nq > 0) {
 #pragma unroll
@@ -701,13 +703,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const GemmItem *
     }
   }
   // all MMAs complete (bounded wait) before the TMEM is freed
-  if (warp == 9) {
+  if (warp == OZ_MMA_WARP) {
     if (lane == 0 && !mbar_wait(smem_addr(&bar_done), 0u)) atomicOr(&g_oz_status, 1u);
     __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 9) {
+  if (warp == OZ_MMA_WARP) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
   }
 }
