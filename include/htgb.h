@@ -215,9 +215,9 @@ ht_status ht_gramians(ht_tensor *x_orth, double *dev_out, int prec);
  * The workspace is one fixed device array of HT_NOALLOC_SCRATCH_BYTES that
  * every GPU loading this library keeps until the process exits; the caller
  * still provides the tensor and dev_out.  The first call on a device looks up
- * the array's device address (with that device current); make that first
- * call before any stream capture.  A tensor whose workspace needs more than
- * the array holds is rejected with HT_ENOMEM and a message giving both sizes.
+ * the array's device address (with that device current).  A tensor whose
+ * workspace needs more than the array holds is rejected with HT_ENOMEM and a
+ * message giving both sizes.
  * All calls share the one array and its contents persist between calls:
  * calls that can run at the same time on the GPU (different streams, or
  * several host threads) race on it and must be serialised by the caller. */
