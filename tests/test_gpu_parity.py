@@ -167,6 +167,16 @@ def test_truncate_eps(dtype):
     _trunc_compare(d, n, a, c, dtype, dict(mode="eps", eps=1e-3, eps_relative=True))
 
 
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_truncate_to_ranks_per_node(dtype):
+    """Target ranks given per node: 0 keeps every rank left after
+    orthogonalization, the root's two sons keep the smaller of their targets."""
+    d, n, a, c = _case("uneven")
+    ranks = np.array([1, 4, 2, 3, 5, 0, 3, 2, 4])
+    rep, ref = _trunc_compare(d, n, a, c, dtype, dict(mode="rank", ranks=ranks))
+    assert list(ref["k"]) == [1, 4, 2, 3, 4, 7, 3, 2, 4]
+
+
 def test_truncate_x_plus_x():
     (n, ka, xa), _ = I.small_pair(9)
     d = 8

@@ -226,6 +226,28 @@ def test_truncation_equals_full_svd_truncation(seed, r):
     assert rel(_full(d, n, res["k"], res["x"]), ref) < 1e-11
 
 
+@pytest.mark.parametrize("seed,ranks,effective", [
+    (3, [1, 5, 3, 2, 3, 0, 4], [1, 3, 3, 2, 3, 8, 4]),
+    (4, [1, 2, 4, 1, 6, 2, 5], [1, 2, 4, 1, 2, 2, 5]),
+])
+def test_truncation_to_prescribed_ranks_per_node(seed, ranks, effective):
+    """Target ranks given per node (Sec. 3.5, truncation to prescribed ranks):
+    node t keeps ranks[t] (0: every rank left after orthogonalization), and the
+    root's two sons, whose matricizations are transposes of each other, keep
+    the smaller of their two targets.  The result is the projection of the full
+    tensor onto the leading singular vectors of each matricization with those
+    ranks; a rank read from the wrong node (a father's, a brother's) or a root
+    pair left unequal gives a different tensor."""
+    (n, ka, xa), (_, kc, xc) = I.brute_pair(seed)
+    d = 4
+    k, x = O.add(d, n, ka, xa, kc, xc)
+    res = O.truncate(d, n, k, x, mode="rank", ranks=np.array(ranks))
+    assert list(res["k"]) == effective
+    full = _full(d, n, k, x)
+    ref = F.brute_truncate(d, full, effective)
+    assert rel(_full(d, n, res["k"], res["x"]), ref) < 1e-11
+
+
 @pytest.mark.parametrize("seed", [1, 3, 8])
 def test_truncation_error_bounds(seed):
     """||A - T(A)|| <= sqrt(sum discarded sigma^2) <= sqrt(2d-3) max_t tail_t <= sqrt(2d-3) best."""
