@@ -359,6 +359,32 @@ def test_eps_rank_rule_against_full_svds(seed, eps):
     assert len(set(want[1:])) > 1  # the cases cut at different ranks per node
 
 
+@pytest.mark.parametrize("seed,eps,cap", [(7, 1e-2, 5), (2, 1e-1, 4), (5, 3e-2, 5)])
+def test_eps_rank_rule_with_rank_cap(seed, eps, cap):
+    """Accuracy with a rank cap (Sec. 5 truncates to an accuracy with a bound
+    on the ranks): each node takes the eps rule's rank, then the cap; the
+    root's second son follows the first.  The cap cuts below the eps rank at
+    some nodes and not at others in these cases."""
+    (n, ka, xa), (_, kc, xc) = I.brute_pair(seed)
+    d = 4
+    k, x = O.add(d, n, ka, xa, kc, xc)
+    full = F.frames(d, n, k, x)[1]
+    res = O.truncate(d, n, k, x, mode="eps", eps=eps, eps_relative=True, rank_cap=cap)
+    plain = _eps_ranks_from_svds(d, full, res["korth"], eps, 0.0)
+    want = [1] + [min(r, cap) for r in plain[1:]]
+    assert list(res["k"]) == want
+    assert any(r > cap for r in plain[1:]) and any(r < cap for r in plain[1:])
+    # the discarded energy is what the capped ranks leave out, root pair once
+    tr = I.tree(d)
+    disc = 0.0
+    for t in range(1, 2 * d - 1):
+        if t == tr["son2"][0]:
+            continue
+        s = np.linalg.svd(F.matricization(full, tr["lo"][t], tr["hi"][t]), compute_uv=False)
+        disc += float(np.sum(s[want[t]:] ** 2))
+    assert abs(res["discarded_sq"] - disc) <= 1e-12 * float(np.sum(full ** 2))
+
+
 @pytest.mark.parametrize("seed,eps,noise", [(7, 1e-2, 3e-6), (7, 3e-2, 1e-5), (5, 1e-1, 3e-4), (5, 3e-1, 3e-3)])
 def test_eps_rank_rule_noise_floor(seed, eps, noise):
     """The rule with a charge nu_t = noise * sigma_{t,1}^2 per dropped
