@@ -2628,10 +2628,11 @@ static ht_status truncate_many(ht_tensor *const *xs, int count, const ht_trunc_o
   if (o->mode != HT_TRUNC_RANK && o->mode != HT_TRUNC_EPS) return fail(HT_EINVAL, "bad mode");
   if (o->mode == HT_TRUNC_EPS && !(o->eps >= 0.0)) return fail(HT_EINVAL, "eps must be >= 0");
   if (o->qr_kernel < 0 || o->qr_kernel > 3) return fail(HT_EINVAL, "qr_kernel must be 0, 1, 2 or 3");
+  for (int i = 0; i < count; ++i)
+    if (!xs[i]) return fail(HT_EINVAL, "null tensor");
   const int dtype = xs[0]->dtype;
   cudaStream_t s = xs[0]->stream;
   for (int i = 0; i < count; ++i) {
-    if (!xs[i]) return fail(HT_EINVAL, "null tensor");
     if (xs[i]->dtype != dtype) return fail(HT_EINVAL, "batch mixes dtypes");
     HT_TRY(check_prec(xs[i], o->prec));
     HT_TRY(sync_ranks(xs[i]));
