@@ -22,18 +22,20 @@
 //     2^(-8(i+j+2)); summed over <= 256 reduction indices, the diagonals
 //     i+j = 0 (|d_0 d_0'| <= 2^16) and i+j = 1 (<= 2^16 per index) stay below
 //     2^24 grid units, i.e. their FP32 sums are exact whatever the order of
-//     the additions; i+j = 2 rounds at most at 2^-24 of its own size, which is
-//     2^-40 of the result's scale, and all products with i+j >= 3 share a
-//     fourth accumulator (rounding at about 2^-48 of the scale).
+//     the additions.  With S = 5 all products with i+j >= 2 share a third
+//     accumulator, which rounds at most at 2^-24 of its own size, 2^-40 of the
+//     result's scale; with S = 6 (the Gramian contractions) i+j = 2 keeps the
+//     third and i+j >= 3 share a fourth (rounding at about 2^-48 of the
+//     scale).
 //   * Products with i+j >= S are dropped; with the rounding of F this leaves a
 //     normwise error of about 2^-(8S) |A| |B| per product: S = 5 gives about
 //     2^-40 of the row scale, far below what the 1e-6 results of the mixed
 //     path need and well beyond FP32 (2^-24).
-//   * The four accumulators are read from TMEM, summed in double-float FP32
-//     arithmetic and assembled into FP64 (scaled by 2^(E_row + E_col)) with
-//     integer operations, then written (or written as a split-K partial; the
-//     chunks of a long reduction are added in FP64 by the reduction kernel of
-//     k_gemm.cu).
+//   * The three or four accumulators are read from TMEM, summed in
+//     double-float FP32 arithmetic and assembled into FP64 (scaled by
+//     2^(E_row + E_col)) with integer operations, then written (or written as
+//     a split-K partial; the chunks of a long reduction are added in FP64 by
+//     the reduction kernel of k_gemm.cu).
 //
 // Kernels:
 //   oz_split_kernel  one CTA per (item, operand, batch, 128-row block, chunk):
@@ -70,13 +72,13 @@ __device__ unsigned g_oz_status = 0;
 namespace {
 
 constexpr int OZ_M = 128;                       // rows of a tile (MMA M); also the rows of one split block
-constexpr int OZ_N = 128;                       // columns of a tile (MMA N)
+constexpr int OZ_N = 128;                       // rows of a B-operand slice block (two 64-column GEMM tiles)
 constexpr int OZ_KC = 32;                       // reduction indices per stage
 constexpr uint32_t OZ_BLK = OZ_M * OZ_KC * 2;   // bytes of one slice block of one stage (8 KB)
 constexpr int OZ_THREADS = 576;                 // warps 0-15 epilogue, 16 producer, 17 MMA
 constexpr int OZ_EPI_THREADS = 512;
 constexpr int OZ_PROD_WARP = 16, OZ_MMA_WARP = 17;
-constexpr int OZ_TMEM_COLS = 512;               // four FP32 accumulators of 128 columns
+constexpr int OZ_TMEM_COLS = 512;               // two tile buffers of up to four FP32 accumulators of 64 columns
 constexpr int OZ_EXP_NONFINITE = 0x7FF0;        // exponent marking a row with NaN / Inf
 
 __device__ __forceinline__ int eff_dim(int lit, int ref, int mult, const int *ranks) {
