@@ -1,7 +1,7 @@
 // dfloat.cuh -- double-float helpers (a value held as an unevaluated sum h + l
 // of two FP32 numbers) shared by the tensor-core contractions (k_oz.cu) and
 // the double-float QR blocks (k_qr_df.cu).  The FP64 pipe of this GPU runs at
-// about 1/64 of the FP32 rate, so FP64-accurate work that is not a dense
+// about 1/62 of the FP32 rate, so FP64-accurate work that is not a dense
 // contraction is cheaper in pairs of FP32 numbers, and conversions to FP64 are
 // built with integer operations.
 #pragma once

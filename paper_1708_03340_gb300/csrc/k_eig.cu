@@ -9,6 +9,11 @@
 // rotations to its own rows of H.  On GB300 a dependent FP64 operation costs
 // ~64 cycles and an FP64 divide or square root ~430-670 cycles, so the
 // recurrence uses one reciprocal square root per rotation and no divides.
+// The eigenvector matrix lives in shared memory, or, for launches with more
+// matrices than SMs, in the L2-resident scratch so that four CTAs share an SM
+// and overlap their recurrences.  On the mixed path (df_rot) the rotations are
+// applied to the eigenvectors in double-float on the FP32 pipe; the recurrence
+// itself, which decides the eigenvalues, stays in FP64.
 //
 // refine_df_kernel: one step of the Ogita-Aishima iterative refinement
 // (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue

@@ -206,7 +206,7 @@ __device__ __forceinline__ unsigned long long combine_to_f64(float d0, float d1,
 // these words is the order of the exponents, so the largest word of a row
 // carries the row's largest exponent; a word >= kHiNonFinite is Inf or NaN.
 // Integer operations only: compares and maxima of FP64 values would run on the
-// FP64 pipe (1/64 of the FP32 rate on this GPU).
+// FP64 pipe (about 1/62 of the FP32 rate on this GPU).
 constexpr uint32_t kHiNonFinite = 0x7FF00000u;
 __device__ __forceinline__ uint32_t abs_hi(double x) {
   return (uint32_t)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7FFFFFFFu;

@@ -4,7 +4,7 @@
 // FP64 register-resident kernel of k_qr.cu (the leaf level of the TSQR behind
 // the reduced QR decompositions of Sec. 3.4: leaf frames U = Q R and
 // M_{2,3}(B_t) = Q R_t, eq. "qrtransfer"), with the arithmetic moved from the
-// FP64 pipe (about 1/64 of the FP32 rate on this GPU) to the FP32 pipe: one
+// FP64 pipe (about 1/62 of the FP32 rate on this GPU) to the FP32 pipe: one
 // FP64 multiply-add becomes about 13 FP32 instructions.
 //
 // Layout: as in k_qr.cu, warp w owns columns 4w..4w+3, one per group of 8
