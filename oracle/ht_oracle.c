@@ -3,8 +3,8 @@
  * Hierarchical Tucker (HT) tensor after HT addition.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
- * CPU-baseline leg of the benchmark may load this file.  The product (the
- * CUDA library) shares no code with it.
+ * CPU-baseline and reference legs of the benchmark may load this file.  The
+ * product (the CUDA library) shares no code with it.
  *
  * Every routine follows the paper (Grasedyck & Loebbert, "Distributed
  * Hierarchical SVD in the Hierarchical Tucker Format"), cited by section and
